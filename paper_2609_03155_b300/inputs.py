@@ -1,0 +1,191 @@
+"""Seeded synthetic inputs: hexahedral meshes, materials and boundary tags.
+
+This module holds no arithmetic of the DPG method.  It produces the plain
+arrays that both the CUDA path (through ``dpg_setup_mesh``) and the test
+oracle consume, shaped like the paper's cases:
+
+* rectangular waveguides with PEC walls, a TE_mn port at x3 = 0 and an
+  impedance outlet at the far end (Sec. 4.1, Table of App. C.1);
+* box cavities with PEC walls and a tangential Dirichlet excitation
+  n x E = (sin(pi x2), 0, 0) on the top face (the Fichera excitation of
+  Sec. 4.2), optionally with jittered interior vertices and per-element
+  random permittivity.
+
+Random numbers come from splitmix64 (Steele, Lea, Flood 2014), a counter-based
+generator: value k of stream s is splitmix64(seed + s * 2^32 + k), so every
+draw can be recomputed independently.
+
+Mesh conventions: vertex v = i + 2 j + 4 k of an element sits at reference
+corner (i, j, k); every element's local axes point along the global +x1, +x2,
++x3 directions.  Face f = 2 d + s is the face xi_d = s.  Boundary tags:
+face_bc 0 = none, 1 = Dirichlet (group in face_grp indexes ``dirichlet``),
+2 = Robin (group indexes ``robin``).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BC_NONE, BC_DIRICHLET, BC_ROBIN = 0, 1, 2
+DIRICHLET_ZERO, DIRICHLET_SIN_PI_X2, DIRICHLET_TE = 0, 1, 2
+C0 = 299792458.0
+
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(x):
+    """splitmix64 finaliser applied to uint64 array x (wrapping arithmetic)."""
+    x = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over='ignore'):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed, stream, count):
+    """count doubles in [0,1) from the counter-based stream (seed, stream)."""
+    ctr = np.uint64(seed) + np.uint64(stream) * np.uint64(1 << 32) + np.arange(count, dtype=np.uint64)
+    return (splitmix64(ctr) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+@dataclass
+class Mesh:
+    vert: np.ndarray            # (nv, 3) float64
+    elem: np.ndarray            # (ne, 8) int32
+    p: np.ndarray               # (ne,) int8
+    eps: np.ndarray             # (ne,) complex128, dimensionless, loss => Im > 0
+    mu: np.ndarray              # (ne,) complex128
+    face_bc: np.ndarray         # (ne, 6) int8
+    face_grp: np.ndarray        # (ne, 6) int16
+    omega: float                # dimensionless angular frequency 2 pi f L / c0, L = 1 m
+    robin: list = field(default_factory=list)      # [{'zinv': complex, 'port': None | (a, b, m, n, eps, mu)}]
+    dirichlet: list = field(default_factory=list)  # [{'kind': int, 'port': None | (a, b, m, n, eps, mu)}]
+    name: str = ""
+    grid: tuple = None          # (nx, ny, nz) for structured meshes
+
+    @property
+    def n_elem(self):
+        return self.elem.shape[0]
+
+
+def omega_from_hz(f_hz, L=1.0):
+    return 2.0 * np.pi * f_hz * L / C0
+
+
+def te_zinv(omega, a, b, m, n, eps=1.0, mu=1.0):
+    """Impedance parameter k3 / (omega mu) of a TE_mn guide (the paper's port/outlet value)."""
+    kc2 = (m * np.pi / a) ** 2 + (n * np.pi / b) ** 2
+    k3 = np.sqrt(complex(omega * omega * eps * mu - kc2))
+    return k3 / (omega * mu)
+
+
+def structured_hex(lx, ly, lz, nx, ny, nz, origin=(0.0, 0.0, 0.0)):
+    """Uniform hex grid: vertices (nv,3), elements (ne,8), element grid coords (ne,3)."""
+    xs = origin[0] + np.linspace(0.0, lx, nx + 1)
+    ys = origin[1] + np.linspace(0.0, ly, ny + 1)
+    zs = origin[2] + np.linspace(0.0, lz, nz + 1)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing='ij')
+    vert = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    vid = lambda i, j, k: (k * (ny + 1) + j) * (nx + 1) + i
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing='ij')
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    elem = np.zeros((i.size, 8), dtype=np.int32)
+    for v in range(8):
+        di, dj, dk = v & 1, (v >> 1) & 1, (v >> 2) & 1
+        elem[:, v] = vid(i + di, j + dj, k + dk)
+    return vert, elem, np.stack([i, j, k], axis=1)
+
+
+def box_boundary_tags(ijk, nx, ny, nz, spec):
+    """face_bc / face_grp from a per-side spec {'x0': (bc, grp), ...}; sides not given stay 0."""
+    ne = ijk.shape[0]
+    bc = np.zeros((ne, 6), dtype=np.int8)
+    grp = np.zeros((ne, 6), dtype=np.int16)
+    n = (nx, ny, nz)
+    for d, axis in enumerate('xyz'):
+        for s in (0, 1):
+            key = f'{axis}{s}'
+            if key not in spec:
+                continue
+            on = ijk[:, d] == (0 if s == 0 else n[d] - 1)
+            bc[on, 2 * d + s] = spec[key][0]
+            grp[on, 2 * d + s] = spec[key][1]
+    return bc, grp
+
+
+def waveguide(a, b, length, nx, ny, nz, f_hz, p, name="waveguide", m=1, n=0):
+    """PEC-walled guide [0,a]x[0,b]x[0,length], TE_mn port at x3=0, impedance end at x3=length."""
+    omega = omega_from_hz(f_hz)
+    vert, elem, ijk = structured_hex(a, b, length, nx, ny, nz)
+    zinv = te_zinv(omega, a, b, m, n)
+    spec = {'x0': (BC_DIRICHLET, 0), 'x1': (BC_DIRICHLET, 0), 'y0': (BC_DIRICHLET, 0),
+            'y1': (BC_DIRICHLET, 0), 'z0': (BC_ROBIN, 0), 'z1': (BC_ROBIN, 1)}
+    bc, grp = box_boundary_tags(ijk, nx, ny, nz, spec)
+    ne = elem.shape[0]
+    return Mesh(vert=vert, elem=elem, p=np.full(ne, p, dtype=np.int8),
+                eps=np.ones(ne, dtype=complex), mu=np.ones(ne, dtype=complex),
+                face_bc=bc, face_grp=grp, omega=omega,
+                robin=[{'zinv': zinv, 'port': (a, b, m, n, 1.0, 1.0)}, {'zinv': zinv, 'port': None}],
+                dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None}], name=name, grid=(nx, ny, nz))
+
+
+def waveguide_2d_config(p=1, refine=1):
+    """0.086 m x 0.043 m guide section in the x1-x3 plane, 8 x 4 cells at refine=1.
+
+    The paper solves only in 3D and shows the x1-x3 plane of its guide; the
+    two-dimensional case is one cell layer in x2 (thickness h = 0.086/8 m, PEC
+    on both x2 faces, which the TE10 field satisfies exactly).
+    """
+    a, length = 0.086, 0.043
+    nx, nz = 8 * refine, 4 * refine
+    h = a / 8
+    return waveguide(a, h, length, nx, 1, nz, 2.45e9, p, name=f"waveguide2d_8x4_r{refine}_p{p}")
+
+
+def waveguide_3d_config(nx=32, ny=16, nz=64, p=2):
+    """WR340-like guide 86.36 x 43.18 x 300 mm, TE10 at 2.45 GHz, uniform hex grid."""
+    return waveguide(0.08636, 0.04318, 0.300, nx, ny, nz, 2.45e9, p,
+                     name=f"waveguide3d_{nx}x{ny}x{nz}_p{p}")
+
+
+def cavity(n, p, omega=5.0, jitter=0.0, seed=20260903, eps_mode=None, name="cavity", L=1.0):
+    """Unit box cavity n^3, PEC walls, top face x3 = L driven by n x E = (sin(pi x2), 0, 0).
+
+    jitter: interior vertices move by U[-jitter h, jitter h]^3; boundary
+    vertices only tangentially, so faces stay planar.  eps_mode 'random':
+    Re eps = exp(U[0, ln 80]), Im eps = U[0, 20] per element (streams 3, 4).
+    """
+    vert, elem, ijk = structured_hex(L, L, L, n, n, n)
+    h = L / n
+    if jitter > 0:
+        nv = vert.shape[0]
+        for d in range(3):
+            u = uniform01(seed, d, nv)
+            dv = (2.0 * u - 1.0) * jitter * h
+            on_bnd = (np.abs(vert[:, d]) < 1e-12) | (np.abs(vert[:, d] - L) < 1e-12)
+            dv[on_bnd] = 0.0
+            vert[:, d] += dv
+    spec = {'x0': (BC_DIRICHLET, 0), 'x1': (BC_DIRICHLET, 0), 'y0': (BC_DIRICHLET, 0),
+            'y1': (BC_DIRICHLET, 0), 'z0': (BC_DIRICHLET, 0), 'z1': (BC_DIRICHLET, 1)}
+    bc, grp = box_boundary_tags(ijk, n, n, n, spec)
+    ne = elem.shape[0]
+    eps = np.ones(ne, dtype=complex)
+    if eps_mode == 'random':
+        re = np.exp(uniform01(seed, 3, ne) * np.log(80.0))
+        im = 20.0 * uniform01(seed, 4, ne)
+        eps = re + 1j * im
+    return Mesh(vert=vert, elem=elem, p=np.full(ne, p, dtype=np.int8), eps=eps,
+                mu=np.ones(ne, dtype=complex), face_bc=bc, face_grp=grp, omega=omega,
+                robin=[], dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None},
+                                     {'kind': DIRICHLET_SIN_PI_X2, 'port': None}],
+                name=name, grid=(n, n, n))
+
+
+def sphere_obstacle(mesh, center=(0.5, 0.5, 0.5), radius=0.2, eps=20.0 + 5.0j):
+    """Set eps on the elements whose centroid lies inside the sphere; returns the mask."""
+    cen = mesh.vert[mesh.elem].mean(axis=1)
+    mask = np.linalg.norm(cen - np.asarray(center)[None, :], axis=1) < radius
+    mesh.eps = mesh.eps.copy()
+    mesh.eps[mask] = eps
+    return mask

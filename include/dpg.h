@@ -1,0 +1,222 @@
+/*
+ * dpg.h -- C ABI of the B300 (sm_103a) DPG time-harmonic Maxwell hot path.
+ *
+ * The method is the discontinuous Petrov-Galerkin (DPG) discretisation of the
+ * dimensionless time-harmonic Maxwell equations in ultraweak form of
+ * arXiv 2609.03155 (Marquis, Maier, Blais):
+ *   Sec. 2.2, Eq. (maxwell_dimensionless): curl E - i w mu H = 0,
+ *             curl H + i w eps E = J (here J = 0), time factor e^{-i w t};
+ *   Sec. 2.2, Eqs. (bilinear_form), (trace_pairing), (linear_form) and the
+ *             adjoint graph test norm Eq. (test_inner_product) with alpha;
+ *   Sec. 2.3: element block system, the two static condensations,
+ *             Eq. (linear_system), local recovery and the estimator ||Psi||_V;
+ *   Algorithm 1 (solve) and Algorithm 2 (assembly).
+ *
+ * Discrete spaces (reading of Sec. 2.3 and Fig. 1, pinned by the DoF counts of
+ * Sec. 4.1): per component of E and H a discontinuous tensor Lagrange space of
+ * degree p on Gauss-Legendre nodes; traces E-hat, H-hat = tangential traces of
+ * the Nedelec space of FEEC order r = p + 1; test functions F, I in the broken
+ * Nedelec space of order p + 1 + dp.  Nedelec basis of order r, component c:
+ * l^open_{i_c}(xi_c) prod_{d != c} l^closed_{i_d}(xi_d) e_c, open = Lagrange on
+ * the r Gauss-Legendre points, closed = Lagrange on the r + 1 Gauss-Lobatto
+ * points, mapped by the covariant Piola transform.  Quadrature: Gauss-Legendre,
+ * p + dp + 2 points per direction in volume and on faces.
+ *
+ * Element-local ordering (used by every per-element input and output):
+ *   test  [F (n_f), I (n_f)], n_f = 3 rt (rt+1)^2, rt = p + 1 + dp;
+ *   interior trial u = [E_x, E_y, E_z, H_x, H_y, H_z], each (p+1)^3 tensor
+ *         Lagrange coefficients, x-index fastest;            n_u = 6 (p+1)^3;
+ *   trace u-hat = [E-hat (12 r^2), H-hat (12 r^2)]: the Nedelec functions of
+ *         order r (component-major, x-index fastest) whose tangential trace is
+ *         non-zero on some face, in that order;                n_h = 24 r^2.
+ *
+ * Mesh conventions: hexahedra with trilinear geometry; element vertex
+ * v = i + 2 j + 4 k sits at reference corner (i, j, k); every element's local
+ * axes must agree with its neighbours' on shared edges and faces (the setup
+ * rejects meshes where they do not, DPG_ERR_MESH).  Face f = 2 d + s is the
+ * face xi_d = s.
+ *
+ * Memory and errors: every pointer argument documented "host" is read during
+ * the call only; "device" pointers are caller-owned device memory, used on
+ * the given stream in stream order.  The handle owns every internal buffer.
+ * Functions return 0 (DPG_OK) or a negative DPG_ERR_* code and never abort,
+ * trap or print; dpg_last_error() describes the last failure on a handle.
+ * Work is enqueued on the caller's stream; a call synchronises that stream
+ * only when it returns a host value that depends on device work (stated per
+ * function).  Complex numbers are two doubles (re, im), layout-compatible
+ * with C99 double _Complex and CUDA double2.
+ */
+#ifndef DPG_H
+#define DPG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpg_handle dpg_handle;
+typedef void* dpg_stream; /* a cudaStream_t; NULL = legacy default stream */
+typedef struct { double re, im; } dpg_complex;
+
+enum {
+  DPG_OK = 0,
+  DPG_ERR_ARG = -1,            /* invalid argument (null pointer, size, range) */
+  DPG_ERR_MESH = -2,           /* invalid mesh: ids, orientation, Jacobian, tags */
+  DPG_ERR_NOMEM = -3,          /* device or host allocation failed */
+  DPG_ERR_NOT_HPD = -4,        /* a Cholesky pivot was not positive (status per element) */
+  DPG_ERR_NOT_CONVERGED = -5,  /* CG hit its iteration limit */
+  DPG_ERR_TIMEOUT = -6,        /* a bounded device wait gave up */
+  DPG_ERR_CUDA = -7,           /* a CUDA runtime call failed */
+  DPG_ERR_STATE = -8,          /* call out of order (e.g. solve before assemble) */
+  DPG_ERR_UNSUPPORTED = -9     /* valid request this build does not implement */
+};
+
+enum { DPG_BC_NONE = 0, DPG_BC_DIRICHLET = 1, DPG_BC_ROBIN = 2 };
+enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2 };
+enum { DPG_PREC_FP64 = 0 };
+enum { DPG_PASS_ASSEMBLE = 0 };
+enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1 };
+
+/* Robin group (Sec. 2.2, Eq. robin_boundary; Sec. 4.1 port / outlet):
+ * n x H + Z^{-1} n x (E x n) = g.  port = 0: g = 0; port = 1: g is the TE_mn
+ * datum n x H_TE + Z^{-1} n x (E_TE x n) of the mode of Sec. 4.1 in the guide
+ * [0,a] x [0,b] (x3 = propagation axis) filled with (eps, mu). */
+typedef struct {
+  double zinv_re, zinv_im;
+  int32_t port;
+  int32_t m, n;
+  double a, b;
+  double eps_re, eps_im, mu_re, mu_im;
+} dpg_robin_group;
+
+/* Dirichlet group (Sec. 2.2, Eq. dirichlet_boundary): n x E = n x E_D on the
+ * trace E-hat, imposed by nodal interpolation of the tangential datum.
+ * kind ZERO: PEC; SIN_PI_X2: n x E = (sin(pi x2), 0, 0) (Sec. 4.2 excitation);
+ * TE: E_D = E of the TE_mn mode described as in dpg_robin_group.  On an edge
+ * shared by a ZERO face and a data face the data face wins. */
+typedef struct {
+  int32_t kind;
+  int32_t m, n;
+  double a, b;
+  double eps_re, eps_im, mu_re, mu_im;
+} dpg_dirichlet_group;
+
+/* Mesh (host arrays, read during dpg_setup_mesh only). */
+typedef struct {
+  int32_t n_vert;
+  const double* vert;          /* n_vert x 3 */
+  int32_t n_elem;
+  const int32_t* elem;         /* n_elem x 8 vertex ids */
+  const int8_t* elem_p;        /* n_elem trial degree, 1..4 (uniform in this build) */
+  const dpg_complex* elem_eps; /* n_elem relative permittivity, loss => Im > 0 */
+  const dpg_complex* elem_mu;  /* n_elem relative permeability */
+  const int8_t* face_bc;       /* n_elem x 6, DPG_BC_*; boundary faces only */
+  const int16_t* face_grp;     /* n_elem x 6, index into robin[] / dirichlet[] */
+  int32_t n_robin;
+  const dpg_robin_group* robin;
+  int32_t n_dirichlet;
+  const dpg_dirichlet_group* dirichlet;
+} dpg_mesh_desc;
+
+typedef struct {
+  double omega;      /* dimensionless angular frequency (App. A, L = 1 m) */
+  double alpha;      /* test-norm weight alpha of Eq. (test_inner_product), > 0 */
+  int32_t dp;        /* enrichment, must be 1 in this build */
+  int32_t precision; /* DPG_PREC_FP64 */
+  int32_t chunk;     /* elements per batched launch, 0 = automatic */
+  int32_t reserved;
+} dpg_params;
+
+typedef struct {
+  int32_t iterations;      /* total CG iterations (inner ones for IR) */
+  int32_t outer;           /* IR outer corrections (0 for plain CG) */
+  double rel_residual;     /* final ||b - A x|| / ||b||, FP64 */
+  double ms;               /* device time of the solve */
+  int32_t converged;
+  int32_t reserved;
+} dpg_cg_report;
+
+/* Build the DPG discretisation of the mesh on the current CUDA device:
+ * trace numbering (entity based), Dirichlet values, removal of the H-hat
+ * unknowns that pair with nothing (Robin faces, end of Sec. 2.3), CSR pattern
+ * of the condensed trace system, reference tables, and every device buffer.
+ * Errors: DPG_ERR_ARG (null / out of range), DPG_ERR_MESH (bad ids,
+ * inconsistent orientation, non-positive Jacobian at a corner, dp != 1,
+ * mixed p), DPG_ERR_NOMEM, DPG_ERR_CUDA.  On error *h is NULL.
+ * Synchronises the stream before returning. */
+int dpg_setup_mesh(dpg_handle** h, const dpg_mesh_desc* mesh, const dpg_params* prm, dpg_stream s);
+
+/* Element pass (Algorithm 2 minus the distribution): for every element form
+ * G_K, B_K, B-hat_K, l_K by quadrature (Sec. 2.3), factor G_K = L L^H, condense
+ * to S_K = M3 - M2^H M1^{-1} M2 and s_K (Eq. linear_system), and keep S_K, s_K,
+ * M1^{-1} M2, M1^{-1} M4 l and the scalar l^H G^{-1} l - (M4 l)^H M1^{-1} M4 l
+ * in handle-owned per-element storage.  pass must be DPG_PASS_ASSEMBLE.
+ * A non-positive pivot marks the element (DPG_ERR_NOT_HPD is returned by the
+ * next call that synchronises). Asynchronous. */
+int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream s);
+
+/* DistributeLocalToGlobal of Algorithm 2: sum the stored S_K, s_K into the
+ * handle-owned CSR matrix and right-hand side of Eq. (linear_system), with
+ * Dirichlet lifting b -= S_{free,fixed} x_D.  Deterministic (elements are
+ * summed in a fixed colour order, no atomics).  Asynchronous.
+ * Errors: DPG_ERR_STATE if no element pass has run. */
+int dpg_assemble(dpg_handle* h, dpg_stream s);
+
+/* Unpreconditioned conjugate gradients on the Hermitian positive definite
+ * system (Sec. 2.3 end): x0 = 0, stop when ||r|| <= max(rtol ||b||, atol).
+ * mode DPG_CG_FP64: plain FP64 CG.  DPG_CG_IR_FP32: iterative refinement,
+ * FP64 residuals and updates around FP32 inner CG solves on an FP32 copy of
+ * the matrix (inner relative tolerance inner_rtol).
+ * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or
+ * NULL for the assembled right-hand side.  rep: host, may be NULL.
+ * Synchronises the stream (the report is a host value).
+ * Errors: DPG_ERR_NOT_CONVERGED (x holds the last iterate), DPG_ERR_STATE. */
+int dpg_cg_solve(dpg_handle* h, int32_t mode, double rtol, double atol, int32_t max_iter,
+                 double inner_rtol, dpg_complex* x, const dpg_complex* b,
+                 dpg_cg_report* rep, dpg_stream s);
+
+/* Local recovery and residual estimator (Sec. 2.3): for the trace solution
+ * xhat (device, n complex) compute per element u_K = M1^{-1}(M4 l - M2 uhat_K)
+ * (u: device, n_elem x n_u complex, element-local order above, may be NULL)
+ * and eta_K = ||Psi_K||_V with Psi_K = G^{-1}(l - B u - B-hat uhat)
+ * (eta: device, n_elem doubles, may be NULL), evaluated as the minimum of the
+ * element's residual quadratic, eta_K^2 = c_K - 2 Re(uhat^H s_K) + uhat^H S_K uhat.
+ * eta_global: host, sqrt(sum eta_K^2) (may be NULL; synchronises if given). */
+int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
+                 double* eta_global, dpg_stream s);
+
+/* Sizes: n = free trace unknowns, nnz of the CSR matrix, per-element sizes. */
+int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_elem, int32_t* n_v,
+              int32_t* n_u, int32_t* n_h);
+
+/* Element-local to global trace map (host out, n_elem x n_h int32):
+ * >= 0 free unknown index, -1 fixed by Dirichlet data, -2 removed (unpaired H-hat).
+ * fixed_val (host out, n_elem x n_h complex, may be NULL): value of fixed
+ * entries (0 elsewhere). */
+int dpg_trace_map(dpg_handle* h, int32_t* map, dpg_complex* fixed_val);
+
+/* Debug dump for parity tests: for n_ids element ids (host) write into host
+ * buffers (each may be NULL) G (n_v x n_v, row-major), B (n_v x n_u),
+ * B-hat (n_v x n_h), l (n_v), S (n_h x n_h), s (n_h).  Runs the element
+ * formation and condensation for those elements only; synchronises. */
+int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids, dpg_complex* G,
+                     dpg_complex* B, dpg_complex* Bh, dpg_complex* l, dpg_complex* S,
+                     dpg_complex* s, dpg_stream st);
+
+/* Copy of the assembled CSR system to host buffers (each may be NULL):
+ * row_ptr (n + 1 int64), col (nnz int32), val (nnz complex), b (n complex). */
+int dpg_csr_copy(dpg_handle* h, int64_t* row_ptr, int32_t* col, dpg_complex* val,
+                 dpg_complex* b, dpg_stream s);
+
+/* Device FP64 and FP32 fused-multiply-add throughput (FLOP/s) measured by a
+ * short probe kernel on the current device (used to state roofline peaks). */
+int dpg_probe_peaks(double* fp64_flops, double* fp32_flops, dpg_stream s);
+
+const char* dpg_last_error(dpg_handle* h);
+void dpg_destroy(dpg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPG_H */

@@ -1,0 +1,143 @@
+// Internal declarations of the DPG library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dpg.h"
+
+namespace dpg {
+
+constexpr int MAXP = 4;          // largest trial degree
+constexpr int MAXF1D = MAXP + 3; // largest 1D family size: closed rule of order rt = p + 2 has rt + 1
+constexpr int MAXPT = MAXP + 5;  // quadrature points p + 3, plus the endpoints 0 and 1
+
+// 1D function families tabulated on the extended point set
+// [Gauss-Legendre points of the element rule (nq1), 0, 1].
+enum Family { F_OPEN_T = 0, F_CLOSED_T = 1, F_OPEN_R = 2, F_CLOSED_R = 3, F_L2 = 4, NFAM = 5 };
+
+struct Tables {
+  int p, r, rt, nq1, npt;          // npt = nq1 + 2
+  int nfun[NFAM];                  // functions per family
+  double pt[MAXPT];                // the extended 1D points
+  double w[MAXPT];                 // Gauss-Legendre weights (first nq1 entries)
+  double val[NFAM][MAXPT][MAXF1D]; // l_j(pt)
+  double der[NFAM][MAXPT][MAXF1D]; // l_j'(pt)
+};
+
+// Element sizes for degree p and dp = 1.
+struct Sizes {
+  int p, r, rt, nq1, nq, nqf;
+  int n_f, n_v, nL, n_u, nt, n_h, N;  // N = augmented system size n_v + n_u + n_h + 1
+};
+Sizes make_sizes(int p);
+
+// Host-side reference computations (tables.cpp).
+void gauss_legendre01(int n, double* x, double* w);
+void gauss_lobatto01(int n, double* x);
+void lagrange1d(const double* nodes, int n, double x, double* val, double* der);
+void build_tables(int p, Tables* t);
+// Packed Nedelec function id: c | i0 << 2 | i1 << 6 | i2 << 10.
+inline int pack_fun(int c, int i0, int i1, int i2) { return c | (i0 << 2) | (i1 << 6) | (i2 << 10); }
+// Trace functions of order r in element-local order (12 r^2 entries).
+std::vector<int> trace_functions(int r);
+
+struct RobinEntry {  // one Robin face of one element
+  int elem, face, grp;
+};
+
+// Per-chunk device workspace of the element pipeline.
+struct Workspace {
+  int cap = 0;               // elements per chunk
+  double2* K = nullptr;      // cap x N x N augmented Hermitian system (column-major, lower used)
+  double* V = nullptr;       // cap x 3nq x n_f   sqrt(w detJ) psi
+  double* Cu = nullptr;      // cap x 3nq x n_f   sqrt(w detJ) curl psi
+  double* PhiL = nullptr;    // cap x 3nq x 3nL   sqrt(w detJ) L e_d
+  double* MC = nullptr;      // cap x (2 n_f^2 + 2 n_f 3nL): M, C, P, Q
+  int* ids = nullptr;        // cap element ids of the chunk
+  // Robin face scratch (per Robin entry of the chunk)
+  int rcap = 0;
+  double* FV = nullptr;      // rcap x 3nqf x (2 n_f + nt + 2)
+  double* FR = nullptr;      // rcap x (2 n_f^2 + n_f nt + 2 n_f)
+  int* rent = nullptr;       // rcap x 4 (elem slot, face, grp, elem id)
+};
+
+}  // namespace dpg
+
+struct dpg_handle {
+  std::string err;
+  dpg::Sizes sz{};
+  dpg::Tables tab{};
+  int ne = 0;
+  double omega = 0, alpha = 1;
+  // host copies used by setup / dumps
+  std::vector<dpg_robin_group> robin;
+  std::vector<dpg_dirichlet_group> dirichlet;
+  std::vector<dpg::RobinEntry> robin_entries;  // sorted by element
+  std::vector<int> robin_first;                // per element: first entry index or -1
+  std::vector<int> color_off;                  // element ids sorted by colour: offsets
+  std::vector<int> color_elems;
+  int64_t n = 0, nnz = 0;
+  std::vector<int32_t> l2g;                    // ne x n_h
+  // device buffers
+  double* d_X = nullptr;        // ne x 24 corner coordinates
+  double2* d_eps = nullptr;     // ne
+  double2* d_mu = nullptr;      // ne
+  int8_t* d_fbc = nullptr;      // ne x 6
+  double* d_Xref = nullptr;     // n_f x n_f  int curl psi_i . psi_j (metric free)
+  double* d_Tf = nullptr;       // 6 x n_f x nt  int_f psi_i . (N x phi_t) (metric free)
+  double* d_Tall = nullptr;     // n_f x nt
+  int* d_trfun = nullptr;       // nt packed trace functions
+  int32_t* d_l2g = nullptr;     // ne x n_h
+  double2* d_xfix = nullptr;    // ne x n_h
+  int* d_color_elems = nullptr; // ne
+  dpg_robin_group* d_robin = nullptr;
+  int* d_status = nullptr;      // ne
+  // per-element stores
+  double2* d_S = nullptr;       // ne x n_h x n_h
+  double2* d_s = nullptr;       // ne x n_h
+  double* d_c = nullptr;        // ne
+  double2* d_Z = nullptr;       // ne x n_u x n_h  (M1^{-1} M2)
+  double2* d_z = nullptr;       // ne x n_u        (M1^{-1} M4 l)
+  // CSR system
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  double2* d_val = nullptr;
+  double2* d_b = nullptr;
+  float2* d_val32 = nullptr;    // FP32 copy for IR inner solves (lazily built)
+  bool have_elements = false, have_system = false, have_val32 = false;
+  // CG scratch
+  double2 *d_r = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_xw = nullptr;
+  float2 *d_r32 = nullptr, *d_p32 = nullptr, *d_Ap32 = nullptr, *d_x32 = nullptr;
+  double* d_red = nullptr;      // reduction scratch
+  double* d_scal = nullptr;     // device scalars of the CG recurrences
+  int red_blocks = 0;
+  dpg::Workspace ws;
+};
+
+namespace dpg {
+// setup.cpp
+int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cudaStream_t s);
+// element.cu
+int alloc_workspace(dpg_handle* h, int cap);
+int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor,
+                      bool extract);
+int compute_reference_matrices(dpg_handle* h, cudaStream_t s);
+// solve.cu
+int assemble_system(dpg_handle* h, cudaStream_t s);
+int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, double inner_rtol,
+             double2* x, const double2* b, dpg_cg_report* rep, cudaStream_t s);
+int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
+             cudaStream_t s);
+}  // namespace dpg
+
+#define DPG_CUDA_TRY(h, call)                                                     \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+      return DPG_ERR_CUDA;                                                        \
+    }                                                                             \
+  } while (0)

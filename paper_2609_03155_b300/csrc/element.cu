@@ -1,0 +1,901 @@
+// Element pass of the DPG method on sm_103a, complex FP64 (Sec. 2.3, Algorithm 2).
+//
+// Per element K the pass builds the augmented Hermitian matrix
+//
+//        [ G_K        B_K   B-hat_K   0 ]      columns/rows: test (n_v),
+//   K =  [ B_K^H      0     0         0 ]      interior trial (n_u),
+//        [ B-hat_K^H  0     0         0 ]      trace (n_h), load (1);
+//        [ l_K^H      0     0         0 ]      the load is the last row.
+//
+// and eliminates it by one blocked right-looking partial Cholesky: n_v positive
+// pivots (G = L L^H), a sign flip of the trailing block, which then holds
+// A_full = [B B-hat l]^H G^{-1} [B B-hat l], and n_u further pivots (M1 = L1 L1^H).
+// The remaining trailing block is [[S_K, s_K], [s_K^H, c_K]] with
+// S_K = M3 - M2^H M1^{-1} M2 and s_K = (M5 - M2^H M1^{-1} M4) l of Eq. (linear_system),
+// and c_K = l^H G^{-1} l - (M4 l)^H M1^{-1} M4 l, the constant of the element's
+// residual quadratic.  Below L1 sit (L1^{-1} M2)^H and (L1^{-1} M4 l)^H.
+//
+// G_K and B_K come from real quadrature contractions (batched FP64 GEMMs) of
+// weighted, Piola-mapped basis values: with s_q = sqrt(w_q det J_q),
+//   M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL, X = Cu^T V (metric free),
+// and G_FF = C + (|w eps|^2 + alpha) M, G_II = C + (|w mu|^2 + alpha) M,
+// G_FI = i w conj(mu) X + i w eps X^T (+ Robin terms), B = [[i w eps P, Q], [Q, -i w mu P]]
+// (Eq. test_inner_product and Eq. bilinear_form with real basis functions and
+// conjugation on the first argument).  The skeleton pairing of Eq.
+// (trace_pairing) is metric free for covariant Piola functions and Nanson's
+// formula, so B-hat comes from reference face matrices T_f.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "dpg_internal.h"
+
+namespace dpg {
+
+// ---------------------------------------------------------------- helpers --
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// Test function i of the order-rt Nedelec space: component and 1D indices.
+__device__ __forceinline__ void test_index(int i, int rt, int& c, int ii[3]) {
+  const int nc = rt * (rt + 1) * (rt + 1);
+  c = i / nc;
+  int rem = i - c * nc;
+  int n0 = (c == 0) ? rt : rt + 1;
+  int n1 = (c == 1) ? rt : rt + 1;
+  ii[0] = rem % n0;
+  rem /= n0;
+  ii[1] = rem % n1;
+  ii[2] = rem / n1;
+}
+
+// Value f and reference gradient of the scalar factor of a Nedelec function
+// (component c, 1D indices ii) at the extended-grid point (q0, q1, q2).
+// fo/fc: open/closed family of the space (F_OPEN_T/F_CLOSED_T or F_OPEN_R/F_CLOSED_R).
+__device__ __forceinline__ void ned_eval(const Tables& T, int fo, int fc, int c, const int ii[3],
+                                         const int q[3], double& f, double g[3]) {
+  double v[3], d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int fam = (k == c) ? fo : fc;
+    v[k] = T.val[fam][q[k]][ii[k]];
+    d[k] = T.der[fam][q[k]][ii[k]];
+  }
+  f = v[0] * v[1] * v[2];
+  g[0] = d[0] * v[1] * v[2];
+  g[1] = v[0] * d[1] * v[2];
+  g[2] = v[0] * v[1] * d[2];
+}
+
+// reference curl of f e_c: grad f x e_c
+__device__ __forceinline__ void ref_curl(int c, const double g[3], double cu[3]) {
+  if (c == 0) {
+    cu[0] = 0.0; cu[1] = g[2]; cu[2] = -g[1];
+  } else if (c == 1) {
+    cu[0] = -g[2]; cu[1] = 0.0; cu[2] = g[0];
+  } else {
+    cu[0] = g[1]; cu[1] = -g[0]; cu[2] = 0.0;
+  }
+}
+
+// Trilinear map of the corner coordinates X (8 x 3) at reference point xi.
+__device__ __forceinline__ void geom(const double* X, const double xi[3], double J[3][3], double x[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[a] = 0.0;
+    J[a][0] = J[a][1] = J[a][2] = 0.0;
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    double f0 = (v & 1) ? xi[0] : 1.0 - xi[0], d0 = (v & 1) ? 1.0 : -1.0;
+    double f1 = (v & 2) ? xi[1] : 1.0 - xi[1], d1 = (v & 2) ? 1.0 : -1.0;
+    double f2 = (v & 4) ? xi[2] : 1.0 - xi[2], d2 = (v & 4) ? 1.0 : -1.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double Xa = X[3 * v + a];
+      x[a] += f0 * f1 * f2 * Xa;
+      J[a][0] += d0 * f1 * f2 * Xa;
+      J[a][1] += f0 * d1 * f2 * Xa;
+      J[a][2] += f0 * f1 * d2 * Xa;
+    }
+  }
+}
+
+__device__ __forceinline__ double inv3(const double J[3][3], double Ji[3][3]) {
+  double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  double id = 1.0 / det;
+  Ji[0][0] = c00 * id;
+  Ji[1][0] = c01 * id;
+  Ji[2][0] = c02 * id;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  return det;
+}
+
+// complex square root, principal branch
+__device__ __forceinline__ double2 csqrt(double2 z) {
+  double m = hypot(z.x, z.y);
+  double re = sqrt(0.5 * (m + z.x));
+  double im = sqrt(0.5 * fmax(m - z.x, 0.0));
+  return make_double2(re, z.y < 0 ? -im : im);
+}
+
+// TE_mn mode of Sec. 4.1 at x (guide [0,a] x [0,b], propagation along +x3).
+__device__ void te_fields(const dpg_robin_group& g, double omega, const double x[3], double2 E[3],
+                          double2 H[3]) {
+  const double pi = 3.14159265358979323846;
+  double k1 = g.m * pi / g.a, k2 = g.n * pi / g.b, kc2 = k1 * k1 + k2 * k2;
+  double2 eps = make_double2(g.eps_re, g.eps_im), mu = make_double2(g.mu_re, g.mu_im);
+  double2 em = cmul(eps, mu);
+  double2 k3 = csqrt(make_double2(omega * omega * em.x - kc2, omega * omega * em.y));
+  double sn, cs;
+  sincos(k3.x * x[2], &sn, &cs);
+  double dec = exp(-k3.y * x[2]);
+  double2 ph = make_double2(cs * dec, sn * dec);  // e^{i k3 x3}
+  double s1, c1, s2, c2;
+  sincos(k1 * x[0], &s1, &c1);
+  sincos(k2 * x[1], &s2, &c2);
+  double2 pre = cscale(cmul(make_double2(0.0, omega), mu), 1.0 / kc2);  // i w mu / kc^2
+  E[0] = cmul(cscale(pre, -k2 * c1 * s2), ph);
+  E[1] = cmul(cscale(pre, k1 * s1 * c2), ph);
+  E[2] = make_double2(0.0, 0.0);
+  double2 ik3 = make_double2(-k3.y, k3.x);  // i k3
+  H[0] = cmul(cscale(ik3, -k1 / kc2 * s1 * c2), ph);
+  H[1] = cmul(cscale(ik3, -k2 / kc2 * c1 * s2), ph);
+  H[2] = cscale(ph, c1 * c2);
+}
+
+// ------------------------------------------------- volume basis arrays --
+// V[(q*3+a)][i] = s_q (J^{-T} e_c f_i)_a, Cu[(q*3+a)][i] = s_q (J curl_ref / det J)_a,
+// PhiL[(q*3+a)][d*nL+l] = delta_ad s_q L_l(q).
+constexpr int QB = 8;
+
+__global__ void __launch_bounds__(256) k_vol_arrays(const __grid_constant__ Tables T, Sizes S, const double* __restrict__ Xall,
+                                                    const int* __restrict__ ids, double* V, double* Cu, double* PhiL) {
+  const int slot = blockIdx.y;
+  const int e = ids[slot];
+  __shared__ double sX[24];
+  __shared__ double sJi[QB][9], sJs[QB][9], sw[QB];  // J^{-1}, J/detJ scaled, s_q
+  if (threadIdx.x < 24) sX[threadIdx.x] = Xall[(size_t)e * 24 + threadIdx.x];
+  __syncthreads();
+  const int nq1 = S.nq1, nq = S.nq;
+  const int q0b = blockIdx.x * QB;
+  if (threadIdx.x < QB) {
+    int q = q0b + threadIdx.x;
+    if (q < nq) {
+      int qi[3] = {q % nq1, (q / nq1) % nq1, q / (nq1 * nq1)};
+      double xi[3] = {T.pt[qi[0]], T.pt[qi[1]], T.pt[qi[2]]};
+      double J[3][3], x[3], Ji[3][3];
+      geom(sX, xi, J, x);
+      double det = inv3(J, Ji);
+      double s = sqrt(T.w[qi[0]] * T.w[qi[1]] * T.w[qi[2]] * det);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          sJi[threadIdx.x][3 * a + b] = Ji[a][b];
+          sJs[threadIdx.x][3 * a + b] = J[a][b] * (s / det);
+        }
+      sw[threadIdx.x] = s;
+    }
+  }
+  __syncthreads();
+  const size_t nf = S.n_f;
+  const size_t stride = (size_t)3 * nq * nf;
+  double* Ve = V + slot * stride;
+  double* Ce = Cu + slot * stride;
+  const int nqb = min(QB, nq - q0b);
+  for (int idx = threadIdx.x; idx < nqb * S.n_f; idx += blockDim.x) {
+    int ql = idx / S.n_f, i = idx - ql * S.n_f;
+    int q = q0b + ql;
+    int qi[3] = {q % nq1, (q / nq1) % nq1, q / (nq1 * nq1)};
+    int c, ii[3];
+    test_index(i, S.rt, c, ii);
+    double f, g[3], cr[3];
+    ned_eval(T, F_OPEN_T, F_CLOSED_T, c, ii, qi, f, g);
+    ref_curl(c, g, cr);
+    const double* Ji = sJi[ql];
+    const double* Js = sJs[ql];
+    double s = sw[ql];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Ve[((size_t)q * 3 + a) * nf + i] = s * Ji[3 * c + a] * f;  // (J^{-T})_{a c} = (J^{-1})_{c a}
+      Ce[((size_t)q * 3 + a) * nf + i] = Js[3 * a + 0] * cr[0] + Js[3 * a + 1] * cr[1] + Js[3 * a + 2] * cr[2];
+    }
+  }
+  const int nL = S.nL, w3 = 3 * nL;
+  double* Pe = PhiL + slot * (size_t)3 * nq * w3;
+  for (int idx = threadIdx.x; idx < nqb * 3 * w3; idx += blockDim.x) {
+    int ql = idx / (3 * w3), rem = idx - ql * 3 * w3;
+    int a = rem / w3, col = rem - a * w3;
+    int d = col / nL, l = col - d * nL;
+    int q = q0b + ql;
+    int qi[3] = {q % nq1, (q / nq1) % nq1, q / (nq1 * nq1)};
+    int p1 = S.p + 1;
+    int l0 = l % p1, l1 = (l / p1) % p1, l2 = l / (p1 * p1);
+    double v = 0.0;
+    if (a == d) v = sw[ql] * T.val[F_L2][qi[0]][l0] * T.val[F_L2][qi[1]][l1] * T.val[F_L2][qi[2]][l2];
+    Pe[((size_t)q * 3 + a) * w3 + col] = v;
+  }
+}
+
+// --------------------------------------------------------- face arrays --
+// Per (element, face) entry: columns [Vt (n_f) | Nx (n_f) | Pt (nt) | NxP (nt) | g_re | g_im],
+// rows (qf*3+a), all scaled by sqrt(w dS):  Vt = tangential test values,
+// Nx = n x test, Pt = tangential trace values, NxP = n x trace, g = Robin datum.
+__global__ void __launch_bounds__(256) k_face_arrays(const __grid_constant__ Tables T, Sizes S, const double* __restrict__ Xall,
+                                                     const int* __restrict__ rent, const dpg_robin_group* __restrict__ groups,
+                                                     const int* __restrict__ trfun, double omega, int use_unit_cube,
+                                                     double* FV) {
+  const int ent = blockIdx.y;
+  const int e = rent[4 * ent + 3], f = rent[4 * ent + 1], grp = rent[4 * ent + 2];
+  const int d = f >> 1, sd = f & 1;
+  const int nq1 = S.nq1, nqf = S.nqf;
+  const int W = 2 * S.n_f + 2 * S.nt + 2;
+  __shared__ double sX[24];
+  __shared__ double sJi[9], sn[3], ssw;
+  __shared__ int sq[3];
+  if (threadIdx.x < 24) {
+    if (use_unit_cube) {
+      int v = threadIdx.x / 3, a = threadIdx.x % 3;
+      sX[threadIdx.x] = (double)((v >> a) & 1);
+    } else {
+      sX[threadIdx.x] = Xall[(size_t)e * 24 + threadIdx.x];
+    }
+  }
+  double* Fe = FV + (size_t)ent * 3 * nqf * W;
+  for (int qf = 0; qf < nqf; ++qf) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ta = qf % nq1, tb = qf / nq1;
+      int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+      int qi[3];
+      qi[d] = nq1 + sd;  // extended point index of xi_d = sd
+      qi[a] = ta;
+      qi[b] = tb;
+      double xi[3] = {T.pt[qi[0]], T.pt[qi[1]], T.pt[qi[2]]};
+      double J[3][3], x[3], Ji[3][3];
+      geom(sX, xi, J, x);
+      double det = inv3(J, Ji);
+      // Nanson: n dS = det J J^{-T} N_ref, N_ref = (2 sd - 1) e_d
+      double sg = sd ? 1.0 : -1.0;
+      double nv[3] = {det * Ji[d][0] * sg, det * Ji[d][1] * sg, det * Ji[d][2] * sg};
+      double dS = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      for (int k = 0; k < 3; ++k) sn[k] = nv[k] / dS;
+      for (int k = 0; k < 9; ++k) sJi[k] = Ji[k / 3][k % 3];
+      double sw = sqrt(T.w[ta] * T.w[tb] * dS);
+      ssw = sw;
+      sq[0] = qi[0];
+      sq[1] = qi[1];
+      sq[2] = qi[2];
+      // Robin datum g = n x H_TE + zinv (E_TE)_t  (port) or 0
+      double2 gv[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+      if (!use_unit_cube && groups[grp].port) {
+        double2 E[3], H[3];
+        te_fields(groups[grp], omega, x, E, H);
+        double2 zinv = make_double2(groups[grp].zinv_re, groups[grp].zinv_im);
+        double2 En = cadd(cadd(cscale(E[0], sn[0]), cscale(E[1], sn[1])), cscale(E[2], sn[2]));
+        double2 Et[3], nH[3];
+        for (int k = 0; k < 3; ++k) Et[k] = csub(E[k], cscale(En, sn[k]));
+        nH[0] = csub(cscale(H[2], sn[1]), cscale(H[1], sn[2]));
+        nH[1] = csub(cscale(H[0], sn[2]), cscale(H[2], sn[0]));
+        nH[2] = csub(cscale(H[1], sn[0]), cscale(H[0], sn[1]));
+        for (int k = 0; k < 3; ++k) gv[k] = cadd(nH[k], cmul(zinv, Et[k]));
+      }
+      for (int k = 0; k < 3; ++k) {
+        Fe[((size_t)qf * 3 + k) * W + W - 2] = sw * gv[k].x;
+        Fe[((size_t)qf * 3 + k) * W + W - 1] = sw * gv[k].y;
+      }
+    }
+    __syncthreads();
+    const int qi[3] = {sq[0], sq[1], sq[2]};
+    const double n0 = sn[0], n1 = sn[1], n2 = sn[2], sw = ssw;
+    const int nfun = S.n_f + S.nt;
+    for (int k = threadIdx.x; k < nfun; k += blockDim.x) {
+      int c, ii[3];
+      double fv, g[3];
+      if (k < S.n_f) {
+        test_index(k, S.rt, c, ii);
+        ned_eval(T, F_OPEN_T, F_CLOSED_T, c, ii, qi, fv, g);
+      } else {
+        int pk = trfun[k - S.n_f];
+        c = pk & 3;
+        ii[0] = (pk >> 2) & 15;
+        ii[1] = (pk >> 6) & 15;
+        ii[2] = (pk >> 10) & 15;
+        ned_eval(T, F_OPEN_R, F_CLOSED_R, c, ii, qi, fv, g);
+      }
+      // physical value psi = J^{-T} e_c f
+      double ps[3] = {sJi[3 * c + 0] * fv, sJi[3 * c + 1] * fv, sJi[3 * c + 2] * fv};
+      double pn = ps[0] * n0 + ps[1] * n1 + ps[2] * n2;
+      double pt[3] = {ps[0] - pn * n0, ps[1] - pn * n1, ps[2] - pn * n2};
+      double nx[3] = {n1 * ps[2] - n2 * ps[1], n2 * ps[0] - n0 * ps[2], n0 * ps[1] - n1 * ps[0]};
+      int colT = (k < S.n_f) ? k : 2 * S.n_f + (k - S.n_f);      // tangential value column
+      int colN = (k < S.n_f) ? S.n_f + k : 2 * S.n_f + S.nt + (k - S.n_f);  // n x value column
+      for (int a = 0; a < 3; ++a) {
+        Fe[((size_t)qf * 3 + a) * W + colT] = sw * pt[a];
+        Fe[((size_t)qf * 3 + a) * W + colN] = sw * nx[a];
+      }
+    }
+  }
+}
+
+// -------------------------------------------------- batched FP64 GEMM --
+// C[b] (Ma x Nb, row-major, ldc) = A[b]^T B[b]; A: Kd x Ma (lda), B: Kd x Nb (ldb).
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_tn(int Ma, int Nb, int Kd, const double* __restrict__ A, int lda, long long sA,
+                                                 const double* __restrict__ B, int ldb, long long sB, double* C, int ldc,
+                                                 long long sC) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int b = blockIdx.z;
+  const double* Ab = A + b * sA;
+  const double* Bb = B + b * sB;
+  double* Cb = C + b * sC;
+  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < Kd; k0 += GK) {
+    for (int t = threadIdx.x; t < GK * GT; t += 256) {
+      int kk = t / GT, mm = t - kk * GT;
+      int k = k0 + kk;
+      As[kk][mm] = (k < Kd && m0 + mm < Ma) ? Ab[(size_t)k * lda + m0 + mm] : 0.0;
+      Bs[kk][mm] = (k < Kd && n0 + mm < Nb) ? Bb[(size_t)k * ldb + n0 + mm] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int m = m0 + ty + 16 * i;
+    if (m >= Ma) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int n = n0 + tx + 16 * j;
+      if (n < Nb) Cb[(size_t)m * ldc + n] = acc[i][j];
+    }
+  }
+}
+
+static void gemm_tn(int Ma, int Nb, int Kd, const double* A, int lda, long long sA, const double* B, int ldb,
+                    long long sB, double* C, int ldc, long long sC, int batch, cudaStream_t s) {
+  dim3 grid((Nb + GT - 1) / GT, (Ma + GT - 1) / GT, batch);
+  k_gemm_tn<<<grid, 256, 0, s>>>(Ma, Nb, Kd, A, lda, sA, B, ldb, sB, C, ldc, sC);
+}
+
+// ------------------------------------------------------ build K matrix --
+// K (column-major, N x N) from M, C, P, Q, X_ref, T_f; full matrix written.
+__global__ void __launch_bounds__(256) k_build_K(Sizes S, double omega, double alpha, const int* __restrict__ ids,
+                                                 const double2* __restrict__ eps_all, const double2* __restrict__ mu_all,
+                                                 const int8_t* __restrict__ fbc, const double* __restrict__ MC,
+                                                 const double* __restrict__ Xref, const double* __restrict__ Tf,
+                                                 const double* __restrict__ Tall, double2* K) {
+  const int slot = blockIdx.y;
+  const int e = ids[slot];
+  const int N = S.N, nf = S.n_f, nv = S.n_v, nu = S.n_u, nt = S.nt, nL3 = 3 * S.nL;
+  const double2 eps = eps_all[e], mu = mu_all[e];
+  const double a1 = omega * omega * (eps.x * eps.x + eps.y * eps.y) + alpha;
+  const double a2 = omega * omega * (mu.x * mu.x + mu.y * mu.y) + alpha;
+  // i w mu, i w eps
+  const double2 iwmu = make_double2(-omega * mu.y, omega * mu.x);
+  const double2 iweps = make_double2(-omega * eps.y, omega * eps.x);
+  const double* M = MC + (size_t)slot * (2 * (size_t)nf * nf + 2 * (size_t)nf * nL3);
+  const double* Cm = M + (size_t)nf * nf;
+  const double* P = Cm + (size_t)nf * nf;
+  const double* Q = P + (size_t)nf * nL3;
+  int robin_mask = 0;
+  for (int f = 0; f < 6; ++f)
+    if (fbc[(size_t)e * 6 + f] == DPG_BC_ROBIN) robin_mask |= 1 << f;
+  double2* Ke = K + (size_t)slot * N * N;
+  const size_t total = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / N), i = (int)(idx - (size_t)j * N);
+    double2 v = make_double2(0.0, 0.0);
+    if (j < nv && i < nv) {
+      // M and C are symmetric: read [j][i] so that consecutive rows i coalesce
+      if (i < nf && j < nf) {
+        v.x = Cm[(size_t)j * nf + i] + a1 * M[(size_t)j * nf + i];
+      } else if (i >= nf && j >= nf) {
+        v.x = Cm[(size_t)(j - nf) * nf + (i - nf)] + a2 * M[(size_t)(j - nf) * nf + (i - nf)];
+      } else if (i >= nf) {
+        // G_IF[i'][j] = -i w mu X[j][i'] - i w conj(eps) X[i'][j]
+        const int ip = i - nf;
+        double xji = Xref[(size_t)j * nf + ip], xij = Xref[(size_t)ip * nf + j];
+        v = make_double2(-(iwmu.x * xji) - (-omega * (-eps.y)) * xij, -(iwmu.y * xji) - (omega * eps.x) * xij);
+      } else {
+        // G_FI[i][j'] = i w conj(mu) X[i][j'] + i w eps X[j'][i]
+        const int jp = j - nf;
+        double xij = Xref[(size_t)i * nf + jp], xji = Xref[(size_t)jp * nf + i];
+        v = make_double2((omega * mu.y) * xij + iweps.x * xji, (omega * mu.x) * xij + iweps.y * xji);
+      }
+    } else if (j < nv && i < nv + nu) {
+      // K[nv+u][j] = conj(BK[j][u])
+      const int u = i - nv;
+      const bool Fj = j < nf;
+      const int jj = Fj ? j : j - nf;
+      if (u < nL3) {
+        if (Fj) {  // conj(i w eps P)
+          double pv = P[(size_t)jj * nL3 + u];
+          v = make_double2(iweps.x * pv, -iweps.y * pv);
+        } else {
+          v.x = Q[(size_t)jj * nL3 + u];
+        }
+      } else {
+        const int up = u - nL3;
+        if (Fj) {
+          v.x = Q[(size_t)jj * nL3 + up];
+        } else {  // conj(-i w mu P)
+          double pv = P[(size_t)jj * nL3 + up];
+          v = make_double2(-iwmu.x * pv, iwmu.y * pv);
+        }
+      }
+    } else if (j < nv && i < nv + nu + 2 * nt) {
+      const int t = i - nv - nu;
+      if (t < nt) {  // E-hat: <I, n x E-hat> on all faces (real)
+        if (j >= nf) v.x = Tall[(size_t)(j - nf) * nt + t];
+      } else {       // H-hat: <F, n x H-hat> on faces not on Gamma_R
+        if (j < nf) {
+          const int tp = t - nt;
+          double s = Tall[(size_t)j * nt + tp];
+          for (int f = 0; f < 6; ++f)
+            if (robin_mask & (1 << f)) s -= Tf[((size_t)f * nf + j) * nt + tp];
+          v.x = s;
+        }
+      }
+    }
+    Ke[idx] = v;
+  }
+}
+
+// Robin additions (one block per element with Robin faces, its entries in order).
+// FR per entry: n_f x W with W = 2 n_f + 2 nt + 2 = Vt^T [Vt | Nx | Pt | NxP | g].
+__global__ void __launch_bounds__(256) k_robin_add(Sizes S, const int* __restrict__ rlist, const int* __restrict__ rent,
+                                                   const dpg_robin_group* __restrict__ groups, const double* __restrict__ FR,
+                                                   double2* K) {
+  const int el = blockIdx.x;
+  const int first = rlist[2 * el], count = rlist[2 * el + 1];
+  const int N = S.N, nf = S.n_f, nv = S.n_v, nu = S.n_u, nt = S.nt;
+  const int W = 2 * nf + 2 * nt + 2;
+  for (int k = 0; k < count; ++k) {
+    const int ent = first + k;
+    const int slot = rent[4 * ent + 0], grp = rent[4 * ent + 2];
+    const double2 zinv = make_double2(groups[grp].zinv_re, groups[grp].zinv_im);
+    const double z2 = zinv.x * zinv.x + zinv.y * zinv.y;
+    const double* Fr = FR + (size_t)ent * nf * W;
+    double2* Ke = K + (size_t)slot * N * N;
+    for (int idx = threadIdx.x; idx < nf * nf; idx += blockDim.x) {
+      int i = idx / nf, j = idx - i * nf;  // j fastest: K rows j -> strided, acceptable (boundary only)
+      double R = Fr[(size_t)i * W + j];
+      double Xc_ij = Fr[(size_t)i * W + nf + j];
+      double Xc_ji = Fr[(size_t)j * W + nf + i];
+      // column-major K: entry (row, col) at row + col * N
+      double2* g_ff = &Ke[(size_t)i + (size_t)j * N];
+      g_ff->x += z2 * R;
+      double2* g_ii = &Ke[(size_t)(nf + i) + (size_t)(nf + j) * N];
+      g_ii->x += R;
+      // G_IF[i][j] += conj(zinv) Xc[j][i]
+      double2* g_if = &Ke[(size_t)(nf + i) + (size_t)j * N];
+      g_if->x += zinv.x * Xc_ji;
+      g_if->y += -zinv.y * Xc_ji;
+      // G_FI[i][j] += zinv Xc[i][j]
+      double2* g_fi = &Ke[(size_t)i + (size_t)(nf + j) * N];
+      g_fi->x += zinv.x * Xc_ij;
+      g_fi->y += zinv.y * Xc_ij;
+    }
+    for (int idx = threadIdx.x; idx < nf * nt; idx += blockDim.x) {
+      int i = idx / nt, t = idx - i * nt;
+      double Bt = Fr[(size_t)i * W + 2 * nf + t];
+      // K[nv+nu+t][i] += conj(-zinv Bt)
+      double2* kk = &Ke[(size_t)(nv + nu + t) + (size_t)i * N];
+      kk->x += -zinv.x * Bt;
+      kk->y += zinv.y * Bt;
+    }
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+      double lre = Fr[(size_t)i * W + W - 2], lim = Fr[(size_t)i * W + W - 1];
+      // l_i = -(lre + i lim);  K[N-1][i] += conj(l_i)
+      double2* kk = &Ke[(size_t)(N - 1) + (size_t)i * N];
+      kk->x += -lre;
+      kk->y += lim;
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------- blocked partial Cholesky --
+// One CTA per element.  Pivots [0, nv) with positive sign; the trailing block
+// is negated after them; pivots [nv, npiv) again positive.  Lower triangle,
+// column-major, leading dimension N.  Non-positive pivots set status[elem].
+constexpr int NB = 32;   // panel width
+constexpr int TT = 64;   // trailing tile
+
+__global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const int* __restrict__ ids, double2* K,
+                                                int* status) {
+  extern __shared__ double2 sm[];
+  double2* sD = sm;                 // NB x NB diagonal block (column-major)
+  double2* sPI = sD + NB * NB;      // NB x TT panel rows of tile I ([k][row])
+  double2* sPJ = sPI + NB * TT;     // NB x TT panel rows of tile J
+  const int slot = blockIdx.x;
+  double2* A = K + (size_t)slot * N * N;
+  const int tid = threadIdx.x;
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  for (int k0 = 0; k0 < npiv;) {
+    const int stage_end = (k0 < nv) ? nv : npiv;
+    const int w = min(NB, stage_end - k0);
+    const int k1 = k0 + w;
+    if (k0 == nv) {
+      // sign flip: the trailing block now holds -A_full; negate it (lower part)
+      __syncthreads();
+      const size_t R = N - nv;
+      for (size_t t = tid; t < R * R; t += blockDim.x) {
+        int jj = (int)(t / R), ii = (int)(t - (size_t)jj * R);
+        if (ii >= jj) {
+          double2* p = &A[(size_t)(nv + ii) + (size_t)(nv + jj) * N];
+          *p = make_double2(-p->x, -p->y);
+        }
+      }
+      __syncthreads();
+    }
+    // --- diagonal block: load, factor (unblocked), store
+    for (int t = tid; t < w * w; t += blockDim.x) {
+      int jj = t / w, ii = t - jj * w;
+      sD[ii + jj * NB] = (ii >= jj) ? A[(size_t)(k0 + ii) + (size_t)(k0 + jj) * N] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+      if (tid == 0) {
+        double d = sD[j + j * NB].x;
+        if (!(d > 0.0)) {
+          bad = 1;
+          d = 1e-300;
+        }
+        sD[j + j * NB] = make_double2(sqrt(d), 0.0);
+      }
+      __syncthreads();
+      const double ljj = sD[j + j * NB].x;
+      for (int ii = j + 1 + tid; ii < w; ii += blockDim.x) sD[ii + j * NB] = cscale(sD[ii + j * NB], 1.0 / ljj);
+      __syncthreads();
+      // rank-1 update of the remaining lower part of the block
+      const int rem = w - j - 1;
+      for (int t = tid; t < rem * rem; t += blockDim.x) {
+        int cc = j + 1 + t / rem, ii = j + 1 + t % rem;
+        if (ii >= cc) sD[ii + cc * NB] = csub(sD[ii + cc * NB], cmul(sD[ii + j * NB], cconj(sD[cc + j * NB])));
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < w * w; t += blockDim.x) {
+      int jj = t / w, ii = t - jj * w;
+      if (ii >= jj) A[(size_t)(k0 + ii) + (size_t)(k0 + jj) * N] = sD[ii + jj * NB];
+    }
+    // --- panel: rows [k1, N) of columns [k0, k1): X L_D^H = P  (one row per thread)
+    for (int row = k1 + tid; row < N; row += blockDim.x) {
+      double2 x[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (j < w) x[j] = A[(size_t)row + (size_t)(k0 + j) * N];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (j < w) {
+          double2 v = x[j];
+#pragma unroll
+          for (int kk = 0; kk < NB; ++kk)
+            if (kk < j) v = csub(v, cmul(x[kk], cconj(sD[j + kk * NB])));
+          x[j] = cscale(v, 1.0 / sD[j + j * NB].x);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (j < w) A[(size_t)row + (size_t)(k0 + j) * N] = x[j];
+    }
+    __syncthreads();
+    // --- trailing update of the lower triangle of rows/cols [k1, N)
+    const int R = N - k1;
+    const int ntile = (R + TT - 1) / TT;
+    const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16 a, cols ty + 16 b
+    for (int I = 0; I < ntile; ++I) {
+      const int r0 = k1 + I * TT;
+      __syncthreads();
+      for (int t = tid; t < NB * TT; t += blockDim.x) {
+        int kk = t / TT, rr = t - kk * TT;
+        sPI[kk * TT + rr] = (kk < w && r0 + rr < N) ? A[(size_t)(r0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
+      }
+      for (int Jt = 0; Jt <= I; ++Jt) {
+        const int c0 = k1 + Jt * TT;
+        __syncthreads();
+        for (int t = tid; t < NB * TT; t += blockDim.x) {
+          int kk = t / TT, rr = t - kk * TT;
+          sPJ[kk * TT + rr] =
+              (kk < w && c0 + rr < N) ? A[(size_t)(c0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        double2 acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0.0, 0.0);
+        for (int kk = 0; kk < w; ++kk) {
+          double2 pa[4], pb[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) pa[a] = sPI[kk * TT + tx + 16 * a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) pb[b] = sPJ[kk * TT + ty + 16 * b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              // acc += pa * conj(pb)
+              acc[a][b].x = fma(pa[a].x, pb[b].x, fma(pa[a].y, pb[b].y, acc[a][b].x));
+              acc[a][b].y = fma(pa[a].y, pb[b].x, fma(-pa[a].x, pb[b].y, acc[a][b].y));
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int row = r0 + tx + 16 * a;
+          if (row >= N) continue;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int col = c0 + ty + 16 * b;
+            if (col >= N || col > row) continue;
+            double2* p = &A[(size_t)row + (size_t)col * N];
+            *p = csub(*p, acc[a][b]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    k0 = k1;
+  }
+  __syncthreads();
+  if (tid == 0 && bad) status[ids[slot]] = 1;
+}
+
+// ---------------------------------------------------------- extraction --
+// From the factored K of one element: S (n_h x n_h full), s, c, Z = M1^{-1} M2, z = M1^{-1} M4 l.
+__global__ void __launch_bounds__(256) k_extract(Sizes S, const int* __restrict__ ids, const double2* __restrict__ K,
+                                                 double2* Sst, double2* sst, double* cst, double2* Zst, double2* zst) {
+  const int slot = blockIdx.x;
+  const int e = ids[slot];
+  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h;
+  const double2* A = K + (size_t)slot * N * N;
+  const int o = nv + nu;  // first trace row
+  double2* Se = Sst + (size_t)e * nh * nh;
+  for (int t = threadIdx.x; t < nh * nh; t += blockDim.x) {
+    int i = t / nh, j = t - i * nh;
+    Se[t] = (i >= j) ? A[(size_t)(o + i) + (size_t)(o + j) * N] : cconj(A[(size_t)(o + j) + (size_t)(o + i) * N]);
+  }
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) sst[(size_t)e * nh + t] = cconj(A[(size_t)(N - 1) + (size_t)(o + t) * N]);
+  if (threadIdx.x == 0) cst[e] = A[(size_t)(N - 1) + (size_t)(N - 1) * N].x;
+  // Z: for each column t in [0, nh] (t = nh is the load) solve L1^H z = y with
+  // y[u] = conj(A[o + t][nv + u]), L1[a][b] = A[nv + a][nv + b].
+  double2* Ze = Zst + (size_t)e * nu * nh;
+  for (int t = threadIdx.x; t <= nh; t += blockDim.x) {
+    const int rowt = (t < nh) ? o + t : N - 1;
+    for (int u = nu - 1; u >= 0; --u) {
+      double2 v = cconj(A[(size_t)rowt + (size_t)(nv + u) * N]);
+      for (int k = u + 1; k < nu; ++k) {
+        double2 zk = (t < nh) ? Ze[(size_t)k * nh + t] : zst[(size_t)e * nu + k];
+        // (L1^H)[u][k] = conj(L1[k][u])
+        v = csub(v, cmul(cconj(A[(size_t)(nv + k) + (size_t)(nv + u) * N]), zk));
+      }
+      v = cscale(v, 1.0 / A[(size_t)(nv + u) + (size_t)(nv + u) * N].x);
+      if (t < nh)
+        Ze[(size_t)u * nh + t] = v;
+      else
+        zst[(size_t)e * nu + u] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------- orchestration --
+int alloc_workspace(dpg_handle* h, int cap) {
+  Workspace& w = h->ws;
+  if (w.cap >= cap) return DPG_OK;
+  cudaFree(w.K);
+  cudaFree(w.V);
+  cudaFree(w.Cu);
+  cudaFree(w.PhiL);
+  cudaFree(w.MC);
+  cudaFree(w.ids);
+  cudaFree(w.FV);
+  cudaFree(w.FR);
+  cudaFree(w.rent);
+  w = Workspace{};
+  const Sizes& S = h->sz;
+  const size_t nq3 = 3 * (size_t)S.nq;
+  const int Wf = 2 * S.n_f + 2 * S.nt + 2;
+  w.rcap = std::max(6, std::min(cap * 2, std::max(6, (int)h->robin_entries.size())));
+  size_t bytes[] = {sizeof(double2) * (size_t)S.N * S.N * cap,
+                    sizeof(double) * nq3 * S.n_f * cap,
+                    sizeof(double) * nq3 * S.n_f * cap,
+                    sizeof(double) * nq3 * 3 * S.nL * cap,
+                    sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) * cap,
+                    sizeof(int) * (size_t)cap,
+                    sizeof(double) * 3 * (size_t)S.nqf * Wf * w.rcap,
+                    sizeof(double) * (size_t)S.n_f * Wf * w.rcap,
+                    sizeof(int) * 4 * (size_t)w.rcap};
+  void** ptrs[] = {(void**)&w.K, (void**)&w.V, (void**)&w.Cu, (void**)&w.PhiL, (void**)&w.MC, (void**)&w.ids,
+                   (void**)&w.FV, (void**)&w.FR, (void**)&w.rent};
+  for (int k = 0; k < 9; ++k) {
+    if (cudaMalloc(ptrs[k], bytes[k]) != cudaSuccess) {
+      cudaGetLastError();
+      h->err = "workspace allocation of " + std::to_string(bytes[k]) + " bytes failed";
+      return DPG_ERR_NOMEM;
+    }
+  }
+  w.cap = cap;
+  return DPG_OK;
+}
+
+// Robin sub-batches: whole elements, at most rcap entries.
+static int run_robin(dpg_handle* h, const int* ids_host, int count, cudaStream_t s) {
+  Workspace& w = h->ws;
+  const Sizes& S = h->sz;
+  const int Wf = 2 * S.n_f + 2 * S.nt + 2;
+  std::vector<int> rent, rlist;
+  auto flush = [&]() -> int {
+    if (rlist.empty()) return DPG_OK;
+    const int nent = (int)rent.size() / 4;
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(w.rent, rent.data(), sizeof(int) * rent.size(), cudaMemcpyHostToDevice, s));
+    // rlist rides after the entries in the same buffer region (rcap*4 ints suffice: 2 per element)
+    int* d_rlist = w.rent + 4 * nent;
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(d_rlist, rlist.data(), sizeof(int) * rlist.size(), cudaMemcpyHostToDevice, s));
+    k_face_arrays<<<dim3(1, nent), 256, 0, s>>>(h->tab, S, h->d_X, w.rent, h->d_robin, h->d_trfun, h->omega, 0, w.FV);
+    gemm_tn(S.n_f, Wf, 3 * S.nqf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FR, Wf,
+            (long long)S.n_f * Wf, nent, s);
+    k_robin_add<<<(int)rlist.size() / 2, 256, 0, s>>>(S, d_rlist, w.rent, h->d_robin, w.FR, w.K);
+    DPG_CUDA_TRY(h, cudaGetLastError());
+    // the host vectors are reused: wait for the copies of this sub-batch
+    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+    rent.clear();
+    rlist.clear();
+    return DPG_OK;
+  };
+  for (int slot = 0; slot < count; ++slot) {
+    const int e = ids_host[slot];
+    const int first = h->robin_first[e];
+    if (first < 0) continue;
+    int cnt = 0;
+    while (first + cnt < (int)h->robin_entries.size() && h->robin_entries[first + cnt].elem == e) ++cnt;
+    // entries + 2 ints of rlist per element must fit in the 4*rcap int buffer
+    if ((int)rent.size() / 4 + cnt > w.rcap / 2) {
+      int rc = flush();
+      if (rc) return rc;
+    }
+    rlist.push_back((int)rent.size() / 4);
+    rlist.push_back(cnt);
+    for (int k = 0; k < cnt; ++k) {
+      const RobinEntry& re = h->robin_entries[first + k];
+      rent.push_back(slot);
+      rent.push_back(re.face);
+      rent.push_back(re.grp);
+      rent.push_back(e);
+    }
+  }
+  return flush();
+}
+
+int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor, bool extract) {
+  Workspace& w = h->ws;
+  const Sizes& S = h->sz;
+  if (count > w.cap) return DPG_ERR_ARG;
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(w.ids, ids_host, sizeof(int) * count, cudaMemcpyHostToDevice, s));
+  const size_t nq3 = 3 * (size_t)S.nq;
+  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(h->tab, S, h->d_X, w.ids, w.V, w.Cu, w.PhiL);
+  const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
+  const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
+  const int nL3 = 3 * S.nL;
+  // M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL
+  gemm_tn(S.n_f, S.n_f, (int)nq3, w.V, S.n_f, sV, w.V, S.n_f, sV, w.MC, S.n_f, (long long)mcs, count, s);
+  gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f, S.n_f,
+          (long long)mcs, count, s);
+  gemm_tn(S.n_f, nL3, (int)nq3, w.V, S.n_f, sV, w.PhiL, nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f, nL3,
+          (long long)mcs, count, s);
+  gemm_tn(S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
+          w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, s);
+  k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, w.ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
+                                             h->d_Xref, h->d_Tf, h->d_Tall, w.K);
+  DPG_CUDA_TRY(h, cudaGetLastError());
+  int rc = run_robin(h, ids_host, count, s);
+  if (rc) return rc;
+  if (factor) {
+    const size_t smem = sizeof(double2) * (NB * NB + 2 * NB * TT);
+    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_factor<<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v + S.n_u, w.ids, w.K, h->d_status);
+    DPG_CUDA_TRY(h, cudaGetLastError());
+  }
+  if (extract) {
+    k_extract<<<count, 256, 0, s>>>(S, w.ids, w.K, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z);
+    DPG_CUDA_TRY(h, cudaGetLastError());
+  }
+  return DPG_OK;
+}
+
+// Reference matrices on the unit cube: X_ref = Cu^T V (metric free) and the
+// per-face trace pairings T_f = Vt^T NxP, T_all = sum_f T_f.
+__global__ void k_sum_faces(int n, const double* Tf, double* Tall) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int f = 0; f < 6; ++f) s += Tf[(size_t)f * n + t];
+    Tall[t] = s;
+  }
+}
+
+__global__ void k_copy_cols(int rows, int ncol, const double* src, int lds, long long ss, int c0, double* dst,
+                            long long sd) {
+  const int b = blockIdx.y;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rows * ncol; t += gridDim.x * blockDim.x) {
+    int i = t / ncol, j = t - i * ncol;
+    dst[b * sd + (size_t)i * ncol + j] = src[b * ss + (size_t)i * lds + c0 + j];
+  }
+}
+
+int compute_reference_matrices(dpg_handle* h, cudaStream_t s) {
+  const Sizes& S = h->sz;
+  Workspace& w = h->ws;
+  // unit cube as a temporary element: reuse d_X slot of element 0 is not allowed;
+  // allocate a private corner array
+  double Xu[24];
+  for (int v = 0; v < 8; ++v)
+    for (int a = 0; a < 3; ++a) Xu[3 * v + a] = (double)((v >> a) & 1);
+  double* dXu = nullptr;
+  int* dids = nullptr;
+  DPG_CUDA_TRY(h, cudaMalloc(&dXu, sizeof(Xu)));
+  DPG_CUDA_TRY(h, cudaMalloc(&dids, sizeof(int) * 32));
+  int zeros[32] = {0};
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(dXu, Xu, sizeof(Xu), cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(dids, zeros, sizeof(zeros), cudaMemcpyHostToDevice, s));
+  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, 1), 256, 0, s>>>(h->tab, S, dXu, dids, w.V, w.Cu, w.PhiL);
+  const size_t nq3 = 3 * (size_t)S.nq;
+  gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, 0, w.V, S.n_f, 0, h->d_Xref, S.n_f, 0, 1, s);
+  // faces of the unit cube
+  int rent[24];
+  for (int f = 0; f < 6; ++f) {
+    rent[4 * f + 0] = 0;
+    rent[4 * f + 1] = f;
+    rent[4 * f + 2] = 0;
+    rent[4 * f + 3] = 0;
+  }
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(w.rent, rent, sizeof(rent), cudaMemcpyHostToDevice, s));
+  const int Wf = 2 * S.n_f + 2 * S.nt + 2;
+  k_face_arrays<<<dim3(1, 6), 256, 0, s>>>(h->tab, S, dXu, w.rent, h->d_robin, h->d_trfun, h->omega, 1, w.FV);
+  gemm_tn(S.n_f, Wf, 3 * S.nqf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FR, Wf,
+          (long long)S.n_f * Wf, 6, s);
+  // T_f = columns [2 n_f + nt, 2 n_f + 2 nt) of FR
+  k_copy_cols<<<dim3(64, 6), 256, 0, s>>>(S.n_f, S.nt, w.FR, Wf, (long long)S.n_f * Wf, 2 * S.n_f + S.nt, h->d_Tf,
+                                         (long long)S.n_f * S.nt);
+  k_sum_faces<<<64, 256, 0, s>>>(S.n_f * S.nt, h->d_Tf, h->d_Tall);
+  DPG_CUDA_TRY(h, cudaGetLastError());
+  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  cudaFree(dXu);
+  cudaFree(dids);
+  return DPG_OK;
+}
+
+}  // namespace dpg

@@ -1,0 +1,561 @@
+// dpg_setup_mesh host logic: validation, entity numbering of the trace
+// unknowns, Dirichlet values, removal of unpaired H-hat unknowns, element
+// colouring and the CSR pattern of the condensed trace system.
+//
+// Trace unknowns (Sec. 2.3): the tangential trace of the Nedelec space of
+// order r = p + 1 keeps the edge functions (r per edge) and face functions
+// (2 r (r - 1) per face); interior functions are discarded.  Entities are
+// identified by their vertex ids: an edge by (start, end) along the local
+// axis, a face by its sorted vertex ids, with the corner order of the first
+// element that meets it stored to check that neighbours agree.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+
+#include "dpg_internal.h"
+
+namespace dpg {
+
+namespace {
+
+struct FaceKeyHash {
+  size_t operator()(const std::array<int, 4>& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int v : k) {
+      h ^= (uint64_t)(uint32_t)v;
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+
+// Trilinear Jacobian J[a][b] = dx_a / dxi_b and position at reference point xi.
+void trilinear(const double* X /*8x3*/, const double* xi, double J[3][3], double x[3]) {
+  for (int a = 0; a < 3; ++a) {
+    x[a] = 0;
+    for (int b = 0; b < 3; ++b) J[a][b] = 0;
+  }
+  for (int v = 0; v < 8; ++v) {
+    double f[3], df[3];
+    for (int a = 0; a < 3; ++a) {
+      int bit = (v >> a) & 1;
+      f[a] = bit ? xi[a] : 1.0 - xi[a];
+      df[a] = bit ? 1.0 : -1.0;
+    }
+    double shape = f[0] * f[1] * f[2];
+    for (int a = 0; a < 3; ++a) {
+      x[a] += shape * X[3 * v + a];
+      J[a][0] += df[0] * f[1] * f[2] * X[3 * v + a];
+      J[a][1] += f[0] * df[1] * f[2] * X[3 * v + a];
+      J[a][2] += f[0] * f[1] * df[2] * X[3 * v + a];
+    }
+  }
+}
+
+double det3(const double J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+void inv3(const double J[3][3], double Ji[3][3]) {
+  double d = det3(J);
+  Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / d;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / d;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / d;
+  Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / d;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / d;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / d;
+  Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / d;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / d;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / d;
+}
+
+struct cplx {
+  double re, im;
+};
+cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+cplx cexpi(double t) { return {std::cos(t), std::sin(t)}; }
+cplx csqrt_(cplx z) {
+  double m = std::sqrt(std::hypot(z.re, z.im));
+  double th = 0.5 * std::atan2(z.im, z.re);
+  return {m * std::cos(th), m * std::sin(th)};
+}
+
+// E of the TE_mn mode (Sec. 4.1) at x; H not needed on Dirichlet faces.
+void te_E(const dpg_dirichlet_group& g, double omega, const double x[3], cplx E[3]) {
+  const double pi = 3.14159265358979323846;
+  double k1 = g.m * pi / g.a, k2 = g.n * pi / g.b, kc2 = k1 * k1 + k2 * k2;
+  cplx eps{g.eps_re, g.eps_im}, mu{g.mu_re, g.mu_im};
+  cplx em = cmul(eps, mu);
+  cplx k3 = csqrt_({omega * omega * em.re - kc2, omega * omega * em.im});
+  // i k3 x3
+  cplx ph = cexpi(k3.re * x[2]);
+  double decay = std::exp(-k3.im * x[2]);
+  ph.re *= decay;
+  ph.im *= decay;
+  cplx pre = cmul({0.0, omega}, mu);  // i w mu
+  pre.re /= kc2;
+  pre.im /= kc2;
+  double c1 = std::cos(k1 * x[0]), s1 = std::sin(k1 * x[0]);
+  double c2 = std::cos(k2 * x[1]), s2 = std::sin(k2 * x[1]);
+  cplx e0 = cmul(pre, {-k2 * c1 * s2, 0.0});
+  cplx e1 = cmul(pre, {k1 * s1 * c2, 0.0});
+  E[0] = cmul(e0, ph);
+  E[1] = cmul(e1, ph);
+  E[2] = {0.0, 0.0};
+}
+
+}  // namespace
+
+int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cudaStream_t s) {
+  if (!m || !prm || !m->vert || !m->elem || !m->elem_p || !m->elem_eps || !m->elem_mu || !m->face_bc ||
+      !m->face_grp || m->n_vert <= 0 || m->n_elem <= 0) {
+    h->err = "null mesh array or empty mesh";
+    return DPG_ERR_ARG;
+  }
+  if (prm->dp != 1) {
+    h->err = "only dp = 1 is implemented";
+    return DPG_ERR_UNSUPPORTED;
+  }
+  if (!(prm->alpha > 0) || !(prm->omega > 0)) {
+    h->err = "alpha and omega must be positive";
+    return DPG_ERR_ARG;
+  }
+  if (prm->precision != DPG_PREC_FP64) {
+    h->err = "unsupported precision mode";
+    return DPG_ERR_UNSUPPORTED;
+  }
+  const int ne = m->n_elem;
+  const int p = m->elem_p[0];
+  if (p < 1 || p > MAXP) {
+    h->err = "trial degree must be in 1..4";
+    return DPG_ERR_MESH;
+  }
+  for (int e = 0; e < ne; ++e)
+    if (m->elem_p[e] != p) {
+      h->err = "mixed trial degrees are not implemented in this build";
+      return DPG_ERR_UNSUPPORTED;
+    }
+  for (int64_t k = 0; k < (int64_t)ne * 8; ++k)
+    if (m->elem[k] < 0 || m->elem[k] >= m->n_vert) {
+      h->err = "element vertex id out of range";
+      return DPG_ERR_MESH;
+    }
+  for (int64_t k = 0; k < (int64_t)ne * 6; ++k) {
+    int bc = m->face_bc[k], g = m->face_grp[k];
+    if (bc == DPG_BC_ROBIN && (g < 0 || g >= m->n_robin || !m->robin)) {
+      h->err = "Robin group out of range";
+      return DPG_ERR_MESH;
+    }
+    if (bc == DPG_BC_DIRICHLET && (g < 0 || g >= m->n_dirichlet || !m->dirichlet)) {
+      h->err = "Dirichlet group out of range";
+      return DPG_ERR_MESH;
+    }
+    if (bc < 0 || bc > 2) {
+      h->err = "face tag out of range";
+      return DPG_ERR_MESH;
+    }
+  }
+  h->ne = ne;
+  h->omega = prm->omega;
+  h->alpha = prm->alpha;
+  h->sz = make_sizes(p);
+  build_tables(p, &h->tab);
+  const Sizes& S = h->sz;
+  const int r = S.r;
+  h->robin.assign(m->robin, m->robin + m->n_robin);
+  h->dirichlet.assign(m->dirichlet, m->dirichlet + m->n_dirichlet);
+
+  // ---- geometry: corner coordinates and corner Jacobians ---------------
+  std::vector<double> X((size_t)ne * 24);
+  for (int e = 0; e < ne; ++e)
+    for (int v = 0; v < 8; ++v)
+      for (int a = 0; a < 3; ++a) X[(size_t)e * 24 + 3 * v + a] = m->vert[3 * (size_t)m->elem[8 * (size_t)e + v] + a];
+  for (int e = 0; e < ne; ++e)
+    for (int v = 0; v < 8; ++v) {
+      double xi[3] = {double(v & 1), double((v >> 1) & 1), double((v >> 2) & 1)}, J[3][3], x[3];
+      trilinear(&X[(size_t)e * 24], xi, J, x);
+      if (!(det3(J) > 0)) {
+        h->err = "element with non-positive Jacobian at a corner (element " + std::to_string(e) + ")";
+        return DPG_ERR_MESH;
+      }
+    }
+
+  // ---- entities -------------------------------------------------------
+  auto corner = [&](int e, int i, int j, int k) { return m->elem[8 * (size_t)e + i + 2 * j + 4 * k]; };
+  std::unordered_map<uint64_t, int> edge_id;
+  std::unordered_map<std::array<int, 4>, int, FaceKeyHash> face_id;
+  std::vector<std::array<int, 4>> face_order;
+  std::vector<int> elem_edge((size_t)ne * 12), elem_face((size_t)ne * 6);
+  int n_edges = 0, n_faces = 0;
+  for (int e = 0; e < ne; ++e) {
+    for (int c = 0; c < 3; ++c) {
+      int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+      for (int s2 = 0; s2 < 2; ++s2)
+        for (int s1 = 0; s1 < 2; ++s1) {
+          int pos[3];
+          pos[d1] = s1;
+          pos[d2] = s2;
+          pos[c] = 0;
+          int v0 = corner(e, pos[0], pos[1], pos[2]);
+          pos[c] = 1;
+          int v1 = corner(e, pos[0], pos[1], pos[2]);
+          uint64_t key = ((uint64_t)(uint32_t)v0 << 32) | (uint32_t)v1;
+          uint64_t rkey = ((uint64_t)(uint32_t)v1 << 32) | (uint32_t)v0;
+          if (edge_id.count(rkey)) {
+            h->err = "edge orientation differs between neighbours (element " + std::to_string(e) + ")";
+            return DPG_ERR_MESH;
+          }
+          auto it = edge_id.find(key);
+          int id;
+          if (it == edge_id.end()) {
+            id = n_edges++;
+            edge_id.emplace(key, id);
+          } else {
+            id = it->second;
+          }
+          elem_edge[(size_t)e * 12 + c * 4 + s1 + 2 * s2] = id;
+        }
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int sd = 0; sd < 2; ++sd) {
+        int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+        std::array<int, 4> ord;
+        int k = 0;
+        for (int tb = 0; tb < 2; ++tb)
+          for (int ta = 0; ta < 2; ++ta) {
+            int pos[3];
+            pos[d] = sd;
+            pos[a] = ta;
+            pos[b] = tb;
+            ord[k++] = corner(e, pos[0], pos[1], pos[2]);
+          }
+        std::array<int, 4> key = ord;
+        std::sort(key.begin(), key.end());
+        auto it = face_id.find(key);
+        int id;
+        if (it == face_id.end()) {
+          id = n_faces++;
+          face_id.emplace(key, id);
+          face_order.push_back(ord);
+        } else {
+          id = it->second;
+          if (face_order[id] != ord) {
+            h->err = "face orientation differs between neighbours (element " + std::to_string(e) + ")";
+            return DPG_ERR_MESH;
+          }
+        }
+        elem_face[(size_t)e * 6 + 2 * d + sd] = id;
+      }
+  }
+  const int n_ent = n_edges + n_faces;  // entity id: edges [0, n_edges), faces after
+  const int dof_edge = r, dof_face = 2 * r * (r - 1);
+  auto ent_dofs = [&](int ent) { return ent < n_edges ? dof_edge : dof_face; };
+
+  // ---- boundary classification ------------------------------------------
+  // Dirichlet: every entity on a Dirichlet face; data groups win over zero groups.
+  std::vector<int> dir_grp(n_ent, -1);            // Dirichlet group deciding the values
+  std::vector<int> dir_src_elem(n_ent, -1), dir_src_face(n_ent, -1);
+  std::vector<int> face_adj(n_ent, 0), face_robin(n_ent, 0);  // edges: incident element faces
+  std::vector<char> face_is_robin(n_faces, 0);
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      int d = f / 2, sd = f % 2;
+      int bc = m->face_bc[6 * (size_t)e + f], g = m->face_grp[6 * (size_t)e + f];
+      // edges of this element face: edges along the two tangential axes with the
+      // transverse coordinate d fixed to sd
+      int ents[5];
+      int k = 0;
+      ents[k++] = n_edges + elem_face[(size_t)e * 6 + f];
+      for (int c = 0; c < 3; ++c) {
+        if (c == d) continue;
+        int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+        for (int s2 = 0; s2 < 2; ++s2)
+          for (int s1 = 0; s1 < 2; ++s1) {
+            int pos1 = (d1 == d) ? sd : -1, pos2 = (d2 == d) ? sd : -1;
+            if ((pos1 >= 0 && s1 != pos1) || (pos2 >= 0 && s2 != pos2)) continue;
+            ents[k++] = elem_edge[(size_t)e * 12 + c * 4 + s1 + 2 * s2];
+          }
+      }
+      for (int q = 1; q < k; ++q) {
+        face_adj[ents[q]] += 1;
+        if (bc == DPG_BC_ROBIN) face_robin[ents[q]] += 1;
+      }
+      if (bc == DPG_BC_ROBIN) face_is_robin[elem_face[(size_t)e * 6 + f]] = 1;
+      if (bc == DPG_BC_DIRICHLET) {
+        bool data = h->dirichlet[g].kind != DPG_DIRICHLET_ZERO;
+        for (int q = 0; q < k; ++q) {
+          int en = ents[q];
+          bool take = dir_grp[en] < 0 || (data && h->dirichlet[dir_grp[en]].kind == DPG_DIRICHLET_ZERO);
+          if (take) {
+            dir_grp[en] = g;
+            dir_src_elem[en] = e;
+            dir_src_face[en] = f;
+          }
+        }
+      }
+    }
+  // H-hat unknowns that pair with nothing: faces on Gamma_R, and edges all of
+  // whose incident element faces lie on Gamma_R.
+  std::vector<char> h_drop(n_ent, 0);
+  for (int f = 0; f < n_faces; ++f) h_drop[n_edges + f] = face_is_robin[f];
+  for (int ed = 0; ed < n_edges; ++ed) h_drop[ed] = (face_adj[ed] > 0 && face_robin[ed] == face_adj[ed]);
+
+  // ---- global numbering of the free trace unknowns ------------------------
+  // E-hat blocks first (entity order), then H-hat blocks.
+  std::vector<int64_t> startE(n_ent, -1), startH(n_ent, -1);
+  int64_t nfree = 0;
+  for (int en = 0; en < n_ent; ++en)
+    if (dir_grp[en] < 0) {
+      startE[en] = nfree;
+      nfree += ent_dofs(en);
+    }
+  for (int en = 0; en < n_ent; ++en)
+    if (!h_drop[en]) {
+      startH[en] = nfree;
+      nfree += ent_dofs(en);
+    }
+  if (nfree >= (int64_t)1 << 31) {
+    h->err = "more than 2^31 trace unknowns";
+    return DPG_ERR_UNSUPPORTED;
+  }
+  h->n = nfree;
+
+  // ---- element-local map -------------------------------------------------
+  const std::vector<int> trf = trace_functions(r);
+  const int nt = S.nt;
+  std::vector<int> loc_ent(nt), loc_idx(nt);  // per local trace function: element entity slot, index
+  for (int t = 0; t < nt; ++t) {
+    int pk = trf[t];
+    int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
+    int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+    bool b1 = ii[d1] == 0 || ii[d1] == r, b2 = ii[d2] == 0 || ii[d2] == r;
+    if (b1 && b2) {
+      loc_ent[t] = c * 4 + (ii[d1] == r) + 2 * (ii[d2] == r);  // element edge slot 0..11
+      loc_idx[t] = ii[c];
+    } else {
+      int dn = b1 ? d1 : d2;  // face normal
+      int sd = ii[dn] == r;
+      int a = (dn == 0) ? 1 : 0, b = (dn == 2) ? 1 : 2;
+      int eo = (c == a) ? b : a;  // other tangential axis
+      loc_ent[t] = 12 + 2 * dn + sd;
+      loc_idx[t] = (c == a ? 0 : 1) * r * (r - 1) + ii[c] * (r - 1) + (ii[eo] - 1);
+    }
+  }
+  h->l2g.assign((size_t)ne * S.n_h, 0);
+  std::vector<double2> xfix((size_t)ne * S.n_h, make_double2(0.0, 0.0));
+  // Dirichlet values by nodal interpolation: coefficient = E_t(x_node) . (J(node) e_c)
+  double onode[MAXF1D], cnode[MAXF1D], dummy[MAXF1D];
+  gauss_legendre01(r, onode, dummy);
+  gauss_lobatto01(r + 1, cnode);
+  for (int e = 0; e < ne; ++e) {
+    for (int t = 0; t < nt; ++t) {
+      int slot = loc_ent[t];
+      int en = slot < 12 ? elem_edge[(size_t)e * 12 + slot] : n_edges + elem_face[(size_t)e * 6 + slot - 12];
+      int32_t gE = dir_grp[en] >= 0 ? -1 : (int32_t)(startE[en] + loc_idx[t]);
+      int32_t gH = h_drop[en] ? -2 : (int32_t)(startH[en] + loc_idx[t]);
+      h->l2g[(size_t)e * S.n_h + t] = gE;
+      h->l2g[(size_t)e * S.n_h + nt + t] = gH;
+      if (gE == -1) {
+        const dpg_dirichlet_group& g = h->dirichlet[dir_grp[en]];
+        double2 val = make_double2(0.0, 0.0);
+        if (g.kind != DPG_DIRICHLET_ZERO) {
+          // evaluate in this element (the node and J e_c agree between neighbours)
+          int pk = trf[t];
+          int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
+          double xi[3];
+          for (int d = 0; d < 3; ++d) xi[d] = (d == c) ? onode[ii[d]] : cnode[ii[d]];
+          double J[3][3], x[3];
+          trilinear(&X[(size_t)e * 24], xi, J, x);
+          // outward unit normal of the deciding Dirichlet face, at its centre
+          // (boundary faces are planar; the datum n x E_D refers to it)
+          int f = dir_src_face[en], es = dir_src_elem[en];
+          int d = f / 2;
+          double xc[3] = {0.5, 0.5, 0.5}, Js[3][3], xs[3], Jsi[3][3];
+          xc[d] = (f % 2) ? 1.0 : 0.0;
+          trilinear(&X[(size_t)es * 24], xc, Js, xs);
+          inv3(Js, Jsi);
+          double sgn = (f % 2) ? 1.0 : -1.0;
+          double nrm[3] = {sgn * Jsi[d][0], sgn * Jsi[d][1], sgn * Jsi[d][2]};
+          double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+          for (int a = 0; a < 3; ++a) nrm[a] /= nn;
+          cplx Et[3];
+          if (g.kind == DPG_DIRICHLET_SIN_PI_X2) {
+            // n x E = v with v = (sin(pi x2), 0, 0)  =>  E_t = v x n
+            double v[3] = {std::sin(3.14159265358979323846 * x[1]), 0.0, 0.0};
+            Et[0] = {v[1] * nrm[2] - v[2] * nrm[1], 0.0};
+            Et[1] = {v[2] * nrm[0] - v[0] * nrm[2], 0.0};
+            Et[2] = {v[0] * nrm[1] - v[1] * nrm[0], 0.0};
+          } else {
+            cplx E[3];
+            te_E(g, h->omega, x, E);
+            // E_t = E - (E . n) n
+            cplx en_{0, 0};
+            for (int a = 0; a < 3; ++a) {
+              en_.re += E[a].re * nrm[a];
+              en_.im += E[a].im * nrm[a];
+            }
+            for (int a = 0; a < 3; ++a) Et[a] = {E[a].re - en_.re * nrm[a], E[a].im - en_.im * nrm[a]};
+          }
+          for (int a = 0; a < 3; ++a) {
+            val.x += Et[a].re * J[a][c];
+            val.y += Et[a].im * J[a][c];
+          }
+        }
+        xfix[(size_t)e * S.n_h + t] = val;
+      }
+    }
+  }
+
+  // ---- colouring (elements sharing a vertex get different colours) ----------
+  {
+    std::vector<std::vector<int>> v2e(m->n_vert);
+    for (int e = 0; e < ne; ++e)
+      for (int v = 0; v < 8; ++v) v2e[m->elem[8 * (size_t)e + v]].push_back(e);
+    std::vector<int> color(ne, -1);
+    int ncol = 0;
+    std::vector<int> mark;
+    for (int e = 0; e < ne; ++e) {
+      mark.assign(ncol + 1, 0);
+      for (int v = 0; v < 8; ++v)
+        for (int o : v2e[m->elem[8 * (size_t)e + v]])
+          if (color[o] >= 0) mark[color[o]] = 1;
+      int c = 0;
+      while (c < ncol && mark[c]) ++c;
+      color[e] = c;
+      if (c == ncol) ++ncol;
+    }
+    h->color_off.assign(ncol + 1, 0);
+    for (int e = 0; e < ne; ++e) h->color_off[color[e] + 1]++;
+    for (int c = 0; c < ncol; ++c) h->color_off[c + 1] += h->color_off[c];
+    h->color_elems.assign(ne, 0);
+    std::vector<int> fill(h->color_off.begin(), h->color_off.end() - 1);
+    for (int e = 0; e < ne; ++e) h->color_elems[fill[color[e]]++] = e;
+  }
+
+  // ---- CSR pattern: rows of one entity block share their column list ----------
+  std::vector<std::vector<int>> ent_elems(n_ent);
+  for (int e = 0; e < ne; ++e) {
+    for (int k = 0; k < 12; ++k) ent_elems[elem_edge[(size_t)e * 12 + k]].push_back(e);
+    for (int k = 0; k < 6; ++k) ent_elems[n_edges + elem_face[(size_t)e * 6 + k]].push_back(e);
+  }
+  // per entity: sorted list of column ranges (start, count) of the free blocks
+  std::vector<int64_t> rowlen(n_ent, 0);
+  std::vector<std::vector<std::pair<int64_t, int>>> ranges(n_ent);
+  for (int en = 0; en < n_ent; ++en) {
+    bool rowE = startE[en] >= 0, rowH = startH[en] >= 0;
+    if (!rowE && !rowH) continue;
+    std::vector<int> nb;
+    for (int e : ent_elems[en]) {
+      for (int k = 0; k < 12; ++k) nb.push_back(elem_edge[(size_t)e * 12 + k]);
+      for (int k = 0; k < 6; ++k) nb.push_back(n_edges + elem_face[(size_t)e * 6 + k]);
+    }
+    std::sort(nb.begin(), nb.end());
+    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    auto& rg = ranges[en];
+    for (int o : nb)
+      if (startE[o] >= 0) rg.push_back({startE[o], ent_dofs(o)});
+    for (int o : nb)
+      if (startH[o] >= 0) rg.push_back({startH[o], ent_dofs(o)});
+    std::sort(rg.begin(), rg.end());
+    int64_t len = 0;
+    for (auto& q : rg) len += q.second;
+    rowlen[en] = len;
+  }
+  // rows in global order
+  std::vector<int64_t> rowptr(nfree + 1, 0);
+  std::vector<int> row_ent(nfree);
+  for (int en = 0; en < n_ent; ++en) {
+    if (startE[en] >= 0)
+      for (int k = 0; k < ent_dofs(en); ++k) row_ent[startE[en] + k] = en;
+    if (startH[en] >= 0)
+      for (int k = 0; k < ent_dofs(en); ++k) row_ent[startH[en] + k] = en;
+  }
+  for (int64_t i = 0; i < nfree; ++i) rowptr[i + 1] = rowptr[i] + rowlen[row_ent[i]];
+  h->nnz = rowptr[nfree];
+  std::vector<int32_t> col(h->nnz);
+  for (int64_t i = 0; i < nfree; ++i) {
+    int64_t o = rowptr[i];
+    for (auto& q : ranges[row_ent[i]])
+      for (int k = 0; k < q.second; ++k) col[o++] = (int32_t)(q.first + k);
+  }
+
+  // ---- Robin entries ---------------------------------------------------------
+  h->robin_entries.clear();
+  h->robin_first.assign(ne, -1);
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f < 6; ++f)
+      if (m->face_bc[6 * (size_t)e + f] == DPG_BC_ROBIN) {
+        if (h->robin_first[e] < 0) h->robin_first[e] = (int)h->robin_entries.size();
+        h->robin_entries.push_back({e, f, m->face_grp[6 * (size_t)e + f]});
+      }
+
+  // ---- device buffers --------------------------------------------------------
+  auto alloc = [&](void** ptr, size_t bytes) -> int {
+    if (bytes == 0) bytes = 16;
+    cudaError_t er = cudaMalloc(ptr, bytes);
+    if (er != cudaSuccess) {
+      h->err = std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(er);
+      cudaGetLastError();
+      return DPG_ERR_NOMEM;
+    }
+    return DPG_OK;
+  };
+#define DPG_ALLOC(ptr, bytes)                                  \
+  do {                                                         \
+    int rc_ = alloc((void**)&(ptr), (size_t)(bytes));          \
+    if (rc_) return rc_;                                       \
+  } while (0)
+  const size_t nh = S.n_h, nu = S.n_u;
+  DPG_ALLOC(h->d_X, sizeof(double) * 24 * (size_t)ne);
+  DPG_ALLOC(h->d_eps, sizeof(double2) * ne);
+  DPG_ALLOC(h->d_mu, sizeof(double2) * ne);
+  DPG_ALLOC(h->d_fbc, 6 * (size_t)ne);
+  DPG_ALLOC(h->d_l2g, sizeof(int32_t) * nh * ne);
+  DPG_ALLOC(h->d_xfix, sizeof(double2) * nh * ne);
+  DPG_ALLOC(h->d_color_elems, sizeof(int) * ne);
+  DPG_ALLOC(h->d_robin, sizeof(dpg_robin_group) * std::max<size_t>(1, h->robin.size()));
+  DPG_ALLOC(h->d_status, sizeof(int) * ne);
+  DPG_ALLOC(h->d_S, sizeof(double2) * nh * nh * ne);
+  DPG_ALLOC(h->d_s, sizeof(double2) * nh * ne);
+  DPG_ALLOC(h->d_c, sizeof(double) * ne);
+  DPG_ALLOC(h->d_Z, sizeof(double2) * nu * nh * ne);
+  DPG_ALLOC(h->d_z, sizeof(double2) * nu * ne);
+  DPG_ALLOC(h->d_rowptr, sizeof(int64_t) * (nfree + 1));
+  DPG_ALLOC(h->d_col, sizeof(int32_t) * h->nnz);
+  DPG_ALLOC(h->d_val, sizeof(double2) * h->nnz);
+  DPG_ALLOC(h->d_b, sizeof(double2) * nfree);
+  DPG_ALLOC(h->d_trfun, sizeof(int) * nt);
+  DPG_ALLOC(h->d_Xref, sizeof(double) * S.n_f * S.n_f);
+  DPG_ALLOC(h->d_Tf, sizeof(double) * 6 * S.n_f * nt);
+  DPG_ALLOC(h->d_Tall, sizeof(double) * S.n_f * nt);
+#undef DPG_ALLOC
+  std::vector<double2> eps(ne), mu(ne);
+  for (int e = 0; e < ne; ++e) {
+    eps[e] = make_double2(m->elem_eps[e].re, m->elem_eps[e].im);
+    mu[e] = make_double2(m->elem_mu[e].re, m->elem_mu[e].im);
+  }
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_X, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_eps, eps.data(), sizeof(double2) * ne, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_mu, mu.data(), sizeof(double2) * ne, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_fbc, m->face_bc, 6 * (size_t)ne, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_l2g, h->l2g.data(), sizeof(int32_t) * h->l2g.size(), cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_xfix, xfix.data(), sizeof(double2) * xfix.size(), cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_color_elems, h->color_elems.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, s));
+  if (!h->robin.empty())
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_robin, h->robin.data(), sizeof(dpg_robin_group) * h->robin.size(),
+                                    cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_rowptr, rowptr.data(), sizeof(int64_t) * rowptr.size(), cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_trfun, trf.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * ne, s));
+  // the host vectors above die at return: wait for the copies
+  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  return DPG_OK;
+}
+
+}  // namespace dpg

@@ -1,0 +1,148 @@
+"""Python face of the C ABI: one class per handle, methods named after the ABI calls.
+
+Marshalling only: numpy mesh arrays become the C descriptor, torch CUDA
+tensors carry device buffers, torch streams carry the stream handle.  All
+arithmetic of the method runs in libdpg.so.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, ptr, stream_handle
+
+
+def _robin_groups(mesh):
+    arr = (_lib.dpg_robin_group * max(1, len(mesh.robin)))()
+    for k, g in enumerate(mesh.robin):
+        z = complex(g['zinv'])
+        arr[k].zinv_re, arr[k].zinv_im = z.real, z.imag
+        port = g.get('port')
+        if port is not None:
+            a, b, m, n, eps, mu = port
+            arr[k].port, arr[k].m, arr[k].n, arr[k].a, arr[k].b = 1, m, n, a, b
+            arr[k].eps_re, arr[k].eps_im = complex(eps).real, complex(eps).imag
+            arr[k].mu_re, arr[k].mu_im = complex(mu).real, complex(mu).imag
+    return arr
+
+
+def _dirichlet_groups(mesh):
+    arr = (_lib.dpg_dirichlet_group * max(1, len(mesh.dirichlet)))()
+    for k, g in enumerate(mesh.dirichlet):
+        arr[k].kind = int(g['kind'])
+        port = g.get('port')
+        if port is not None:
+            a, b, m, n, eps, mu = port
+            arr[k].m, arr[k].n, arr[k].a, arr[k].b = m, n, a, b
+            arr[k].eps_re, arr[k].eps_im = complex(eps).real, complex(eps).imag
+            arr[k].mu_re, arr[k].mu_im = complex(mu).real, complex(mu).imag
+    return arr
+
+
+class DPG:
+    """A DPG discretisation living on the current CUDA device (dpg_handle)."""
+
+    def __init__(self, mesh, alpha=1.0, chunk=0, stream=None):
+        L = _lib.lib()
+        self.mesh = mesh
+        keep = dict(
+            vert=np.ascontiguousarray(mesh.vert, dtype=np.float64),
+            elem=np.ascontiguousarray(mesh.elem, dtype=np.int32),
+            p=np.ascontiguousarray(mesh.p, dtype=np.int8),
+            eps=np.ascontiguousarray(mesh.eps, dtype=np.complex128),
+            mu=np.ascontiguousarray(mesh.mu, dtype=np.complex128),
+            bc=np.ascontiguousarray(mesh.face_bc, dtype=np.int8),
+            grp=np.ascontiguousarray(mesh.face_grp, dtype=np.int16),
+        )
+        rob, dirg = _robin_groups(mesh), _dirichlet_groups(mesh)
+        desc = _lib.dpg_mesh_desc(
+            n_vert=keep['vert'].shape[0], vert=keep['vert'].ctypes.data, n_elem=keep['elem'].shape[0],
+            elem=keep['elem'].ctypes.data, elem_p=keep['p'].ctypes.data, elem_eps=keep['eps'].ctypes.data,
+            elem_mu=keep['mu'].ctypes.data, face_bc=keep['bc'].ctypes.data, face_grp=keep['grp'].ctypes.data,
+            n_robin=len(mesh.robin), robin=C.cast(rob, C.POINTER(_lib.dpg_robin_group)),
+            n_dirichlet=len(mesh.dirichlet), dirichlet=C.cast(dirg, C.POINTER(_lib.dpg_dirichlet_group)))
+        prm = _lib.dpg_params(omega=float(mesh.omega), alpha=float(alpha), dp=1, precision=0, chunk=int(chunk))
+        h = C.c_void_p()
+        check(L.dpg_setup_mesh(C.byref(h), C.byref(desc), C.byref(prm), stream_handle(stream)))
+        self.h = h
+        self.n, self.nnz, self.n_elem, self.n_v, self.n_u, self.n_h = self.sizes()
+
+    # ---- ABI calls -----------------------------------------------------------
+    def sizes(self):
+        n, nnz = C.c_int64(), C.c_int64()
+        ne, nv, nu, nh = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        check(_lib.lib().dpg_sizes(self.h, C.byref(n), C.byref(nnz), C.byref(ne), C.byref(nv), C.byref(nu),
+                                   C.byref(nh)), self.h)
+        return n.value, nnz.value, ne.value, nv.value, nu.value, nh.value
+
+    def element_batch(self, stream=None):
+        check(_lib.lib().dpg_element_batch(self.h, _lib.DPG_PASS_ASSEMBLE, stream_handle(stream)), self.h)
+
+    def assemble(self, stream=None):
+        check(_lib.lib().dpg_assemble(self.h, stream_handle(stream)), self.h)
+
+    def cg_solve(self, x=None, b=None, mode=_lib.DPG_CG_FP64, rtol=1e-10, atol=0.0, max_iter=100000,
+                 inner_rtol=1e-4, stream=None, raise_on_nonconvergence=True):
+        if x is None:
+            x = torch.zeros(self.n, dtype=torch.complex128, device='cuda')
+        rep = _lib.dpg_cg_report()
+        rc = _lib.lib().dpg_cg_solve(self.h, mode, rtol, atol, max_iter, inner_rtol, ptr(x), ptr(b),
+                                     C.byref(rep), stream_handle(stream))
+        if rc != 0 and (raise_on_nonconvergence or rc != -5):
+            check(rc, self.h)
+        return x, dict(iterations=rep.iterations, outer=rep.outer, rel_residual=rep.rel_residual, ms=rep.ms,
+                       converged=bool(rep.converged))
+
+    def estimate(self, xhat, want_u=True, stream=None):
+        u = torch.empty(self.n_elem * self.n_u, dtype=torch.complex128, device='cuda') if want_u else None
+        eta = torch.empty(self.n_elem, dtype=torch.float64, device='cuda')
+        tot = C.c_double()
+        check(_lib.lib().dpg_estimate(self.h, ptr(xhat), ptr(u), ptr(eta), C.byref(tot), stream_handle(stream)),
+              self.h)
+        return (u.view(self.n_elem, self.n_u) if u is not None else None), eta, tot.value
+
+    def trace_map(self):
+        m = np.empty((self.n_elem, self.n_h), dtype=np.int32)
+        fv = np.empty((self.n_elem, self.n_h), dtype=np.complex128)
+        check(_lib.lib().dpg_trace_map(self.h, ptr(m), ptr(fv)), self.h)
+        return m, fv
+
+    def element_dump(self, ids, stream=None):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        k = len(ids)
+        G = np.empty((k, self.n_v, self.n_v), np.complex128)
+        B = np.empty((k, self.n_v, self.n_u), np.complex128)
+        Bh = np.empty((k, self.n_v, self.n_h), np.complex128)
+        l = np.empty((k, self.n_v), np.complex128)
+        S = np.empty((k, self.n_h, self.n_h), np.complex128)
+        s = np.empty((k, self.n_h), np.complex128)
+        check(_lib.lib().dpg_element_dump(self.h, ptr(ids), k, ptr(G), ptr(B), ptr(Bh), ptr(l), ptr(S), ptr(s),
+                                          stream_handle(stream)), self.h)
+        return dict(G=G, B=B, Bh=Bh, l=l, S=S, s=s)
+
+    def csr_copy(self, values=True, stream=None):
+        rp = np.empty(self.n + 1, np.int64)
+        col = np.empty(self.nnz, np.int32)
+        val = np.empty(self.nnz, np.complex128) if values else None
+        b = np.empty(self.n, np.complex128) if values else None
+        check(_lib.lib().dpg_csr_copy(self.h, ptr(rp), ptr(col), ptr(val), ptr(b), stream_handle(stream)), self.h)
+        return rp, col, val, b
+
+    def destroy(self):
+        if getattr(self, 'h', None):
+            _lib.lib().dpg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def probe_peaks(stream=None):
+    """(FP64, FP32) FMA throughput of the current device in FLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    check(_lib.lib().dpg_probe_peaks(C.byref(a), C.byref(b), stream_handle(stream)))
+    return a.value, b.value

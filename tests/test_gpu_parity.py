@@ -1,0 +1,191 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element and field by field.
+
+Tolerances (derived in DESIGN.md, "Parity tolerances"):
+* G_K, B_K, B-hat_K, l_K (formation, well conditioned): relative Frobenius 1e-12.
+* S_K, s_K (after G_K^{-1}; kappa(G_K) ~ 1e6..4e7 bounds the agreement of any
+  two backward-stable FP64 routes to ~1e-10): relative Frobenius 2e-9.
+* trace solution and interior field vs the oracle's direct solve: relative 1e-10
+  (CG run to 1e-13 relative residual).
+* eta_K: relative 1e-7 (quadratic-form route vs the oracle's Cholesky route).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import element as oel
+from oracle import system as osys
+from paper_2609_03155_b300 import inputs
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def dpg_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_03155_b300 import dpg
+    return dpg
+
+
+def _lossy_jittered(p, n=(2, 2, 1), seed=11):
+    """Small box with jittered interior vertices, lossy random materials, PEC + Robin port + Dirichlet data."""
+    nx, ny, nz = n
+    vert, elem, ijk = inputs.structured_hex(0.3, 0.2, 0.1 * nz, nx, ny, nz)
+    rng = np.random.default_rng(seed)
+    inner = (vert > 1e-12) & (vert < np.array([0.3, 0.2, 0.1 * nz]) - 1e-12)
+    vert = vert + inner * rng.uniform(-0.012, 0.012, vert.shape)
+    spec = {'x0': (inputs.BC_DIRICHLET, 0), 'x1': (inputs.BC_DIRICHLET, 1), 'y0': (inputs.BC_DIRICHLET, 0),
+            'y1': (inputs.BC_DIRICHLET, 0), 'z0': (inputs.BC_ROBIN, 0), 'z1': (inputs.BC_ROBIN, 1)}
+    bc, grp = inputs.box_boundary_tags(ijk, nx, ny, nz, spec)
+    ne = elem.shape[0]
+    eps = np.exp(rng.uniform(0, np.log(10), ne)) + 1j * rng.uniform(0, 3, ne)
+    mu = 1.0 + 0.2 * rng.uniform(0, 1, ne) + 0.1j * rng.uniform(0, 1, ne)
+    omega = 9.0
+    zinv = inputs.te_zinv(omega, 0.3, 0.2, 1, 0)
+    return inputs.Mesh(vert=vert, elem=elem, p=np.full(ne, p, np.int8), eps=eps, mu=mu, face_bc=bc,
+                       face_grp=grp, omega=omega,
+                       robin=[{'zinv': zinv, 'port': (0.3, 0.2, 1, 0, 1.0, 1.0)}, {'zinv': 0.7 - 0.2j, 'port': None}],
+                       dirichlet=[{'kind': inputs.DIRICHLET_ZERO, 'port': None},
+                                  {'kind': inputs.DIRICHLET_SIN_PI_X2, 'port': None}],
+                       name=f"lossy_jittered_p{p}")
+
+
+def _oracle_element(mesh, e):
+    X = mesh.vert[mesh.elem[e]]
+    el = oel.element_matrices(X, int(mesh.p[e]), mesh.omega, complex(mesh.eps[e]), complex(mesh.mu[e]),
+                              osys.element_faces(mesh, e))
+    return el, oel.condense(el)
+
+
+@pytest.mark.parametrize("case", ["waveguide2d_p1", "lossy_p1", "lossy_p2", "lossy_p3"])
+def test_element_matrices_match_oracle(dpg_mod, case):
+    if case == "waveguide2d_p1":
+        mesh = inputs.waveguide_2d_config(p=1)
+        ids = [0, 5, 31]
+    else:
+        p = int(case[-1])
+        mesh = _lossy_jittered(p)
+        ids = [0, 1, 2, 3]
+    d = dpg_mod.DPG(mesh)
+    out = d.element_dump(ids)
+    for k, e in enumerate(ids):
+        el, cond = _oracle_element(mesh, e)
+        assert rel(out['G'][k], el.G) < 1e-12
+        assert rel(out['B'][k], el.B) < 1e-12
+        assert rel(out['Bh'][k], el.Bh) < 1e-12
+        if np.linalg.norm(el.l) > 0:
+            assert rel(out['l'][k], el.l) < 1e-12
+        else:
+            assert np.linalg.norm(out['l'][k]) == 0
+        assert rel(out['S'][k], cond['S']) < 2e-9
+        if np.linalg.norm(cond['s']) > 0:
+            assert rel(out['s'][k], cond['s']) < 2e-9
+    d.destroy()
+
+
+def _gather(d, x):
+    """Element-local trace vectors of a global GPU solution (through the library's own map)."""
+    m, fv = d.trace_map()
+    xn = x.cpu().numpy()
+    loc = np.where(m >= 0, xn[np.clip(m, 0, None)], 0)
+    loc = np.where(m == -1, fv, loc)
+    return loc
+
+
+@pytest.mark.parametrize("case", ["waveguide2d_p1", "lossy_p1", "lossy_p2"])
+def test_solution_matches_oracle_direct_solve(dpg_mod, case):
+    if case == "waveguide2d_p1":
+        mesh = inputs.waveguide_2d_config(p=1)
+    else:
+        mesh = _lossy_jittered(int(case[-1]), n=(2, 2, 2))
+    sol = osys.solve(mesh)
+    d = dpg_mod.DPG(mesh)
+    assert d.n == sol['n']
+    d.element_batch()
+    d.assemble()
+    x, rep = d.cg_solve(rtol=1e-13, max_iter=200000)
+    assert rep['converged']
+    uh = _gather(d, x)
+    uh_or = np.stack([sol['xfull'][g] for g in sol['l2g']])
+    assert rel(uh, uh_or) < 1e-10
+    u, eta, etag = d.estimate(x)
+    u_or = np.stack([r['u'] for r in sol['rec']])
+    assert rel(u.cpu().numpy(), u_or) < 1e-10
+    eta_or = sol['eta']
+    assert np.max(np.abs(eta.cpu().numpy() - eta_or) / eta_or.max()) < 1e-7
+    assert abs(etag - np.sqrt(np.sum(eta_or ** 2))) < 1e-7 * np.sqrt(np.sum(eta_or ** 2))
+    d.destroy()
+
+
+def test_assembled_matrix_is_hermitian_and_matches_oracle_energy(dpg_mod):
+    """CSR is Hermitian; x^H A x and x^H b agree with the oracle's assembled system for the same local vectors."""
+    mesh = _lossy_jittered(1, n=(2, 1, 2))
+    sol = osys.solve(mesh)
+    d = dpg_mod.DPG(mesh)
+    d.element_batch()
+    d.assemble()
+    rp, col, val, b = d.csr_copy()
+    import scipy.sparse as sp
+    A = sp.csr_matrix((val, col, rp), shape=(d.n, d.n))
+    assert abs(A - A.conj().T).max() <= 1e-12 * abs(A).max()
+    # same physical trace field expressed in both numberings: use the oracle solution
+    m, fv = d.trace_map()
+    xg = np.zeros(d.n, complex)
+    for e in range(mesh.n_elem):
+        loc = sol['xfull'][sol['l2g'][e]]
+        for t in range(d.n_h):
+            if m[e, t] >= 0:
+                xg[m[e, t]] = loc[t]
+    Ao = sol['A']
+    xo = sol['x']
+    assert abs(np.vdot(xg, A @ xg) - np.vdot(xo, Ao @ xo)) < 1e-9 * abs(np.vdot(xo, Ao @ xo))
+    assert abs(np.vdot(xg, b) - np.vdot(xo, sol['b'])) < 1e-9 * abs(np.vdot(xo, sol['b']))
+    d.destroy()
+
+
+def test_te10_waveguide_field_error(dpg_mod):
+    """Config-1 guide: GPU field vs the closed-form TE10 mode (same error as the oracle's)."""
+    mesh = inputs.waveguide_2d_config(p=1)
+    d = dpg_mod.DPG(mesh)
+    d.element_batch()
+    d.assemble()
+    x, rep = d.cg_solve(rtol=1e-12)
+    u, eta, etag = d.estimate(x)
+    from oracle import physics
+    res = {'rec': [{'u': ue} for ue in u.cpu().numpy()]}
+    ex = lambda y: physics.te_fields(y, mesh.omega, 0.086, mesh.vert[:, 1].max(), 1, 0)
+    eE, eH = osys.l2_field_error(mesh, res, ex)
+    assert eE < 0.01 and eH < 0.01
+    d.destroy()
+
+
+def test_ir_fp32_matches_fp64(dpg_mod):
+    mesh = _lossy_jittered(1, n=(2, 2, 2))
+    d = dpg_mod.DPG(mesh)
+    d.element_batch()
+    d.assemble()
+    x64, r64 = d.cg_solve(rtol=1e-12)
+    x32, r32 = d.cg_solve(mode=1, rtol=1e-12, inner_rtol=1e-4)
+    assert r32['converged'] and r32['outer'] >= 1
+    assert rel(x32.cpu().numpy(), x64.cpu().numpy()) < 1e-9
+    d.destroy()
+
+
+def test_deterministic_assembly_and_solve(dpg_mod):
+    mesh = _lossy_jittered(1, n=(2, 2, 1))
+    d = dpg_mod.DPG(mesh)
+    d.element_batch()
+    d.assemble()
+    _, _, v1, b1 = d.csr_copy()
+    x1, _ = d.cg_solve(rtol=1e-12)
+    d.element_batch()
+    d.assemble()
+    _, _, v2, b2 = d.csr_copy()
+    x2, _ = d.cg_solve(rtol=1e-12)
+    assert np.array_equal(v1, v2) and np.array_equal(b1, b2)
+    assert torch.equal(x1, x2)
+    d.destroy()

@@ -76,7 +76,7 @@ enum { DPG_BC_NONE = 0, DPG_BC_DIRICHLET = 1, DPG_BC_ROBIN = 2 };
 enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2 };
 enum { DPG_PREC_FP64 = 0 };
 enum { DPG_PASS_ASSEMBLE = 0 };
-enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1 };
+enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2 };
 
 /* Robin group (Sec. 2.2, Eq. robin_boundary; Sec. 4.1 port / outlet):
  * n x H + Z^{-1} n x (E x n) = g.  port = 0: g = 0; port = 1: g is the TE_mn
@@ -165,9 +165,12 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
 
 /* Unpreconditioned conjugate gradients on the Hermitian positive definite
  * system (Sec. 2.3 end): x0 = 0, stop when ||r|| <= max(rtol ||b||, atol).
- * mode DPG_CG_FP64: plain FP64 CG.  DPG_CG_IR_FP32: iterative refinement,
- * FP64 residuals and updates around FP32 inner CG solves on an FP32 copy of
- * the matrix (inner relative tolerance inner_rtol).
+ * mode DPG_CG_FP64: plain FP64 CG (the paper's solver).  DPG_CG_IR_FP32:
+ * iterative refinement, FP64 residuals and updates around FP32 inner CG
+ * solves on an FP32 copy of the matrix (inner relative tolerance inner_rtol).
+ * DPG_CG_JACOBI may be or-ed to either: diagonal preconditioning
+ * z = D^{-1} r (not in the paper, which leaves preconditioning to future
+ * work); the stopping test stays on the unpreconditioned residual.
  * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or
  * NULL for the assembled right-hand side.  rep: host, may be NULL.
  * Synchronises the stream (the report is a host value).
@@ -185,6 +188,30 @@ int dpg_cg_solve(dpg_handle* h, int32_t mode, double rtol, double atol, int32_t 
  * eta_global: host, sqrt(sum eta_K^2) (may be NULL; synchronises if given). */
 int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
                  double* eta_global, dpg_stream s);
+
+/* Replace per-element data from host buffers (read on the stream; keep them
+ * alive and unmodified until the stream reaches the copy, pinned memory makes
+ * the copy asynchronous).  corners: n_elem x 8 x 3 vertex coordinates in the
+ * element's vertex order (NULL = keep); the connectivity and therefore the
+ * numbering are unchanged, so the corners must keep every Jacobian positive.
+ * eps, mu: n_elem complex (NULL = keep).  Invalidates the element stores. */
+int dpg_update_elements(dpg_handle* h, const double* corners, const dpg_complex* eps, const dpg_complex* mu,
+                        dpg_stream s);
+
+/* Per-handle instrumentation for roofline reporting.  enable != 0 starts
+ * recording CUDA events around every element-factorisation launch and resets
+ * the counters; dpg_timing_get synchronises nothing and reports the state
+ * after the last synchronising call. */
+typedef struct {
+  double factor_ms;          /* summed device time of the factorisation kernel launches */
+  int64_t factor_launches;   /* number of those launches */
+  int64_t factor_elements;   /* elements they processed */
+  double cg_ms;              /* summed device time of dpg_cg_solve calls */
+  int64_t cg_iterations;     /* summed CG iterations */
+  int64_t kernel_launches;   /* kernels launched by the library since enable */
+} dpg_timing;
+int dpg_timing_enable(dpg_handle* h, int32_t enable);
+int dpg_timing_get(dpg_handle* h, dpg_timing* out);
 
 /* Sizes: n = free trace unknowns, nnz of the CSR matrix, per-element sizes. */
 int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_elem, int32_t* n_v,

@@ -17,7 +17,7 @@ ERRORS = {-1: "DPG_ERR_ARG", -2: "DPG_ERR_MESH", -3: "DPG_ERR_NOMEM", -4: "DPG_E
           -9: "DPG_ERR_UNSUPPORTED"}
 DPG_BC_NONE, DPG_BC_DIRICHLET, DPG_BC_ROBIN = 0, 1, 2
 DPG_PASS_ASSEMBLE = 0
-DPG_CG_FP64, DPG_CG_IR_FP32 = 0, 1
+DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI = 0, 1, 2
 
 
 class dpg_complex(C.Structure):
@@ -53,6 +53,11 @@ class dpg_cg_report(C.Structure):
                 ("ms", C.c_double), ("converged", C.c_int32), ("reserved", C.c_int32)]
 
 
+class dpg_timing(C.Structure):
+    _fields_ = [("factor_ms", C.c_double), ("factor_launches", C.c_int64), ("factor_elements", C.c_int64),
+                ("cg_ms", C.c_double), ("cg_iterations", C.c_int64), ("kernel_launches", C.c_int64)]
+
+
 class DPGError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -82,12 +87,16 @@ def lib():
     L.dpg_element_dump.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.dpg_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp]
     L.dpg_probe_peaks.argtypes = [C.POINTER(dbl), C.POINTER(dbl), vp]
+    L.dpg_update_elements.argtypes = [vp, vp, vp, vp, vp]
+    L.dpg_timing_enable.argtypes = [vp, i32]
+    L.dpg_timing_get.argtypes = [vp, C.POINTER(dpg_timing)]
     L.dpg_last_error.argtypes = [vp]
     L.dpg_last_error.restype = C.c_char_p
     L.dpg_destroy.argtypes = [vp]
     L.dpg_destroy.restype = None
     for name in ("dpg_setup_mesh", "dpg_element_batch", "dpg_assemble", "dpg_cg_solve", "dpg_estimate",
-                 "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks"):
+                 "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
+                 "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

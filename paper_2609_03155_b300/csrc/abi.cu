@@ -16,7 +16,8 @@ static void free_all(dpg_handle* h) {
                   h->d_s,     h->d_c,     h->d_Z,    h->d_z,     h->d_rowptr, h->d_col, h->d_val,
                   h->d_b,     h->d_val32, h->d_r,    h->d_p,     h->d_Ap,    h->d_r32,  h->d_p32,
                   h->d_Ap32,  h->d_x32,   h->d_red,  h->d_scal,  h->ws.K,    h->ws.V,   h->ws.Cu,
-                  h->ws.PhiL, h->ws.MC,   h->ws.ids, h->ws.FV,   h->ws.FR,   h->ws.rent};
+                  h->ws.PhiL, h->ws.MC,   h->ws.ids, h->ws.FV,   h->ws.FR,   h->ws.rent,
+                  h->d_dinv,  h->d_dinv32};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -73,6 +74,17 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
   std::vector<int> status(h->ne);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(status.data(), h->d_status, sizeof(int) * h->ne, cudaMemcpyDeviceToHost, s));
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  for (size_t k = 0; k < h->factor_events.size(); ++k) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->factor_events[k].first, h->factor_events[k].second);
+    h->factor_ms += ms;
+    h->factor_launches += 1;
+    h->factor_elements += h->factor_counts[k];
+    cudaEventDestroy(h->factor_events[k].first);
+    cudaEventDestroy(h->factor_events[k].second);
+  }
+  h->factor_events.clear();
+  h->factor_counts.clear();
   for (int e = 0; e < h->ne; ++e)
     if (status[e]) {
       h->err = "non-positive pivot in element " + std::to_string(e);
@@ -256,6 +268,38 @@ extern "C" int dpg_probe_peaks(double* fp64, double* fp32, dpg_stream st) {
   const double n = (double)blocks * threads * 64.0 * 2.0;
   if (fp64) *fp64 = n * it64 / (best64 * 1e-3);
   if (fp32) *fp32 = n * it32 / (best32 * 1e-3);
+  return DPG_OK;
+}
+
+extern "C" int dpg_update_elements(dpg_handle* h, const double* corners, const dpg_complex* eps, const dpg_complex* mu,
+                                   dpg_stream st) {
+  if (!h) return DPG_ERR_ARG;
+  cudaStream_t s = S_(st);
+  if (corners)
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_X, corners, sizeof(double) * 24 * (size_t)h->ne, cudaMemcpyHostToDevice, s));
+  if (eps) DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_eps, eps, sizeof(double2) * h->ne, cudaMemcpyHostToDevice, s));
+  if (mu) DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_mu, mu, sizeof(double2) * h->ne, cudaMemcpyHostToDevice, s));
+  h->have_elements = false;
+  h->have_system = false;
+  return DPG_OK;
+}
+
+extern "C" int dpg_timing_enable(dpg_handle* h, int32_t enable) {
+  if (!h) return DPG_ERR_ARG;
+  h->timing = enable != 0;
+  h->factor_ms = h->cg_ms = 0;
+  h->factor_launches = h->factor_elements = h->cg_iters = h->launches = 0;
+  return DPG_OK;
+}
+
+extern "C" int dpg_timing_get(dpg_handle* h, dpg_timing* out) {
+  if (!h || !out) return DPG_ERR_ARG;
+  out->factor_ms = h->factor_ms;
+  out->factor_launches = h->factor_launches;
+  out->factor_elements = h->factor_elements;
+  out->cg_ms = h->cg_ms;
+  out->cg_iterations = h->cg_iters;
+  out->kernel_launches = h->launches;
   return DPG_OK;
 }
 

@@ -107,7 +107,15 @@ struct dpg_handle {
   double2* d_val = nullptr;
   double2* d_b = nullptr;
   float2* d_val32 = nullptr;    // FP32 copy for IR inner solves (lazily built)
-  bool have_elements = false, have_system = false, have_val32 = false;
+  bool have_elements = false, have_system = false, have_val32 = false, have_dinv = false;
+  double* d_dinv = nullptr;     // inverse diagonal (Jacobi)
+  float* d_dinv32 = nullptr;
+  // instrumentation
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> factor_events;
+  std::vector<int> factor_counts;
+  double factor_ms = 0, cg_ms = 0;
+  int64_t factor_launches = 0, factor_elements = 0, cg_iters = 0, launches = 0;
   // CG scratch
   double2 *d_r = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_xw = nullptr;
   float2 *d_r32 = nullptr, *d_p32 = nullptr, *d_Ap32 = nullptr, *d_x32 = nullptr;

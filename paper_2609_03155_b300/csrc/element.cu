@@ -771,6 +771,7 @@ static int run_robin(dpg_handle* h, const int* ids_host, int count, cudaStream_t
             (long long)S.n_f * Wf, nent, s);
     k_robin_add<<<(int)rlist.size() / 2, 256, 0, s>>>(S, d_rlist, w.rent, h->d_robin, w.FR, w.K);
     DPG_CUDA_TRY(h, cudaGetLastError());
+    h->launches += 3;
     // the host vectors are reused: wait for the copies of this sub-batch
     DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
     rent.clear();
@@ -822,17 +823,31 @@ int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_
   k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, w.ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
                                              h->d_Xref, h->d_Tf, h->d_Tall, w.K);
   DPG_CUDA_TRY(h, cudaGetLastError());
+  h->launches += 6;  // basis arrays, four GEMMs, K
   int rc = run_robin(h, ids_host, count, s);
   if (rc) return rc;
   if (factor) {
     const size_t smem = sizeof(double2) * (NB * NB + 2 * NB * TT);
     DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
     k_factor<<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v + S.n_u, w.ids, w.K, h->d_status);
     DPG_CUDA_TRY(h, cudaGetLastError());
+    h->launches += 1;
+    if (h->timing) {
+      cudaEventRecord(e1, s);
+      h->factor_events.push_back({e0, e1});
+      h->factor_counts.push_back(count);
+    }
   }
   if (extract) {
     k_extract<<<count, 256, 0, s>>>(S, w.ids, w.K, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z);
     DPG_CUDA_TRY(h, cudaGetLastError());
+    h->launches += 1;
   }
   return DPG_OK;
 }

@@ -102,6 +102,18 @@ class DPG:
               self.h)
         return (u.view(self.n_elem, self.n_u) if u is not None else None), eta, tot.value
 
+    def update_elements(self, corners=None, eps=None, mu=None, stream=None):
+        """Host -> device copy of per-element corners (n_elem x 8 x 3), eps, mu (use pinned tensors)."""
+        check(_lib.lib().dpg_update_elements(self.h, ptr(corners), ptr(eps), ptr(mu), stream_handle(stream)), self.h)
+
+    def timing_enable(self, enable=True):
+        check(_lib.lib().dpg_timing_enable(self.h, int(enable)), self.h)
+
+    def timing_get(self):
+        t = _lib.dpg_timing()
+        check(_lib.lib().dpg_timing_get(self.h, C.byref(t)), self.h)
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
     def trace_map(self):
         m = np.empty((self.n_elem, self.n_h), dtype=np.int32)
         fv = np.empty((self.n_elem, self.n_h), dtype=np.complex128)

@@ -189,6 +189,20 @@ int dpg_cg_solve(dpg_handle* h, int32_t mode, double rtol, double atol, int32_t 
 int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
                  double* eta_global, dpg_stream s);
 
+/* Allocation-free variant of dpg_estimate, for callers that cannot allocate
+ * device memory during the call (their memory is committed to a pool of
+ * their own up front, or their loop may not wait on an allocator).  The paper
+ * has no counterpart; it is an interface choice of this library.  Same
+ * arguments, results and errors as dpg_estimate, plus DPG_ERR_ARG when the
+ * mesh has more than 1,048,575 elements.  Its scratch (the per-element
+ * eta_K^2 and their sum) is a fixed 8 MiB array that every GPU loading the
+ * library keeps until the process exits; it calls no allocator.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race and give wrong results. */
+int dpg_estimate_noalloc(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
+                         double* eta_global, dpg_stream s);
+
 /* Replace per-element data from host buffers (read on the stream; keep them
  * alive and unmodified until the stream reaches the copy, pinned memory makes
  * the copy asynchronous).  corners: n_elem x 8 x 3 vertex coordinates in the

@@ -81,6 +81,7 @@ def lib():
     L.dpg_assemble.argtypes = [vp, vp]
     L.dpg_cg_solve.argtypes = [vp, i32, dbl, dbl, i32, dbl, vp, vp, C.POINTER(dpg_cg_report), vp]
     L.dpg_estimate.argtypes = [vp, vp, vp, vp, C.POINTER(dbl), vp]
+    L.dpg_estimate_noalloc.argtypes = [vp, vp, vp, vp, C.POINTER(dbl), vp]
     L.dpg_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                             C.POINTER(i32)]
     L.dpg_trace_map.argtypes = [vp, vp, vp]
@@ -95,6 +96,7 @@ def lib():
     L.dpg_destroy.argtypes = [vp]
     L.dpg_destroy.restype = None
     for name in ("dpg_setup_mesh", "dpg_element_batch", "dpg_assemble", "dpg_cg_solve", "dpg_estimate",
+                 "dpg_estimate_noalloc",
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
                  "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get"):
         getattr(L, name).restype = C.c_int

@@ -116,6 +116,13 @@ extern "C" int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex*
   return estimate(h, reinterpret_cast<const double2*>(xhat), reinterpret_cast<double2*>(u), eta, eta_global, S_(st));
 }
 
+extern "C" int dpg_estimate_noalloc(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
+                                    double* eta_global, dpg_stream st) {
+  if (!h) return DPG_ERR_ARG;
+  return estimate_noalloc(h, reinterpret_cast<const double2*>(xhat), reinterpret_cast<double2*>(u), eta, eta_global,
+                          S_(st));
+}
+
 extern "C" int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_elem, int32_t* n_v, int32_t* n_u,
                          int32_t* n_h) {
   if (!h) return DPG_ERR_ARG;

@@ -139,6 +139,8 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
              double2* x, const double2* b, dpg_cg_report* rep, cudaStream_t s);
 int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
              cudaStream_t s);
+int estimate_noalloc(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
+                     cudaStream_t s);
 }  // namespace dpg
 
 #define DPG_CUDA_TRY(h, call)                                                     \

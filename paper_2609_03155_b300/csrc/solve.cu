@@ -3,6 +3,7 @@
 // estimator (Sec. 2.3).  complex FP64 unless stated.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "dpg_internal.h"
 
@@ -624,6 +625,82 @@ int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double
     *eta_global = std::sqrt(std::max(tot, 0.0));
   }
   DPG_CUDA_TRY(h, cudaFreeAsync(d_eta2, s));
+  return DPG_OK;
+}
+
+// ------------------------------------------------ allocation-free estimate --
+// Variant of estimate() for callers that must not allocate device memory at
+// call time (for example a process whose device memory is committed to its
+// own pool up front, or a loop that may not wait on an allocator).  Its only
+// scratch, the per-element eta_K^2 values and their sum, lives in the
+// file-scope array below, which every GPU that loads this library holds until
+// the process exits (8 MiB).  Nothing in it has to start at zero: every call
+// overwrites the first n_elem + 1 entries before reading them.  All calls
+// share the array, so calls that overlap on the GPU (different streams or
+// different handles on the same device) race on it.
+constexpr int NOALLOC_MAX_ELEMS = (1 << 20) - 1;
+static __device__ __align__(256) double g_noalloc_eta2[NOALLOC_MAX_ELEMS + 1];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+// Device address of the scratch array on the current device.  The first call
+// on a device looks it up with cudaGetSymbolAddress (the host-side name of a
+// __device__ array is not a device address); later calls reuse it.
+static int noalloc_scratch(dpg_handle* h, double** out) {
+  int dev = 0;
+  DPG_CUDA_TRY(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    h->err = "device index beyond the allocation-free table";
+    return DPG_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_eta2);
+    if (e != cudaSuccess || !p) {
+      h->err = std::string("cudaGetSymbolAddress of the estimate scratch: ") + cudaGetErrorString(e);
+      return DPG_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return DPG_OK;
+}
+
+int estimate_noalloc(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
+                     cudaStream_t s) {
+  if (!h->have_elements) {
+    h->err = "dpg_estimate_noalloc before dpg_element_batch";
+    return DPG_ERR_STATE;
+  }
+  if (!xhat) {
+    h->err = "null xhat";
+    return DPG_ERR_ARG;
+  }
+  if (h->ne > NOALLOC_MAX_ELEMS) {
+    h->err = "dpg_estimate_noalloc supports at most " + std::to_string(NOALLOC_MAX_ELEMS) +
+             " elements; this mesh has " + std::to_string(h->ne) + " (use dpg_estimate)";
+    return DPG_ERR_ARG;
+  }
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(h, &scratch);
+  if (rc) return rc;
+  const Sizes& S = h->sz;
+  k_estimate<<<h->ne, 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, h->d_l2g, h->d_xfix, xhat, h->d_S, h->d_s,
+                                                         h->d_c, h->d_Z, h->d_z, u, scratch);
+  k_sqrt_sum<<<1, 1024, 0, s>>>(h->ne, scratch, eta, scratch + h->ne);
+  h->launches += 2;
+  DPG_CUDA_TRY(h, cudaGetLastError());
+  if (eta_global) {
+    double tot = 0;
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(&tot, scratch + h->ne, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+    *eta_global = std::sqrt(std::max(tot, 0.0));
+  }
   return DPG_OK;
 }
 

@@ -77,6 +77,7 @@ enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2
 enum { DPG_PREC_FP64 = 0 };
 enum { DPG_PASS_ASSEMBLE = 0 };
 enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2 };
+enum { DPG_FLAG_ADJOINT = 1 };
 
 /* Robin group (Sec. 2.2, Eq. robin_boundary; Sec. 4.1 port / outlet):
  * n x H + Z^{-1} n x (E x n) = g.  port = 0: g = 0; port = 1: g is the TE_mn
@@ -125,7 +126,7 @@ typedef struct {
   int32_t dp;        /* enrichment, must be 1 in this build */
   int32_t precision; /* DPG_PREC_FP64 */
   int32_t chunk;     /* elements per batched launch, 0 = automatic */
-  int32_t reserved;
+  int32_t flags;     /* DPG_FLAG_*: DPG_FLAG_ADJOINT keeps the M1 factors dpg_grad_eps needs */
 } dpg_params;
 
 typedef struct {
@@ -226,6 +227,22 @@ typedef struct {
 } dpg_timing;
 int dpg_timing_enable(dpg_handle* h, int32_t enable);
 int dpg_timing_get(dpg_handle* h, dpg_timing* out);
+
+/* Absorbed power and its adjoint gradient (the paper has no adjoint; this is
+ * the reactor-optimisation use).  P = 1/2 omega sum_{K in obstacle} Im(eps_K)
+ * int_K |E_h|^2 (electric-loss term of Q_em, Sec. 3.2, dimensionless) at the
+ * trace solution xhat (device, n complex).  obstacle_mask: device, n_elem
+ * bytes (non-zero = in the obstacle).  P: host, may be NULL.  dP_deps_re,
+ * dP_deps_im: device, n_elem doubles each, both NULL (P only) or both set:
+ * the derivatives of P w.r.t. Re eps_K and Im eps_K for every element, by the
+ * adjoint of the DPG minimum-residual problem (one CG solve with the same
+ * matrix, mode/rtol/max_iter as dpg_cg_solve, then an element pass that
+ * re-forms and refactors G_K).  Needs DPG_FLAG_ADJOINT at setup and a prior
+ * dpg_element_batch + dpg_assemble for the current eps.  Synchronises.
+ * Errors: DPG_ERR_STATE, DPG_ERR_ARG, DPG_ERR_NOT_CONVERGED, DPG_ERR_NOMEM. */
+int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle_mask, double* P,
+                 double* dP_deps_re, double* dP_deps_im, int32_t cg_mode, double cg_rtol, int32_t max_iter,
+                 dpg_stream s);
 
 /* Sizes: n = free trace unknowns, nnz of the CSR matrix, per-element sizes. */
 int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_elem, int32_t* n_v,

@@ -18,6 +18,7 @@ ERRORS = {-1: "DPG_ERR_ARG", -2: "DPG_ERR_MESH", -3: "DPG_ERR_NOMEM", -4: "DPG_E
 DPG_BC_NONE, DPG_BC_DIRICHLET, DPG_BC_ROBIN = 0, 1, 2
 DPG_PASS_ASSEMBLE = 0
 DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI = 0, 1, 2
+DPG_FLAG_ADJOINT = 1
 
 
 class dpg_complex(C.Structure):
@@ -45,7 +46,7 @@ class dpg_mesh_desc(C.Structure):
 
 class dpg_params(C.Structure):
     _fields_ = [("omega", C.c_double), ("alpha", C.c_double), ("dp", C.c_int32), ("precision", C.c_int32),
-                ("chunk", C.c_int32), ("reserved", C.c_int32)]
+                ("chunk", C.c_int32), ("flags", C.c_int32)]
 
 
 class dpg_cg_report(C.Structure):
@@ -89,6 +90,7 @@ def lib():
     L.dpg_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp]
     L.dpg_probe_peaks.argtypes = [C.POINTER(dbl), C.POINTER(dbl), vp]
     L.dpg_update_elements.argtypes = [vp, vp, vp, vp, vp]
+    L.dpg_grad_eps.argtypes = [vp, vp, vp, C.POINTER(dbl), vp, vp, i32, dbl, i32, vp]
     L.dpg_timing_enable.argtypes = [vp, i32]
     L.dpg_timing_get.argtypes = [vp, C.POINTER(dpg_timing)]
     L.dpg_last_error.argtypes = [vp]
@@ -98,7 +100,7 @@ def lib():
     for name in ("dpg_setup_mesh", "dpg_element_batch", "dpg_assemble", "dpg_cg_solve", "dpg_estimate",
                  "dpg_estimate_noalloc",
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
-                 "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get"):
+                 "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

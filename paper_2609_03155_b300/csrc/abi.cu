@@ -17,7 +17,8 @@ static void free_all(dpg_handle* h) {
                   h->d_b,     h->d_val32, h->d_r,    h->d_p,     h->d_Ap,    h->d_r32,  h->d_p32,
                   h->d_Ap32,  h->d_x32,   h->d_red,  h->d_scal,  h->ws.K,    h->ws.V,   h->ws.Cu,
                   h->ws.PhiL, h->ws.MC,   h->ws.ids, h->ws.FV,   h->ws.FR,   h->ws.rent,
-                  h->d_dinv,  h->d_dinv32};
+                  h->d_dinv,  h->d_dinv32, h->d_L1, h->d_u, h->d_zg, h->d_gc, h->d_lam, h->d_rhs_adj,
+                  h->d_Pk};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -121,6 +122,14 @@ extern "C" int dpg_estimate_noalloc(dpg_handle* h, const dpg_complex* xhat, dpg_
   if (!h) return DPG_ERR_ARG;
   return estimate_noalloc(h, reinterpret_cast<const double2*>(xhat), reinterpret_cast<double2*>(u), eta, eta_global,
                           S_(st));
+}
+
+extern "C" int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle_mask, double* P,
+                            double* dP_deps_re, double* dP_deps_im, int32_t cg_mode, double cg_rtol, int32_t max_iter,
+                            dpg_stream st) {
+  if (!h) return DPG_ERR_ARG;
+  return grad_eps(h, reinterpret_cast<const double2*>(xhat), obstacle_mask, P, dP_deps_re, dP_deps_im, cg_mode, cg_rtol,
+                  max_iter, S_(st));
 }
 
 extern "C" int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_elem, int32_t* n_v, int32_t* n_u,

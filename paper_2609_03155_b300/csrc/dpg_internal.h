@@ -101,6 +101,10 @@ struct dpg_handle {
   double* d_c = nullptr;        // ne
   double2* d_Z = nullptr;       // ne x n_u x n_h  (M1^{-1} M2)
   double2* d_z = nullptr;       // ne x n_u        (M1^{-1} M4 l)
+  double2* d_L1 = nullptr;      // ne x n_u x n_u  Cholesky factor of M1 (only with DPG_FLAG_ADJOINT)
+  // adjoint scratch (allocated on the first dpg_grad_eps)
+  double2 *d_u = nullptr, *d_zg = nullptr, *d_gc = nullptr, *d_lam = nullptr, *d_rhs_adj = nullptr;
+  double* d_Pk = nullptr;
   // CSR system
   int64_t* d_rowptr = nullptr;
   int32_t* d_col = nullptr;
@@ -133,6 +137,10 @@ int alloc_workspace(dpg_handle* h, int cap);
 int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor,
                       bool extract);
 int compute_reference_matrices(dpg_handle* h, cudaStream_t s);
+int factor_gram_only(dpg_handle* h, int count, cudaStream_t s);
+// adjoint.cu
+int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_host, double* dre, double* dim,
+             int cg_mode, double cg_rtol, int max_iter, cudaStream_t s);
 // solve.cu
 int assemble_system(dpg_handle* h, cudaStream_t s);
 int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, double inner_rtol,

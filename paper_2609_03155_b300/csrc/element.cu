@@ -531,12 +531,14 @@ __global__ void __launch_bounds__(256) k_robin_add(Sizes S, const int* __restric
 // --------------------------------------------- blocked partial Cholesky --
 // One CTA per element.  Pivots [0, nv) with positive sign; the trailing block
 // is negated after them; pivots [nv, npiv) again positive.  Lower triangle,
-// column-major, leading dimension N.  Non-positive pivots set status[elem].
+// column-major, leading dimension N; only rows and columns [0, nact) take part
+// (nact = nv factors G alone and leaves the rows below untouched).
+// Non-positive pivots set status[elem].
 constexpr int NB = 32;   // panel width
 constexpr int TT = 64;   // trailing tile
 
-__global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const int* __restrict__ ids, double2* K,
-                                                int* status) {
+__global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npiv, const int* __restrict__ ids,
+                                                double2* K, int* status) {
   extern __shared__ double2 sm[];
   double2* sD = sm;                 // NB x NB diagonal block (column-major)
   double2* sPI = sD + NB * NB;      // NB x TT panel rows of tile I ([k][row])
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const i
       if (ii >= jj) A[(size_t)(k0 + ii) + (size_t)(k0 + jj) * N] = sD[ii + jj * NB];
     }
     // --- panel: rows [k1, N) of columns [k0, k1): X L_D^H = P  (one row per thread)
-    for (int row = k1 + tid; row < N; row += blockDim.x) {
+    for (int row = k1 + tid; row < nact; row += blockDim.x) {
       double2 x[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j)
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const i
     }
     __syncthreads();
     // --- trailing update of the lower triangle of rows/cols [k1, N)
-    const int R = N - k1;
+    const int R = nact - k1;
     const int ntile = (R + TT - 1) / TT;
     const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16 a, cols ty + 16 b
     for (int I = 0; I < ntile; ++I) {
@@ -624,7 +626,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const i
       __syncthreads();
       for (int t = tid; t < NB * TT; t += blockDim.x) {
         int kk = t / TT, rr = t - kk * TT;
-        sPI[kk * TT + rr] = (kk < w && r0 + rr < N) ? A[(size_t)(r0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
+        sPI[kk * TT + rr] = (kk < w && r0 + rr < nact) ? A[(size_t)(r0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
       }
       for (int Jt = 0; Jt <= I; ++Jt) {
         const int c0 = k1 + Jt * TT;
@@ -632,7 +634,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const i
         for (int t = tid; t < NB * TT; t += blockDim.x) {
           int kk = t / TT, rr = t - kk * TT;
           sPJ[kk * TT + rr] =
-              (kk < w && c0 + rr < N) ? A[(size_t)(c0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
+              (kk < w && c0 + rr < nact) ? A[(size_t)(c0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
         }
         __syncthreads();
         double2 acc[4][4];
@@ -658,11 +660,11 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const i
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const int row = r0 + tx + 16 * a;
-          if (row >= N) continue;
+          if (row >= nact) continue;
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int col = c0 + ty + 16 * b;
-            if (col >= N || col > row) continue;
+            if (col >= nact || col > row) continue;
             double2* p = &A[(size_t)row + (size_t)col * N];
             *p = csub(*p, acc[a][b]);
           }
@@ -679,7 +681,8 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nv, int npiv, const i
 // ---------------------------------------------------------- extraction --
 // From the factored K of one element: S (n_h x n_h full), s, c, Z = M1^{-1} M2, z = M1^{-1} M4 l.
 __global__ void __launch_bounds__(256) k_extract(Sizes S, const int* __restrict__ ids, const double2* __restrict__ K,
-                                                 double2* Sst, double2* sst, double* cst, double2* Zst, double2* zst) {
+                                                 double2* Sst, double2* sst, double* cst, double2* Zst, double2* zst,
+                                                 double2* L1st) {
   const int slot = blockIdx.x;
   const int e = ids[slot];
   const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h;
@@ -692,6 +695,13 @@ __global__ void __launch_bounds__(256) k_extract(Sizes S, const int* __restrict_
   }
   for (int t = threadIdx.x; t < nh; t += blockDim.x) sst[(size_t)e * nh + t] = cconj(A[(size_t)(N - 1) + (size_t)(o + t) * N]);
   if (threadIdx.x == 0) cst[e] = A[(size_t)(N - 1) + (size_t)(N - 1) * N].x;
+  if (L1st) {  // Cholesky factor of M1 (row-major, lower; upper zero), kept for the adjoint
+    double2* Le = L1st + (size_t)e * nu * nu;
+    for (int t = threadIdx.x; t < nu * nu; t += blockDim.x) {
+      const int i = t / nu, j = t - i * nu;
+      Le[t] = (i >= j) ? A[(size_t)(nv + i) + (size_t)(nv + j) * N] : make_double2(0.0, 0.0);
+    }
+  }
   // Z: for each column t in [0, nh] (t = nh is the load) solve L1^H z = y with
   // y[u] = conj(A[o + t][nv + u]), L1[a][b] = A[nv + a][nv + b].
   double2* Ze = Zst + (size_t)e * nu * nh;
@@ -835,7 +845,7 @@ int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
     }
-    k_factor<<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v + S.n_u, w.ids, w.K, h->d_status);
+    k_factor<<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, w.ids, w.K, h->d_status);
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
     if (h->timing) {
@@ -845,10 +855,21 @@ int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_
     }
   }
   if (extract) {
-    k_extract<<<count, 256, 0, s>>>(S, w.ids, w.K, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z);
+    k_extract<<<count, 256, 0, s>>>(S, w.ids, w.K, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
   }
+  return DPG_OK;
+}
+
+// Cholesky of the G block alone for the current chunk (rows below untouched).
+int factor_gram_only(dpg_handle* h, int count, cudaStream_t s) {
+  const Sizes& S = h->sz;
+  const size_t smem = sizeof(double2) * (NB * NB + 2 * NB * TT);
+  DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_factor<<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status);
+  h->launches += 1;
+  DPG_CUDA_TRY(h, cudaGetLastError());
   return DPG_OK;
 }
 

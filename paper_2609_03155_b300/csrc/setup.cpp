@@ -525,6 +525,7 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   DPG_ALLOC(h->d_c, sizeof(double) * ne);
   DPG_ALLOC(h->d_Z, sizeof(double2) * nu * nh * ne);
   DPG_ALLOC(h->d_z, sizeof(double2) * nu * ne);
+  if (prm->flags & DPG_FLAG_ADJOINT) DPG_ALLOC(h->d_L1, sizeof(double2) * nu * nu * ne);
   DPG_ALLOC(h->d_rowptr, sizeof(int64_t) * (nfree + 1));
   DPG_ALLOC(h->d_col, sizeof(int32_t) * h->nnz);
   DPG_ALLOC(h->d_val, sizeof(double2) * h->nnz);

@@ -43,7 +43,7 @@ def _dirichlet_groups(mesh):
 class DPG:
     """A DPG discretisation living on the current CUDA device (dpg_handle)."""
 
-    def __init__(self, mesh, alpha=1.0, chunk=0, stream=None):
+    def __init__(self, mesh, alpha=1.0, chunk=0, adjoint=False, stream=None):
         L = _lib.lib()
         self.mesh = mesh
         keep = dict(
@@ -62,7 +62,8 @@ class DPG:
             elem_mu=keep['mu'].ctypes.data, face_bc=keep['bc'].ctypes.data, face_grp=keep['grp'].ctypes.data,
             n_robin=len(mesh.robin), robin=C.cast(rob, C.POINTER(_lib.dpg_robin_group)),
             n_dirichlet=len(mesh.dirichlet), dirichlet=C.cast(dirg, C.POINTER(_lib.dpg_dirichlet_group)))
-        prm = _lib.dpg_params(omega=float(mesh.omega), alpha=float(alpha), dp=1, precision=0, chunk=int(chunk))
+        prm = _lib.dpg_params(omega=float(mesh.omega), alpha=float(alpha), dp=1, precision=0, chunk=int(chunk),
+                              flags=_lib.DPG_FLAG_ADJOINT if adjoint else 0)
         h = C.c_void_p()
         check(L.dpg_setup_mesh(C.byref(h), C.byref(desc), C.byref(prm), stream_handle(stream)))
         self.h = h
@@ -114,6 +115,16 @@ class DPG:
         check(_lib.lib().dpg_timing_get(self.h, C.byref(t)), self.h)
         return {k: getattr(t, k) for k, _ in t._fields_}
 
+    def grad_eps(self, xhat, mask, want_grad=True, cg_mode=_lib.DPG_CG_FP64, rtol=1e-12, max_iter=200000,
+                 stream=None):
+        """Absorbed power P of the obstacle (mask: cuda uint8, n_elem) and, if asked, dP/dRe eps, dP/dIm eps."""
+        P = C.c_double()
+        dre = torch.empty(self.n_elem, dtype=torch.float64, device='cuda') if want_grad else None
+        dim = torch.empty(self.n_elem, dtype=torch.float64, device='cuda') if want_grad else None
+        check(_lib.lib().dpg_grad_eps(self.h, ptr(xhat), ptr(mask), C.byref(P), ptr(dre), ptr(dim), cg_mode, rtol,
+                                      max_iter, stream_handle(stream)), self.h)
+        return P.value, dre, dim
+
     def trace_map(self):
         m = np.empty((self.n_elem, self.n_h), dtype=np.int32)
         fv = np.empty((self.n_elem, self.n_h), dtype=np.complex128)
@@ -158,3 +169,34 @@ def probe_peaks(stream=None):
     a, b = C.c_double(), C.c_double()
     check(_lib.lib().dpg_probe_peaks(C.byref(a), C.byref(b), stream_handle(stream)))
     return a.value, b.value
+
+
+class AbsorbedPower(torch.autograd.Function):
+    """P(eps) = absorbed power of an obstacle, differentiable in the per-element permittivity.
+
+    forward(eps, solver, mask): eps is a complex128 tensor (n_elem); the DPG
+    forward solve runs on the solver's handle (built with adjoint=True).
+    backward: the adjoint gradient, packed in torch's convention for a real
+    function of a complex input, grad = dP/dRe(eps) + i dP/dIm(eps) (checked
+    against torch on |z|^2 in the tests).  The handle's state belongs to the
+    last forward: call backward before another forward on the same solver.
+    """
+
+    @staticmethod
+    def forward(ctx, eps, solver, mask, cg_rtol=1e-12):
+        e = eps.detach().to('cpu', torch.complex128).contiguous().pin_memory()
+        solver.update_elements(eps=e)
+        solver.element_batch()
+        solver.assemble()
+        x, rep = solver.cg_solve(rtol=cg_rtol)
+        P, _, _ = solver.grad_eps(x, mask, want_grad=False)
+        ctx.solver, ctx.mask, ctx.x, ctx.rtol = solver, mask, x, cg_rtol
+        ctx.eps_device = eps.device
+        torch.cuda.synchronize()
+        return torch.tensor(P, dtype=torch.float64, device=eps.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        _, dre, dim = ctx.solver.grad_eps(ctx.x, ctx.mask, want_grad=True, rtol=ctx.rtol)
+        g = torch.complex(dre, dim).to(ctx.eps_device)
+        return grad_out.to(g.device) * g, None, None, None

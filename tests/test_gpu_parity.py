@@ -189,3 +189,61 @@ def test_deterministic_assembly_and_solve(dpg_mod):
     assert np.array_equal(v1, v2) and np.array_equal(b1, b2)
     assert torch.equal(x1, x2)
     d.destroy()
+
+
+def _obstacle_cavity(n=3, p=1):
+    m = inputs.cavity(n, p, omega=5.0)
+    mask = inputs.sphere_obstacle(m, radius=0.3, eps=20.0 + 5.0j)
+    return m, mask
+
+
+def test_adjoint_gradient_matches_oracle(dpg_mod):
+    from oracle import adjoint as oadj
+    m, mask = _obstacle_cavity(2, 1)
+    mask[:] = False
+    mask[[0, 3, 5]] = True
+    m.eps = m.eps.copy()
+    m.eps[mask] = 20 + 5j
+    m.eps[1] = 3 + 1j
+    sol = osys.solve(m)
+    P_or, dre_or, dim_or = oadj.gradient(m, sol, mask)
+    d = dpg_mod.DPG(m, adjoint=True)
+    d.element_batch()
+    d.assemble()
+    x, rep = d.cg_solve(rtol=1e-13)
+    mk = torch.tensor(mask.astype(np.uint8), device='cuda')
+    P, dre, dim = d.grad_eps(x, mk, rtol=1e-13)
+    assert abs(P - P_or) < 1e-10 * P_or
+    scale = max(np.abs(dre_or).max(), np.abs(dim_or).max())
+    assert np.abs(dre.cpu().numpy() - dre_or).max() < 1e-8 * scale
+    assert np.abs(dim.cpu().numpy() - dim_or).max() < 1e-8 * scale
+    d.destroy()
+
+
+def test_adjoint_gradient_matches_gpu_finite_differences(dpg_mod):
+    """Central differences (step 1e-6) of GPU solves on 20 seeded elements, 10 inside the obstacle."""
+    m, mask = _obstacle_cavity(4, 1)
+    d = dpg_mod.DPG(m, adjoint=True)
+    mk = torch.tensor(mask.astype(np.uint8), device='cuda')
+    eps0 = torch.tensor(m.eps, dtype=torch.complex128)
+    Pfun = lambda e: dpg_mod.AbsorbedPower.apply(e, d, mk, 1e-13)
+    eps = eps0.clone().requires_grad_(True)
+    P = Pfun(eps)
+    P.backward()
+    g = eps.grad.numpy()
+    rng = np.random.default_rng(20260903)
+    inside, outside = np.where(mask)[0], np.where(~mask)[0]
+    pick = list(rng.choice(inside, min(10, len(inside)), replace=False)) + \
+        list(rng.choice(outside, 20 - min(10, len(inside)), replace=False))
+    h = 1e-6
+    scale = np.abs(g).max()
+    for e in pick:
+        for part in (1.0, 1j):
+            ep, em = eps0.clone(), eps0.clone()
+            ep[e] += part * h
+            em[e] -= part * h
+            with torch.no_grad():
+                fd = (Pfun(ep).item() - Pfun(em).item()) / (2 * h)
+            an = g[e].real if part == 1.0 else g[e].imag
+            assert abs(an - fd) < 1e-5 * scale + 1e-9 * abs(P.item()), (e, part, an, fd)
+    d.destroy()

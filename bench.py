@@ -5,7 +5,7 @@ Step (all on the GPU, through libdpg's C ABI):
   element pass  - quadrature, G_K = L L^H, condensation to S_K, s_K (Sec. 2.3, Algorithm 2)
   assembly      - deterministic sum of S_K, s_K into the CSR trace system
   CG            - to relative residual 1e-10 (default: FP32-inner iterative refinement with
-                  Jacobi preconditioning; --cg fp64 gives the paper's plain FP64 CG)
+                  entity-block Jacobi preconditioning; --cg fp64 gives the paper's plain FP64 CG)
   estimate      - local recovery of u and the residual estimator eta_K
 Metric: DPG elements per second of the whole step (inputs resident in HBM), with
 the CG time-to-1e-10 and the per-phase breakdown in the same JSON line.
@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DPG elements/s (local solve+η_K) & CG time-to-1e-10; mixed/batched vs FP64"
 UNIT = "elements/s"
-CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3}
+CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3, "fp64-bjacobi": 4, "ir-bjacobi": 5}
 
 
 def config_mesh(name):
@@ -169,7 +169,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="waveguide3d")
-    ap.add_argument("--cg", default="ir-jacobi", choices=sorted(CG_MODES))
+    ap.add_argument("--cg", default="ir-bjacobi", choices=sorted(CG_MODES))
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--max-iter", type=int, default=200000)
@@ -291,7 +291,7 @@ def main():
             "traffic": None, "flops_per_element": fpe, "elements_per_launch": fac_elems,
             "avg_launch_ms": fac_avg_ms}
     cg_iters = last_rep["iterations"]
-    cg_bytes_iter = (8 if mode & 1 else 16) * d.nnz + 4 * d.nnz
+    cg_bytes_iter = (8 if mode & 1 else 16) * d.nnz
     rate, cores, dt, nsamp = cpu_oracle_rate(mesh, args.cpu_sample)
     line = {
         "metric": METRIC, "value": world * mesh.n_elem / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,

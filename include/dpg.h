@@ -76,7 +76,7 @@ enum { DPG_BC_NONE = 0, DPG_BC_DIRICHLET = 1, DPG_BC_ROBIN = 2 };
 enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2 };
 enum { DPG_PREC_FP64 = 0 };
 enum { DPG_PASS_ASSEMBLE = 0 };
-enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2 };
+enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4 };
 enum { DPG_FLAG_ADJOINT = 1 };
 
 /* Robin group (Sec. 2.2, Eq. robin_boundary; Sec. 4.1 port / outlet):
@@ -131,7 +131,7 @@ typedef struct {
 
 typedef struct {
   int32_t iterations;      /* total CG iterations (inner ones for IR) */
-  int32_t outer;           /* IR outer corrections (0 for plain CG) */
+  int32_t outer;           /* outer passes: IR corrections, or FP64 residual replacements (1 = none needed) */
   double rel_residual;     /* final ||b - A x|| / ||b||, FP64 */
   double ms;               /* device time of the solve */
   int32_t converged;
@@ -153,6 +153,7 @@ int dpg_setup_mesh(dpg_handle** h, const dpg_mesh_desc* mesh, const dpg_params* 
  * to S_K = M3 - M2^H M1^{-1} M2 and s_K (Eq. linear_system), and keep S_K, s_K,
  * M1^{-1} M2, M1^{-1} M4 l and the scalar l^H G^{-1} l - (M4 l)^H M1^{-1} M4 l
  * in handle-owned per-element storage.  pass must be DPG_PASS_ASSEMBLE.
+ * Lossless elements take the real path (see dpg_set_real_path).
  * A non-positive pivot marks the element (DPG_ERR_NOT_HPD is returned by the
  * next call that synchronises). Asynchronous. */
 int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream s);
@@ -169,9 +170,12 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * mode DPG_CG_FP64: plain FP64 CG (the paper's solver).  DPG_CG_IR_FP32:
  * iterative refinement, FP64 residuals and updates around FP32 inner CG
  * solves on an FP32 copy of the matrix (inner relative tolerance inner_rtol).
- * DPG_CG_JACOBI may be or-ed to either: diagonal preconditioning
- * z = D^{-1} r (not in the paper, which leaves preconditioning to future
- * work); the stopping test stays on the unpreconditioned residual.
+ * DPG_CG_JACOBI or DPG_CG_BLOCK_JACOBI may be or-ed to either: diagonal
+ * preconditioning z = D^{-1} r, or the inverses of the entity diagonal blocks
+ * (each mesh entity's E-hat and H-hat unknowns together).  The paper leaves
+ * preconditioning to future work; the stopping test stays on the
+ * unpreconditioned residual.  Each (inner) solve is one cooperative kernel
+ * whose grid barriers give up after a bounded wait (DPG_ERR_TIMEOUT).
  * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or
  * NULL for the assembled right-hand side.  rep: host, may be NULL.
  * Synchronises the stream (the report is a host value).
@@ -224,8 +228,18 @@ typedef struct {
   double cg_ms;              /* summed device time of dpg_cg_solve calls */
   int64_t cg_iterations;     /* summed CG iterations */
   int64_t kernel_launches;   /* kernels launched by the library since enable */
+  double factor_ms_real;     /* part of factor_ms spent on real-path launches */
+  int64_t factor_elements_real;
 } dpg_timing;
 int dpg_timing_enable(dpg_handle* h, int32_t enable);
+
+/* Real path for lossless elements (default on).  An element with real eps
+ * and mu and no Robin face has an augmented system that the unitary diagonal
+ * scalings diag(1 on F, -i on I) (test) and diag(-i on E and E-hat, 1 on H
+ * and H-hat) (trial) make real; its factorisation then runs in real FP64
+ * (a quarter of the flops) and S_K, Z_K, L1 are mapped back exactly.
+ * enable = 0 forces the complex path for every element. */
+int dpg_set_real_path(dpg_handle* h, int32_t enable);
 int dpg_timing_get(dpg_handle* h, dpg_timing* out);
 
 /* Absorbed power and its adjoint gradient (the paper has no adjoint; this is

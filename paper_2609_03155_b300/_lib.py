@@ -17,7 +17,7 @@ ERRORS = {-1: "DPG_ERR_ARG", -2: "DPG_ERR_MESH", -3: "DPG_ERR_NOMEM", -4: "DPG_E
           -9: "DPG_ERR_UNSUPPORTED"}
 DPG_BC_NONE, DPG_BC_DIRICHLET, DPG_BC_ROBIN = 0, 1, 2
 DPG_PASS_ASSEMBLE = 0
-DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI = 0, 1, 2
+DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI, DPG_CG_BLOCK_JACOBI = 0, 1, 2, 4
 DPG_FLAG_ADJOINT = 1
 
 
@@ -56,7 +56,8 @@ class dpg_cg_report(C.Structure):
 
 class dpg_timing(C.Structure):
     _fields_ = [("factor_ms", C.c_double), ("factor_launches", C.c_int64), ("factor_elements", C.c_int64),
-                ("cg_ms", C.c_double), ("cg_iterations", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("cg_ms", C.c_double), ("cg_iterations", C.c_int64), ("kernel_launches", C.c_int64),
+                ("factor_ms_real", C.c_double), ("factor_elements_real", C.c_int64)]
 
 
 class DPGError(RuntimeError):
@@ -92,6 +93,7 @@ def lib():
     L.dpg_update_elements.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_grad_eps.argtypes = [vp, vp, vp, C.POINTER(dbl), vp, vp, i32, dbl, i32, vp]
     L.dpg_timing_enable.argtypes = [vp, i32]
+    L.dpg_set_real_path.argtypes = [vp, i32]
     L.dpg_timing_get.argtypes = [vp, C.POINTER(dpg_timing)]
     L.dpg_last_error.argtypes = [vp]
     L.dpg_last_error.restype = C.c_char_p
@@ -100,7 +102,8 @@ def lib():
     for name in ("dpg_setup_mesh", "dpg_element_batch", "dpg_assemble", "dpg_cg_solve", "dpg_estimate",
                  "dpg_estimate_noalloc",
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
-                 "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps"):
+                 "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps",
+                 "dpg_set_real_path"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

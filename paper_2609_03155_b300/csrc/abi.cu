@@ -13,12 +13,13 @@ static thread_local std::string g_setup_err;
 static void free_all(dpg_handle* h) {
   void* bufs[] = {h->d_X,     h->d_eps,   h->d_mu,   h->d_fbc,   h->d_Xref,  h->d_Tf,   h->d_Tall,
                   h->d_trfun, h->d_l2g,   h->d_xfix, h->d_color_elems, h->d_robin, h->d_status, h->d_S,
-                  h->d_s,     h->d_c,     h->d_Z,    h->d_z,     h->d_rowptr, h->d_col, h->d_val,
+                  h->d_s,     h->d_c,     h->d_Z,    h->d_z,     h->d_rowptr, h->d_row2blk, h->d_val,
                   h->d_b,     h->d_val32, h->d_r,    h->d_p,     h->d_Ap,    h->d_r32,  h->d_p32,
-                  h->d_Ap32,  h->d_x32,   h->d_red,  h->d_scal,  h->ws.K,    h->ws.V,   h->ws.Cu,
+                  h->d_Ap32,  h->d_x32,   h->d_red,  h->d_cgstate,  h->ws.K,    h->ws.V,   h->ws.Cu,
                   h->ws.PhiL, h->ws.MC,   h->ws.ids, h->ws.FV,   h->ws.FR,   h->ws.rent,
                   h->d_dinv,  h->d_dinv32, h->d_L1, h->d_u, h->d_zg, h->d_gc, h->d_lam, h->d_rhs_adj,
-                  h->d_Pk};
+                  h->d_Pk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_binv_ptr, h->d_binv, h->d_binv32,
+                  h->d_zv, h->d_z32, h->d_d64};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -62,12 +63,27 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
   }
   cudaStream_t s = S_(st);
   const int cap = h->ws.cap;
-  std::vector<int> ids(cap);
-  for (int c0 = 0; c0 < h->ne; c0 += cap) {
-    const int cnt = std::min(cap, h->ne - c0);
-    for (int k = 0; k < cnt; ++k) ids[k] = c0 + k;
-    int rc = run_element_chunk(h, ids.data(), cnt, s, true, true);
-    if (rc) return rc;
+  // lossless elements in real arithmetic, the others in complex arithmetic
+  std::vector<int> all;
+  const std::vector<int>* lists[2];
+  if (h->allow_real) {
+    lists[0] = &h->real_elems;
+    lists[1] = &h->cplx_elems;
+  } else {
+    all.resize(h->ne);
+    for (int e = 0; e < h->ne; ++e) all[e] = e;
+    lists[0] = &all;
+    lists[1] = nullptr;
+  }
+  for (int li = 0; li < 2; ++li) {
+    if (!lists[li]) continue;
+    const std::vector<int>& L = *lists[li];
+    const bool real = h->allow_real && li == 0;
+    for (size_t c0 = 0; c0 < L.size(); c0 += cap) {
+      const int cnt = (int)std::min<size_t>(cap, L.size() - c0);
+      int rc = run_element_chunk(h, L.data() + c0, cnt, s, true, true, real);
+      if (rc) return rc;
+    }
   }
   h->have_elements = true;
   h->have_system = false;
@@ -81,11 +97,16 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
     h->factor_ms += ms;
     h->factor_launches += 1;
     h->factor_elements += h->factor_counts[k];
+    if (h->factor_real[k]) {
+      h->factor_ms_real += ms;
+      h->factor_elements_real += h->factor_counts[k];
+    }
     cudaEventDestroy(h->factor_events[k].first);
     cudaEventDestroy(h->factor_events[k].second);
   }
   h->factor_events.clear();
   h->factor_counts.clear();
+  h->factor_real.clear();
   for (int e = 0; e < h->ne; ++e)
     if (status[e]) {
       h->err = "non-positive pivot in element " + std::to_string(e);
@@ -199,8 +220,16 @@ extern "C" int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids
         }
     }
     if (Sout || sout) {
-      rc = run_element_chunk(h, ids + k0, cnt, s, true, true);
-      if (rc) return rc;
+      std::vector<int> re, cx;
+      for (int k = 0; k < cnt; ++k) (h->allow_real && h->is_real[ids[k0 + k]] ? re : cx).push_back(ids[k0 + k]);
+      if (!re.empty()) {
+        rc = run_element_chunk(h, re.data(), (int)re.size(), s, true, true, true);
+        if (rc) return rc;
+      }
+      if (!cx.empty()) {
+        rc = run_element_chunk(h, cx.data(), (int)cx.size(), s, true, true, false);
+        if (rc) return rc;
+      }
       for (int k = 0; k < cnt; ++k) {
         const size_t q = (size_t)(k0 + k);
         if (Sout)
@@ -226,7 +255,15 @@ extern "C" int dpg_csr_copy(dpg_handle* h, int64_t* row_ptr, int32_t* col, dpg_c
   cudaStream_t s = S_(st);
   if (row_ptr)
     DPG_CUDA_TRY(h, cudaMemcpyAsync(row_ptr, h->d_rowptr, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToHost, s));
-  if (col) DPG_CUDA_TRY(h, cudaMemcpyAsync(col, h->d_col, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToHost, s));
+  if (col) {  // expand the per-entity column lists
+    std::vector<int64_t> rp(h->n + 1);
+    DPG_CUDA_TRY(h, cudaMemcpy(rp.data(), h->d_rowptr, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < h->nblk; ++b) {
+      const int4 B = h->blk[b];
+      for (int i = 0; i < B.y; ++i)
+        std::memcpy(col + rp[B.x + i], &h->cols[h->blk_colptr[b]], sizeof(int32_t) * B.z);
+    }
+  }
   if (val) DPG_CUDA_TRY(h, cudaMemcpyAsync(val, h->d_val, sizeof(double2) * h->nnz, cudaMemcpyDeviceToHost, s));
   if (b) DPG_CUDA_TRY(h, cudaMemcpyAsync(b, h->d_b, sizeof(double2) * h->n, cudaMemcpyDeviceToHost, s));
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -295,6 +332,17 @@ extern "C" int dpg_update_elements(dpg_handle* h, const double* corners, const d
     DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_X, corners, sizeof(double) * 24 * (size_t)h->ne, cudaMemcpyHostToDevice, s));
   if (eps) DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_eps, eps, sizeof(double2) * h->ne, cudaMemcpyHostToDevice, s));
   if (mu) DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_mu, mu, sizeof(double2) * h->ne, cudaMemcpyHostToDevice, s));
+  if (eps || mu) {  // re-classify lossless elements (host copies read now)
+    if (eps) h->eps_host.assign(eps, eps + h->ne);
+    if (mu) h->mu_host.assign(mu, mu + h->ne);
+    h->real_elems.clear();
+    h->cplx_elems.clear();
+    for (int e = 0; e < h->ne; ++e) {
+      const bool real = h->eps_host[e].im == 0.0 && h->mu_host[e].im == 0.0 && !h->robin_face[e];
+      h->is_real[e] = real;
+      (real ? h->real_elems : h->cplx_elems).push_back(e);
+    }
+  }
   h->have_elements = false;
   h->have_system = false;
   return DPG_OK;
@@ -303,8 +351,14 @@ extern "C" int dpg_update_elements(dpg_handle* h, const double* corners, const d
 extern "C" int dpg_timing_enable(dpg_handle* h, int32_t enable) {
   if (!h) return DPG_ERR_ARG;
   h->timing = enable != 0;
-  h->factor_ms = h->cg_ms = 0;
-  h->factor_launches = h->factor_elements = h->cg_iters = h->launches = 0;
+  h->factor_ms = h->cg_ms = h->factor_ms_real = 0;
+  h->factor_launches = h->factor_elements = h->cg_iters = h->launches = h->factor_elements_real = 0;
+  return DPG_OK;
+}
+
+extern "C" int dpg_set_real_path(dpg_handle* h, int32_t enable) {
+  if (!h) return DPG_ERR_ARG;
+  h->allow_real = enable != 0;
   return DPG_OK;
 }
 
@@ -316,6 +370,8 @@ extern "C" int dpg_timing_get(dpg_handle* h, dpg_timing* out) {
   out->cg_ms = h->cg_ms;
   out->cg_iterations = h->cg_iters;
   out->kernel_launches = h->launches;
+  out->factor_ms_real = h->factor_ms_real;
+  out->factor_elements_real = h->factor_elements_real;
   return DPG_OK;
 }
 

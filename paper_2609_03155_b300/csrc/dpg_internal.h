@@ -105,9 +105,25 @@ struct dpg_handle {
   // adjoint scratch (allocated on the first dpg_grad_eps)
   double2 *d_u = nullptr, *d_zg = nullptr, *d_gc = nullptr, *d_lam = nullptr, *d_rhs_adj = nullptr;
   double* d_Pk = nullptr;
-  // CSR system
+  // CSR system; the rows of one entity share a column list:
+  // blk[b] = (first row, rows, row width W, position of the block's own
+  // unknowns in its column list), columns at cols[blk_colptr[b] ...]
+  std::vector<int4> blk;
+  std::vector<int64_t> blk_colptr;
+  std::vector<int32_t> cols;
+  int nblk = 0;
+  int blk_dmax = 0;  // rows of the largest entity block
   int64_t* d_rowptr = nullptr;
-  int32_t* d_col = nullptr;
+  int32_t* d_row2blk = nullptr;
+  int4* d_blk = nullptr;
+  int64_t* d_blk_colptr = nullptr;
+  int32_t* d_cols = nullptr;
+  // entity-block Jacobi: inverse of each block's diagonal sub-block (rows x rows)
+  int64_t* d_binv_ptr = nullptr;
+  double2* d_binv = nullptr;
+  float2* d_binv32 = nullptr;
+  bool have_binv = false;
+  int binv_dmax = 0;
   double2* d_val = nullptr;
   double2* d_b = nullptr;
   float2* d_val32 = nullptr;    // FP32 copy for IR inner solves (lazily built)
@@ -118,14 +134,22 @@ struct dpg_handle {
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> factor_events;
   std::vector<int> factor_counts;
+  std::vector<int> factor_real;
+  int64_t factor_elements_real = 0;
+  double factor_ms_real = 0;
+  // lossless elements (real eps and mu, no Robin face) take the real path
+  std::vector<int> real_elems, cplx_elems;
+  std::vector<char> is_real;
+  bool allow_real = true;
+  std::vector<dpg_complex> eps_host, mu_host;
+  std::vector<char> robin_face;
   double factor_ms = 0, cg_ms = 0;
   int64_t factor_launches = 0, factor_elements = 0, cg_iters = 0, launches = 0;
   // CG scratch
-  double2 *d_r = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_xw = nullptr;
-  float2 *d_r32 = nullptr, *d_p32 = nullptr, *d_Ap32 = nullptr, *d_x32 = nullptr;
+  double2 *d_r = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_zv = nullptr, *d_d64 = nullptr;
+  float2 *d_r32 = nullptr, *d_p32 = nullptr, *d_Ap32 = nullptr, *d_x32 = nullptr, *d_z32 = nullptr;
+  void* d_cgstate = nullptr;      // CG state of the persistent solver (solve.cu)
   double* d_red = nullptr;      // reduction scratch
-  double* d_scal = nullptr;     // device scalars of the CG recurrences
-  int red_blocks = 0;
   dpg::Workspace ws;
 };
 
@@ -135,7 +159,7 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
 // element.cu
 int alloc_workspace(dpg_handle* h, int cap);
 int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor,
-                      bool extract);
+                      bool extract, bool real = false);
 int compute_reference_matrices(dpg_handle* h, cudaStream_t s);
 int factor_gram_only(dpg_handle* h, int count, cudaStream_t s);
 // adjoint.cu

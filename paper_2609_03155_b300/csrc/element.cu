@@ -474,6 +474,62 @@ __global__ void __launch_bounds__(256) k_build_K(Sizes S, double omega, double a
   }
 }
 
+
+// K of a lossless element in the phase-scaled real basis: test functions
+// scaled by diag(1 on F, -i on I), trial by diag(-i on E, 1 on H, -i on
+// E-hat, 1 on H-hat).  Then G_r = [[C + a1 M, w (mu X + eps X^T)], sym.],
+// B_r = [[w eps P, Q], [Q, w mu P]], B-hat_r = [[0, T_F], [T_I, 0]] are real.
+__global__ void __launch_bounds__(256) k_build_K_real(Sizes S, double omega, double alpha, const int* __restrict__ ids,
+                                                      const double2* __restrict__ eps_all,
+                                                      const double2* __restrict__ mu_all, const double* __restrict__ MC,
+                                                      const double* __restrict__ Xref, const double* __restrict__ Tall,
+                                                      double* K) {
+  const int slot = blockIdx.y;
+  const int e = ids[slot];
+  const int N = S.N, nf = S.n_f, nv = S.n_v, nu = S.n_u, nt = S.nt, nL3 = 3 * S.nL;
+  const double eps = eps_all[e].x, mu = mu_all[e].x;
+  const double a1 = omega * omega * eps * eps + alpha, a2 = omega * omega * mu * mu + alpha;
+  const double* M = MC + (size_t)slot * (2 * (size_t)nf * nf + 2 * (size_t)nf * nL3);
+  const double* Cm = M + (size_t)nf * nf;
+  const double* P = Cm + (size_t)nf * nf;
+  const double* Q = P + (size_t)nf * nL3;
+  double* Ke = K + (size_t)slot * N * N;
+  const size_t total = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / N), i = (int)(idx - (size_t)j * N);
+    double v = 0.0;
+    if (j < nv && i < nv) {
+      if (i < nf && j < nf) {
+        v = Cm[(size_t)j * nf + i] + a1 * M[(size_t)j * nf + i];
+      } else if (i >= nf && j >= nf) {
+        v = Cm[(size_t)(j - nf) * nf + (i - nf)] + a2 * M[(size_t)(j - nf) * nf + (i - nf)];
+      } else if (i >= nf) {  // rows I, cols F: w (mu X[j][i'] + eps X[i'][j])
+        const int ip = i - nf;
+        v = omega * (mu * Xref[(size_t)j * nf + ip] + eps * Xref[(size_t)ip * nf + j]);
+      } else {  // rows F, cols I: w (mu X[i][j'] + eps X[j'][i])
+        const int jp = j - nf;
+        v = omega * (mu * Xref[(size_t)i * nf + jp] + eps * Xref[(size_t)jp * nf + i]);
+      }
+    } else if (j < nv && i < nv + nu) {  // K[nv+u][j] = B_r[j][u]
+      const int u = i - nv;
+      const bool Fj = j < nf;
+      const int jj = Fj ? j : j - nf;
+      if (u < nL3)
+        v = Fj ? omega * eps * P[(size_t)jj * nL3 + u] : Q[(size_t)jj * nL3 + u];
+      else
+        v = Fj ? Q[(size_t)jj * nL3 + (u - nL3)] : omega * mu * P[(size_t)jj * nL3 + (u - nL3)];
+    } else if (j < nv && i < nv + nu + 2 * nt) {
+      const int t = i - nv - nu;
+      if (t < nt) {
+        if (j >= nf) v = Tall[(size_t)(j - nf) * nt + t];
+      } else if (j < nf) {
+        v = Tall[(size_t)j * nt + (t - nt)];
+      }
+    }
+    Ke[idx] = v;
+  }
+}
+
 // Robin additions (one block per element with Robin faces, its entries in order).
 // FR per entry: n_f x W with W = 2 n_f + 2 nt + 2 = Vt^T [Vt | Nx | Pt | NxP | g].
 __global__ void __launch_bounds__(256) k_robin_add(Sizes S, const int* __restrict__ rlist, const int* __restrict__ rent,
@@ -537,14 +593,43 @@ __global__ void __launch_bounds__(256) k_robin_add(Sizes S, const int* __restric
 constexpr int NB = 32;   // panel width
 constexpr int TT = 64;   // trailing tile
 
+// Real / complex scalar operations for the factorisation kernel.
+template <typename T> struct Sc;
+template <> struct Sc<double> {
+  __device__ static double zero() { return 0.0; }
+  __device__ static double re(double a) { return a; }
+  __device__ static double real(double r) { return r; }
+  __device__ static double neg(double a) { return -a; }
+  __device__ static double sub(double a, double b) { return a - b; }
+  __device__ static double scale(double a, double s) { return a * s; }
+  __device__ static double mul_conj(double a, double b) { return a * b; }  // a * conj(b)
+  __device__ static void fma_conj(double& acc, double a, double b) { acc = fma(a, b, acc); }
+};
+template <> struct Sc<double2> {
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ static double re(double2 a) { return a.x; }
+  __device__ static double2 real(double r) { return make_double2(r, 0.0); }
+  __device__ static double2 neg(double2 a) { return make_double2(-a.x, -a.y); }
+  __device__ static double2 sub(double2 a, double2 b) { return csub(a, b); }
+  __device__ static double2 scale(double2 a, double s) { return cscale(a, s); }
+  __device__ static double2 mul_conj(double2 a, double2 b) { return cmul(a, cconj(b)); }
+  __device__ static void fma_conj(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
+  }
+};
+
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npiv, const int* __restrict__ ids,
-                                                double2* K, int* status) {
-  extern __shared__ double2 sm[];
-  double2* sD = sm;                 // NB x NB diagonal block (column-major)
-  double2* sPI = sD + NB * NB;      // NB x TT panel rows of tile I ([k][row])
-  double2* sPJ = sPI + NB * TT;     // NB x TT panel rows of tile J
+                                                T* K, int* status) {
+  using O = Sc<T>;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  T* sD = reinterpret_cast<T*>(fsm);  // NB x NB diagonal block (column-major)
+  T* sPI = sD + NB * NB;              // NB x TT panel rows of tile I ([k][row])
+  T* sPJ = sPI + NB * TT;             // NB x TT panel rows of tile J
   const int slot = blockIdx.x;
-  double2* A = K + (size_t)slot * N * N;
+  T* A = K + (size_t)slot * N * N;
   const int tid = threadIdx.x;
   __shared__ int bad;
   if (tid == 0) bad = 0;
@@ -559,8 +644,8 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
       for (size_t t = tid; t < R * R; t += blockDim.x) {
         int jj = (int)(t / R), ii = (int)(t - (size_t)jj * R);
         if (ii >= jj) {
-          double2* p = &A[(size_t)(nv + ii) + (size_t)(nv + jj) * N];
-          *p = make_double2(-p->x, -p->y);
+          T* p = &A[(size_t)(nv + ii) + (size_t)(nv + jj) * N];
+          *p = O::neg(*p);
         }
       }
       __syncthreads();
@@ -568,27 +653,27 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
     // --- diagonal block: load, factor (unblocked), store
     for (int t = tid; t < w * w; t += blockDim.x) {
       int jj = t / w, ii = t - jj * w;
-      sD[ii + jj * NB] = (ii >= jj) ? A[(size_t)(k0 + ii) + (size_t)(k0 + jj) * N] : make_double2(0.0, 0.0);
+      sD[ii + jj * NB] = (ii >= jj) ? A[(size_t)(k0 + ii) + (size_t)(k0 + jj) * N] : O::zero();
     }
     __syncthreads();
     for (int j = 0; j < w; ++j) {
       if (tid == 0) {
-        double d = sD[j + j * NB].x;
+        double d = O::re(sD[j + j * NB]);
         if (!(d > 0.0)) {
           bad = 1;
           d = 1e-300;
         }
-        sD[j + j * NB] = make_double2(sqrt(d), 0.0);
+        sD[j + j * NB] = O::real(sqrt(d));
       }
       __syncthreads();
-      const double ljj = sD[j + j * NB].x;
-      for (int ii = j + 1 + tid; ii < w; ii += blockDim.x) sD[ii + j * NB] = cscale(sD[ii + j * NB], 1.0 / ljj);
+      const double ljj = O::re(sD[j + j * NB]);
+      for (int ii = j + 1 + tid; ii < w; ii += blockDim.x) sD[ii + j * NB] = O::scale(sD[ii + j * NB], 1.0 / ljj);
       __syncthreads();
       // rank-1 update of the remaining lower part of the block
       const int rem = w - j - 1;
       for (int t = tid; t < rem * rem; t += blockDim.x) {
         int cc = j + 1 + t / rem, ii = j + 1 + t % rem;
-        if (ii >= cc) sD[ii + cc * NB] = csub(sD[ii + cc * NB], cmul(sD[ii + j * NB], cconj(sD[cc + j * NB])));
+        if (ii >= cc) sD[ii + cc * NB] = O::sub(sD[ii + cc * NB], O::mul_conj(sD[ii + j * NB], sD[cc + j * NB]));
       }
       __syncthreads();
     }
@@ -598,18 +683,18 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
     }
     // --- panel: rows [k1, N) of columns [k0, k1): X L_D^H = P  (one row per thread)
     for (int row = k1 + tid; row < nact; row += blockDim.x) {
-      double2 x[NB];
+      T x[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j)
         if (j < w) x[j] = A[(size_t)row + (size_t)(k0 + j) * N];
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
         if (j < w) {
-          double2 v = x[j];
+          T v = x[j];
 #pragma unroll
           for (int kk = 0; kk < NB; ++kk)
-            if (kk < j) v = csub(v, cmul(x[kk], cconj(sD[j + kk * NB])));
-          x[j] = cscale(v, 1.0 / sD[j + j * NB].x);
+            if (kk < j) v = O::sub(v, O::mul_conj(x[kk], sD[j + kk * NB]));
+          x[j] = O::scale(v, 1.0 / O::re(sD[j + j * NB]));
         }
       }
 #pragma unroll
@@ -626,7 +711,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
       __syncthreads();
       for (int t = tid; t < NB * TT; t += blockDim.x) {
         int kk = t / TT, rr = t - kk * TT;
-        sPI[kk * TT + rr] = (kk < w && r0 + rr < nact) ? A[(size_t)(r0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
+        sPI[kk * TT + rr] = (kk < w && r0 + rr < nact) ? A[(size_t)(r0 + rr) + (size_t)(k0 + kk) * N] : O::zero();
       }
       for (int Jt = 0; Jt <= I; ++Jt) {
         const int c0 = k1 + Jt * TT;
@@ -634,16 +719,16 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
         for (int t = tid; t < NB * TT; t += blockDim.x) {
           int kk = t / TT, rr = t - kk * TT;
           sPJ[kk * TT + rr] =
-              (kk < w && c0 + rr < nact) ? A[(size_t)(c0 + rr) + (size_t)(k0 + kk) * N] : make_double2(0.0, 0.0);
+              (kk < w && c0 + rr < nact) ? A[(size_t)(c0 + rr) + (size_t)(k0 + kk) * N] : O::zero();
         }
         __syncthreads();
-        double2 acc[4][4];
+        T acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0.0, 0.0);
+          for (int b = 0; b < 4; ++b) acc[a][b] = O::zero();
         for (int kk = 0; kk < w; ++kk) {
-          double2 pa[4], pb[4];
+          T pa[4], pb[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) pa[a] = sPI[kk * TT + tx + 16 * a];
 #pragma unroll
@@ -651,11 +736,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              // acc += pa * conj(pb)
-              acc[a][b].x = fma(pa[a].x, pb[b].x, fma(pa[a].y, pb[b].y, acc[a][b].x));
-              acc[a][b].y = fma(pa[a].y, pb[b].x, fma(-pa[a].x, pb[b].y, acc[a][b].y));
-            }
+            for (int b = 0; b < 4; ++b) O::fma_conj(acc[a][b], pa[a], pb[b]);  // acc += pa conj(pb)
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -665,8 +746,8 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
           for (int b = 0; b < 4; ++b) {
             const int col = c0 + ty + 16 * b;
             if (col >= nact || col > row) continue;
-            double2* p = &A[(size_t)row + (size_t)col * N];
-            *p = csub(*p, acc[a][b]);
+            T* p = &A[(size_t)row + (size_t)col * N];
+            *p = O::sub(*p, acc[a][b]);
           }
         }
       }
@@ -720,6 +801,59 @@ __global__ void __launch_bounds__(256) k_extract(Sizes S, const int* __restrict_
       else
         zst[(size_t)e * nu + u] = v;
     }
+  }
+}
+
+
+// Real path: the factored K of a lossless element (real eps, mu, no Robin
+// face) in the phase-scaled basis.  With D_h = diag(-i on E-hat, 1 on H-hat)
+// and D_u = diag(-i on E, 1 on H): S = D_h S_r D_h^H, Z = D_u Z_r D_h^H,
+// L1 = D_u L1_r D_u^H; the load and therefore s, c, z vanish.
+__device__ __forceinline__ double2 phase_apply(double v, bool a_imag, bool b_imag) {
+  // d_a v conj(d_b) with d = -i (imag) or 1
+  if (a_imag == b_imag) return make_double2(v, 0.0);
+  return a_imag ? make_double2(0.0, -v) : make_double2(0.0, v);
+}
+
+__global__ void __launch_bounds__(256) k_extract_real(Sizes S, const int* __restrict__ ids, const double* __restrict__ K,
+                                                      double2* Sst, double2* sst, double* cst, double2* Zst,
+                                                      double2* zst, double2* L1st, double* Zscratch) {
+  const int slot = blockIdx.x;
+  const int e = ids[slot];
+  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h, nt = S.nt, nE = 3 * S.nL;
+  const double* A = K + (size_t)slot * N * N;
+  const int o = nv + nu;
+  double2* Se = Sst + (size_t)e * nh * nh;
+  for (int t = threadIdx.x; t < nh * nh; t += blockDim.x) {
+    const int i = t / nh, j = t - i * nh;
+    const double v = (i >= j) ? A[(size_t)(o + i) + (size_t)(o + j) * N] : A[(size_t)(o + j) + (size_t)(o + i) * N];
+    Se[t] = phase_apply(v, i < nt, j < nt);
+  }
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) sst[(size_t)e * nh + t] = make_double2(0.0, 0.0);
+  for (int t = threadIdx.x; t < nu; t += blockDim.x) zst[(size_t)e * nu + t] = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) cst[e] = 0.0;
+  if (L1st) {
+    double2* Le = L1st + (size_t)e * nu * nu;
+    for (int t = threadIdx.x; t < nu * nu; t += blockDim.x) {
+      const int i = t / nu, j = t - i * nu;
+      Le[t] = (i >= j) ? phase_apply(A[(size_t)(nv + i) + (size_t)(nv + j) * N], i < nE, j < nE)
+                       : make_double2(0.0, 0.0);
+    }
+  }
+  // Z_r = L1_r^{-T} Y_r, Y_r[u][t] = A[o + t][nv + u]; real back substitution per column t
+  double* Zr = Zscratch + (size_t)slot * nu * nh;
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) {
+    for (int u = nu - 1; u >= 0; --u) {
+      double v = A[(size_t)(o + t) + (size_t)(nv + u) * N];
+      for (int k = u + 1; k < nu; ++k) v -= A[(size_t)(nv + k) + (size_t)(nv + u) * N] * Zr[(size_t)k * nh + t];
+      Zr[(size_t)u * nh + t] = v / A[(size_t)(nv + u) + (size_t)(nv + u) * N];
+    }
+  }
+  __syncthreads();
+  double2* Ze = Zst + (size_t)e * nu * nh;
+  for (int q = threadIdx.x; q < nu * nh; q += blockDim.x) {
+    const int u = q / nh, t = q - u * nh;
+    Ze[q] = phase_apply(Zr[q], u < nE, t < nt);
   }
 }
 
@@ -812,7 +946,8 @@ static int run_robin(dpg_handle* h, const int* ids_host, int count, cudaStream_t
   return flush();
 }
 
-int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor, bool extract) {
+int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor, bool extract,
+                      bool real) {
   Workspace& w = h->ws;
   const Sizes& S = h->sz;
   if (count > w.cap) return DPG_ERR_ARG;
@@ -830,32 +965,49 @@ int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_
           (long long)mcs, count, s);
   gemm_tn(S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
           w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, s);
-  k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, w.ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
-                                             h->d_Xref, h->d_Tf, h->d_Tall, w.K);
+  double* Kr = reinterpret_cast<double*>(w.K);
+  if (real) {
+    k_build_K_real<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, w.ids, h->d_eps, h->d_mu, w.MC, h->d_Xref,
+                                                    h->d_Tall, Kr);
+  } else {
+    k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, w.ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
+                                               h->d_Xref, h->d_Tf, h->d_Tall, w.K);
+  }
   DPG_CUDA_TRY(h, cudaGetLastError());
   h->launches += 6;  // basis arrays, four GEMMs, K
-  int rc = run_robin(h, ids_host, count, s);
-  if (rc) return rc;
+  if (!real) {
+    int rc = run_robin(h, ids_host, count, s);
+    if (rc) return rc;
+  }
   if (factor) {
-    const size_t smem = sizeof(double2) * (NB * NB + 2 * NB * TT);
-    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = (real ? sizeof(double) : sizeof(double2)) * (NB * NB + 2 * NB * TT);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->timing) {
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
     }
-    k_factor<<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, w.ids, w.K, h->d_status);
+    if (real) {
+      DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_factor<double><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, w.ids, Kr, h->d_status);
+    } else {
+      DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_factor<double2><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, w.ids, w.K, h->d_status);
+    }
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
     if (h->timing) {
       cudaEventRecord(e1, s);
       h->factor_events.push_back({e0, e1});
       h->factor_counts.push_back(count);
+      h->factor_real.push_back(real ? 1 : 0);
     }
   }
   if (extract) {
-    k_extract<<<count, 256, 0, s>>>(S, w.ids, w.K, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
+    if (real)
+      k_extract_real<<<count, 256, 0, s>>>(S, w.ids, Kr, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1, w.V);
+    else
+      k_extract<<<count, 256, 0, s>>>(S, w.ids, w.K, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
   }
@@ -866,8 +1018,8 @@ int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_
 int factor_gram_only(dpg_handle* h, int count, cudaStream_t s) {
   const Sizes& S = h->sz;
   const size_t smem = sizeof(double2) * (NB * NB + 2 * NB * TT);
-  DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_factor<<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status);
+  DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_factor<double2><<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status);
   h->launches += 1;
   DPG_CUDA_TRY(h, cudaGetLastError());
   return DPG_OK;

@@ -306,19 +306,20 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   for (int ed = 0; ed < n_edges; ++ed) h_drop[ed] = (face_adj[ed] > 0 && face_robin[ed] == face_adj[ed]);
 
   // ---- global numbering of the free trace unknowns ------------------------
-  // E-hat blocks first (entity order), then H-hat blocks.
+  // Entity-major: each entity's free E-hat unknowns, then its free H-hat
+  // unknowns, so the rows of one entity are contiguous and share one column list.
   std::vector<int64_t> startE(n_ent, -1), startH(n_ent, -1);
   int64_t nfree = 0;
-  for (int en = 0; en < n_ent; ++en)
+  for (int en = 0; en < n_ent; ++en) {
     if (dir_grp[en] < 0) {
       startE[en] = nfree;
       nfree += ent_dofs(en);
     }
-  for (int en = 0; en < n_ent; ++en)
     if (!h_drop[en]) {
       startH[en] = nfree;
       nfree += ent_dofs(en);
     }
+  }
   if (nfree >= (int64_t)1 << 31) {
     h->err = "more than 2^31 trace unknowns";
     return DPG_ERR_UNSUPPORTED;
@@ -437,18 +438,23 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     for (int e = 0; e < ne; ++e) h->color_elems[fill[color[e]]++] = e;
   }
 
-  // ---- CSR pattern: rows of one entity block share their column list ----------
+  // ---- CSR pattern: the rows of one entity share their column list ----------
+  // Row i of entity block b has its W_b values at rowptr[i] and its columns
+  // in cols[colptr_b .. colptr_b + W_b) (sorted).  Only these per-entity lists
+  // are stored, not one column index per non-zero.
   std::vector<std::vector<int>> ent_elems(n_ent);
   for (int e = 0; e < ne; ++e) {
     for (int k = 0; k < 12; ++k) ent_elems[elem_edge[(size_t)e * 12 + k]].push_back(e);
     for (int k = 0; k < 6; ++k) ent_elems[n_edges + elem_face[(size_t)e * 6 + k]].push_back(e);
   }
-  // per entity: sorted list of column ranges (start, count) of the free blocks
-  std::vector<int64_t> rowlen(n_ent, 0);
-  std::vector<std::vector<std::pair<int64_t, int>>> ranges(n_ent);
+  h->blk.clear();
+  h->blk_colptr.clear();
+  h->cols.clear();
+  std::vector<int64_t> rowptr(nfree + 1, 0);
+  std::vector<int32_t> row2blk(nfree, -1);
   for (int en = 0; en < n_ent; ++en) {
-    bool rowE = startE[en] >= 0, rowH = startH[en] >= 0;
-    if (!rowE && !rowH) continue;
+    const int dE = startE[en] >= 0 ? ent_dofs(en) : 0, dH = startH[en] >= 0 ? ent_dofs(en) : 0;
+    if (dE + dH == 0) continue;
     std::vector<int> nb;
     for (int e : ent_elems[en]) {
       for (int k = 0; k < 12; ++k) nb.push_back(elem_edge[(size_t)e * 12 + k]);
@@ -456,33 +462,52 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     }
     std::sort(nb.begin(), nb.end());
     nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-    auto& rg = ranges[en];
-    for (int o : nb)
-      if (startE[o] >= 0) rg.push_back({startE[o], ent_dofs(o)});
-    for (int o : nb)
-      if (startH[o] >= 0) rg.push_back({startH[o], ent_dofs(o)});
-    std::sort(rg.begin(), rg.end());
-    int64_t len = 0;
-    for (auto& q : rg) len += q.second;
-    rowlen[en] = len;
+    const int64_t cp = (int64_t)h->cols.size();
+    int W = 0;
+    for (int o : nb) {  // entity-major numbering: neighbours in entity order give sorted columns
+      if (startE[o] >= 0)
+        for (int k = 0; k < ent_dofs(o); ++k) h->cols.push_back((int32_t)(startE[o] + k));
+      if (startH[o] >= 0)
+        for (int k = 0; k < ent_dofs(o); ++k) h->cols.push_back((int32_t)(startH[o] + k));
+    }
+    W = (int)((int64_t)h->cols.size() - cp);
+    const int64_t row0 = dE ? startE[en] : startH[en];
+    const int b = (int)h->blk.size();
+    h->blk.push_back({(int)row0, dE + dH, W, 0});
+    h->blk_colptr.push_back(cp);
+    for (int k = 0; k < dE + dH; ++k) row2blk[row0 + k] = b;
   }
-  // rows in global order
-  std::vector<int64_t> rowptr(nfree + 1, 0);
-  std::vector<int> row_ent(nfree);
-  for (int en = 0; en < n_ent; ++en) {
-    if (startE[en] >= 0)
-      for (int k = 0; k < ent_dofs(en); ++k) row_ent[startE[en] + k] = en;
-    if (startH[en] >= 0)
-      for (int k = 0; k < ent_dofs(en); ++k) row_ent[startH[en] + k] = en;
-  }
-  for (int64_t i = 0; i < nfree; ++i) rowptr[i + 1] = rowptr[i] + rowlen[row_ent[i]];
+  for (int64_t i = 0; i < nfree; ++i) rowptr[i + 1] = rowptr[i] + h->blk[row2blk[i]].z;
   h->nnz = rowptr[nfree];
-  std::vector<int32_t> col(h->nnz);
-  for (int64_t i = 0; i < nfree; ++i) {
-    int64_t o = rowptr[i];
-    for (auto& q : ranges[row_ent[i]])
-      for (int k = 0; k < q.second; ++k) col[o++] = (int32_t)(q.first + k);
+  h->nblk = (int)h->blk.size();
+  h->blk_dmax = 0;
+  for (const int4& B : h->blk) h->blk_dmax = std::max(h->blk_dmax, B.y);
+  // diagonal position of each block's own unknowns inside its column list
+  for (int b = 0; b < h->nblk; ++b) {
+    const int4& B = h->blk[b];
+    const int32_t* c = &h->cols[h->blk_colptr[b]];
+    int pos = 0;
+    while (pos < B.z && c[pos] != B.x) ++pos;
+    h->blk[b].w = pos;
   }
+
+  // ---- element classes: lossless elements without a Robin face are real ----
+  h->is_real.assign(ne, 0);
+  for (int e = 0; e < ne; ++e) {
+    bool real = m->elem_eps[e].im == 0.0 && m->elem_mu[e].im == 0.0;
+    for (int f = 0; f < 6; ++f)
+      if (m->face_bc[6 * (size_t)e + f] == DPG_BC_ROBIN) real = false;
+    h->is_real[e] = real;
+  }
+  h->real_elems.clear();
+  h->cplx_elems.clear();
+  for (int e = 0; e < ne; ++e) (h->is_real[e] ? h->real_elems : h->cplx_elems).push_back(e);
+  h->eps_host.assign(m->elem_eps, m->elem_eps + ne);
+  h->mu_host.assign(m->elem_mu, m->elem_mu + ne);
+  h->robin_face.assign(ne, 0);
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f < 6; ++f)
+      if (m->face_bc[6 * (size_t)e + f] == DPG_BC_ROBIN) h->robin_face[e] = 1;
 
   // ---- Robin entries ---------------------------------------------------------
   h->robin_entries.clear();
@@ -527,7 +552,10 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   DPG_ALLOC(h->d_z, sizeof(double2) * nu * ne);
   if (prm->flags & DPG_FLAG_ADJOINT) DPG_ALLOC(h->d_L1, sizeof(double2) * nu * nu * ne);
   DPG_ALLOC(h->d_rowptr, sizeof(int64_t) * (nfree + 1));
-  DPG_ALLOC(h->d_col, sizeof(int32_t) * h->nnz);
+  DPG_ALLOC(h->d_row2blk, sizeof(int32_t) * nfree);
+  DPG_ALLOC(h->d_blk, sizeof(int4) * h->nblk);
+  DPG_ALLOC(h->d_blk_colptr, sizeof(int64_t) * h->nblk);
+  DPG_ALLOC(h->d_cols, sizeof(int32_t) * h->cols.size());
   DPG_ALLOC(h->d_val, sizeof(double2) * h->nnz);
   DPG_ALLOC(h->d_b, sizeof(double2) * nfree);
   DPG_ALLOC(h->d_trfun, sizeof(int) * nt);
@@ -551,7 +579,12 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_robin, h->robin.data(), sizeof(dpg_robin_group) * h->robin.size(),
                                     cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_rowptr, rowptr.data(), sizeof(int64_t) * rowptr.size(), cudaMemcpyHostToDevice, s));
-  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_row2blk, row2blk.data(), sizeof(int32_t) * nfree, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_blk, h->blk.data(), sizeof(int4) * h->nblk, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_blk_colptr, h->blk_colptr.data(), sizeof(int64_t) * h->nblk,
+                                  cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_cols, h->cols.data(), sizeof(int32_t) * h->cols.size(), cudaMemcpyHostToDevice,
+                                  s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_trfun, trf.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * ne, s));
   // the host vectors above die at return: wait for the copies

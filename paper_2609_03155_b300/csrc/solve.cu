@@ -15,13 +15,34 @@ __device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
 }
 
 // ------------------------------------------------------------ assembly --
+// Position of column gj in row gi (entity column lists are sorted), or -1.
+__device__ __forceinline__ int64_t csr_pos(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ row2blk,
+                                           const int4* __restrict__ blk, const int64_t* __restrict__ colptr,
+                                           const int32_t* __restrict__ cols, int gi, int gj) {
+  const int b = row2blk[gi];
+  const int W = blk[b].z;
+  const int32_t* c = cols + colptr[b];
+  int lo = 0, hi = W - 1;
+  if (W <= 0) return -1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (c[mid] < gj)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return (c[lo] == gj) ? rowptr[gi] + lo : -1;
+}
+
 // One block per element of one colour: elements of a colour share no
 // unknowns, so the plain read-modify-write below has no race and the sum
 // order per entry is the fixed colour order.
 __global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict__ elems, const int32_t* __restrict__ l2g,
                                                   const double2* __restrict__ xfix, const double2* __restrict__ Sst,
                                                   const double2* __restrict__ sst, const int64_t* __restrict__ rowptr,
-                                                  const int32_t* __restrict__ col, double2* val, double2* b) {
+                                                  const int32_t* __restrict__ row2blk, const int4* __restrict__ blk,
+                                                  const int64_t* __restrict__ colptr, const int32_t* __restrict__ cols,
+                                                  double2* val, double2* b) {
   const int e = elems[blockIdx.x];
   const int32_t* g = l2g + (size_t)e * nh;
   const double2* Se = Sst + (size_t)e * nh * nh;
@@ -29,20 +50,8 @@ __global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict_
     const int i = t / nh, j = t - i * nh;
     const int gi = g[i], gj = g[j];
     if (gi < 0 || gj < 0) continue;
-    const int64_t end = rowptr[gi + 1];
-    int64_t lo = rowptr[gi], hi = end - 1;
-    if (lo >= end) continue;
-    while (lo < hi) {  // first position with col >= gj
-      int64_t mid = (lo + hi) >> 1;
-      if (col[mid] < gj)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    if (col[lo] == gj) {
-      double2 v = val[lo];
-      val[lo] = c_add(v, Se[t]);
-    }
+    const int64_t pos = csr_pos(rowptr, row2blk, blk, colptr, cols, gi, gj);
+    if (pos >= 0) val[pos] = c_add(val[pos], Se[t]);
   }
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     const int gi = g[i];
@@ -67,26 +76,47 @@ int assemble_system(dpg_handle* h, cudaStream_t s) {
     int cnt = h->color_off[c + 1] - h->color_off[c];
     if (cnt == 0) continue;
     k_assemble<<<cnt, 256, 0, s>>>(S.n_h, h->d_color_elems + h->color_off[c], h->d_l2g, h->d_xfix, h->d_S, h->d_s,
-                                   h->d_rowptr, h->d_col, h->d_val, h->d_b);
+                                   h->d_rowptr, h->d_row2blk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_val,
+                                   h->d_b);
     h->launches += 1;
   }
   DPG_CUDA_TRY(h, cudaGetLastError());
   h->have_system = true;
   h->have_val32 = false;
   h->have_dinv = false;
+  h->have_binv = false;
   return DPG_OK;
 }
 
 // ------------------------------------------------------------------ CG --
-// Conjugate gradients for the Hermitian positive definite trace system, with
-// optional Jacobi (diagonal) preconditioning z = D^{-1} r.  Device scalars
-// (double): see the SC_* slots.  All reductions are deterministic: per-block
-// partials summed in block order by the last block of each launch.
-enum { SC_RZ = 0, SC_PAP, SC_ALPHA, SC_BETA, SC_TOL2, SC_DONE, SC_ITER, SC_BB, SC_RN, SC_N };
-constexpr int RED_BLOCKS = 1184;  // 8 x 148
-constexpr int RED_THREADS = 256;
+// Conjugate gradients on the Hermitian positive definite trace system
+// (Sec. 2.3 end), optionally preconditioned by the diagonal (Jacobi) or by
+// the inverses of the entity diagonal blocks (each mesh entity's E-hat and
+// H-hat unknowns together).  One persistent cooperative kernel runs a whole
+// (inner) solve: three bounded grid barriers per iteration, every reduction
+// summed in a fixed order by every block (deterministic, identical scalars).
+struct SysView {
+  int64_t n;
+  int nblk;
+  const int64_t* rowptr;
+  const int32_t* row2blk;
+  const int4* blk;
+  const int64_t* colptr;
+  const int32_t* cols;
+  const int64_t* binv_ptr;
+  int dmax;  // rows of the largest entity block
+};
 
-__device__ unsigned int g_red_count[4];
+struct CgState {          // device-resident
+  double tol2;            // in: stop when ||r||^2 <= tol2
+  int max_iter;           // in
+  int status;             // out: 0 ok, 1 a barrier timed out
+  int iters;              // out
+  double rr, rz;          // out
+  unsigned int bar[2];    // grid barrier counter / generation
+};
+
+constexpr int CG_THREADS = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -94,215 +124,301 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Two block partial sums -> red[2 * blockIdx.x + {0,1}]; the last block to
-// finish sums the partials in index order and calls fin(tot0, tot1).
-template <typename Fin>
-__device__ void block_reduce2_last(double v0, double v1, double* red, unsigned int* counter, Fin fin) {
-  __shared__ double sw[2][RED_THREADS / 32];
-  __shared__ bool last;
-  v0 = warp_sum(v0);
-  v1 = warp_sum(v1);
+// Bounded grid-wide barrier for a cooperative launch.  Returns false when a
+// wait gave up (state->status set); callers then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(CgState* st, unsigned int& gen) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int target = gen + 1;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&st->bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      st->bar[0] = 0u;
+      __threadfence();
+      atomicExch(&st->bar[1], target);
+    } else {
+      unsigned long long spins = 0;
+      while (*((volatile unsigned int*)&st->bar[1]) != target) {
+        if (++spins > (1ull << 25)) {  // ~ seconds: something is broken, give up
+          atomicExch(&st->status, 1);
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  ++gen;
+  return *((volatile int*)&st->status) == 0;
+}
+
+// Block-level sum of (a, b) into red[slot*G + block] pairs, then every block
+// sums all partials in index order.  All threads get the totals.
+__device__ __forceinline__ void block_partial(double a, double b, double* red_a, double* red_b) {
+  __shared__ double sw[2][CG_THREADS / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
   if ((threadIdx.x & 31) == 0) {
-    sw[0][threadIdx.x >> 5] = v0;
-    sw[1][threadIdx.x >> 5] = v1;
+    sw[0][threadIdx.x >> 5] = a;
+    sw[1][threadIdx.x >> 5] = b;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t0 = 0, t1 = 0;
-    for (int k = 0; k < RED_THREADS / 32; ++k) {
-      t0 += sw[0][k];
-      t1 += sw[1][k];
+    double ta = 0, tb = 0;
+    for (int k = 0; k < CG_THREADS / 32; ++k) {
+      ta += sw[0][k];
+      tb += sw[1][k];
     }
-    red[2 * blockIdx.x] = t0;
-    red[2 * blockIdx.x + 1] = t1;
-    __threadfence();
-    unsigned int prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
+    red_a[blockIdx.x] = ta;
+    if (red_b) red_b[blockIdx.x] = tb;
+  }
+}
+
+__device__ __forceinline__ void grid_total(const double* red_a, const double* red_b, double& ta, double& tb) {
+  __shared__ double sw[2][CG_THREADS / 32];
+  double a = 0, b = 0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+    a += ((volatile const double*)red_a)[k];
+    if (red_b) b += ((volatile const double*)red_b)[k];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sw[0][threadIdx.x >> 5] = a;
+    sw[1][threadIdx.x >> 5] = b;
   }
   __syncthreads();
-  if (last) {
-    __threadfence();
-    double t0 = 0, t1 = 0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
-      t0 += ((volatile double*)red)[2 * k];
-      t1 += ((volatile double*)red)[2 * k + 1];
-    }
-    t0 = warp_sum(t0);
-    t1 = warp_sum(t1);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-      sw[0][threadIdx.x >> 5] = t0;
-      sw[1][threadIdx.x >> 5] = t1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0, b = 0;
-      for (int k = 0; k < RED_THREADS / 32; ++k) {
-        a += sw[0][k];
-        b += sw[1][k];
-      }
-      fin(a, b);
-      *counter = 0;
-    }
+  ta = tb = 0;
+  for (int k = 0; k < CG_THREADS / 32; ++k) {
+    ta += sw[0][k];
+    tb += sw[1][k];
   }
 }
 
-template <typename V> struct Real;
-template <> struct Real<double2> { using T = double; };
-template <> struct Real<float2> { using T = float; };
-__device__ __forceinline__ double2 mk(double a, double b, double2*) { return make_double2(a, b); }
-__device__ __forceinline__ float2 mk(double a, double b, float2*) { return make_float2((float)a, (float)b); }
+template <typename V> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+__device__ __forceinline__ double2 mkv(double a, double b, double2*) { return make_double2(a, b); }
+__device__ __forceinline__ float2 mkv(double a, double b, float2*) { return make_float2((float)a, (float)b); }
 
-// Ap = A p (one warp per row); partial sums of Re(p^H A p); alpha = rz / pAp at the end.
-// Products run in the storage precision, the row sum in that precision too,
-// the dot product in FP64.
+// y_row = (A x)_row by one warp; the row's columns are its entity's list.
+// Returns, on lane 0, y_row; the caller accumulates Re(x_row^* y_row).
 template <typename V>
-__global__ void __launch_bounds__(RED_THREADS) k_spmv_dot(int64_t n, const int64_t* __restrict__ rowptr,
-                                                          const int32_t* __restrict__ col, const V* __restrict__ val,
-                                                          const V* __restrict__ p, V* Ap, double* red, double* scal) {
-  using R = typename Real<V>::T;
-  if (scal[SC_DONE] != 0.0) return;
+__device__ __forceinline__ V row_spmv(const SysView& S, int64_t row, const V* __restrict__ val, const V* __restrict__ x) {
+  using R = typename RealOf<V>::T;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double dot = 0.0;
-  for (int64_t row = warp; row < n; row += nwarps) {
-    const int64_t a = rowptr[row], b = rowptr[row + 1];
-    R yr = 0, yi = 0;
-    for (int64_t k = a + lane; k < b; k += 32) {
-      const V v = val[k];
-      const V xv = p[col[k]];
-      yr = fma(v.x, xv.x, fma(-v.y, xv.y, yr));
-      yi = fma(v.x, xv.y, fma(v.y, xv.x, yi));
-    }
+  const int b = S.row2blk[row];
+  const int W = S.blk[b].z;
+  const int32_t* c = S.cols + S.colptr[b];
+  const V* v = val + S.rowptr[row];
+  R yr = 0, yi = 0;
+  int k = lane;
+  // four independent column chains in flight per lane
+  for (; k + 96 < W; k += 128) {
+    const int c0 = c[k], c1 = c[k + 32], c2 = c[k + 64], c3 = c[k + 96];
+    const V a0 = v[k], a1 = v[k + 32], a2 = v[k + 64], a3 = v[k + 96];
+    const V x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    yr = fma(a0.x, x0.x, fma(-a0.y, x0.y, yr));
+    yi = fma(a0.x, x0.y, fma(a0.y, x0.x, yi));
+    yr = fma(a1.x, x1.x, fma(-a1.y, x1.y, yr));
+    yi = fma(a1.x, x1.y, fma(a1.y, x1.x, yi));
+    yr = fma(a2.x, x2.x, fma(-a2.y, x2.y, yr));
+    yi = fma(a2.x, x2.y, fma(a2.y, x2.x, yi));
+    yr = fma(a3.x, x3.x, fma(-a3.y, x3.y, yr));
+    yi = fma(a3.x, x3.y, fma(a3.y, x3.x, yi));
+  }
+  for (; k < W; k += 32) {
+    const V a = v[k], xv = x[c[k]];
+    yr = fma(a.x, xv.x, fma(-a.y, xv.y, yr));
+    yi = fma(a.x, xv.y, fma(a.y, xv.x, yi));
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      yr += __shfl_xor_sync(0xffffffffu, yr, o);
-      yi += __shfl_xor_sync(0xffffffffu, yi, o);
-    }
-    if (lane == 0) {
-      Ap[row] = mk(yr, yi, (V*)nullptr);
-      const V pv = p[row];
-      dot += (double)pv.x * (double)yr + (double)pv.y * (double)yi;  // Re(conj(p) Ap)
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    yr += __shfl_xor_sync(0xffffffffu, yr, o);
+    yi += __shfl_xor_sync(0xffffffffu, yi, o);
   }
-  block_reduce2_last(dot, 0.0, red, &g_red_count[0], [&](double tot, double) {
-    scal[SC_PAP] = tot;
-    scal[SC_ALPHA] = scal[SC_RZ] / tot;
-  });
+  return mkv(yr, yi, (V*)nullptr);
 }
 
-// x += alpha p, r -= alpha Ap; partial ||r||^2 and Re(r^H D^{-1} r);
-// beta, the new rz, the iteration count and the done flag at the end.
+// z = M^{-1} r on the rows of block b (precond 0: copy, 1: Jacobi, 2: block
+// inverse) by one warp; rs is this warp's shared staging area (>= rows of the
+// largest block).  The block inverse is Hermitian, so row j read contiguously
+// gives column j: z_i = sum_j conj(Binv[j][i]) r_j with coalesced loads.
+// Returns the partial sums ||r||^2 and Re(r^H z) (per lane, FP64).
 template <typename V>
-__global__ void __launch_bounds__(RED_THREADS) k_cg_update(int64_t n, V* x, V* r, const V* __restrict__ p,
-                                                           const V* __restrict__ Ap,
-                                                           const typename Real<V>::T* __restrict__ dinv, double* red,
-                                                           double* scal) {
-  using R = typename Real<V>::T;
-  if (scal[SC_DONE] != 0.0) return;
-  const R alpha = (R)scal[SC_ALPHA];
-  double rr = 0.0, rz = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    V xv = x[i], rv = r[i];
-    const V pv = p[i], av = Ap[i];
-    xv.x = fma(alpha, pv.x, xv.x);
-    xv.y = fma(alpha, pv.y, xv.y);
-    rv.x = fma(-alpha, av.x, rv.x);
-    rv.y = fma(-alpha, av.y, rv.y);
-    x[i] = xv;
-    r[i] = rv;
-    const double q = (double)rv.x * rv.x + (double)rv.y * rv.y;
-    rr += q;
-    rz += dinv ? q * (double)dinv[i] : q;
-  }
-  block_reduce2_last(rr, rz, red, &g_red_count[1], [&](double trr, double trz) {
-    scal[SC_BETA] = trz / scal[SC_RZ];
-    scal[SC_RZ] = trz;
-    scal[SC_RN] = trr;
-    scal[SC_ITER] += 1.0;
-    if (trr <= scal[SC_TOL2]) scal[SC_DONE] = 1.0;
-  });
-}
-
-// p = D^{-1} r + beta p
-template <typename V>
-__global__ void k_cg_p(int64_t n, const V* __restrict__ r, V* p, const typename Real<V>::T* __restrict__ dinv,
-                       const double* __restrict__ scal) {
-  using R = typename Real<V>::T;
-  if (scal[SC_DONE] != 0.0) return;
-  const R beta = (R)scal[SC_BETA];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const V rv = r[i];
-    const R d = dinv ? dinv[i] : (R)1;
-    V pv = p[i];
-    pv.x = fma(beta, pv.x, d * rv.x);
-    pv.y = fma(beta, pv.y, d * rv.y);
-    p[i] = pv;
-  }
-}
-
-// Start of a (possibly inner) solve for A d = r0 with d = 0: r = r0 (converted
-// to the solve precision), p = D^{-1} r, rz = Re(r^H D^{-1} r), rn = ||r||^2.
-template <typename V>
-__global__ void __launch_bounds__(RED_THREADS) k_cg_start(int64_t n, const double2* __restrict__ r0, V* r, V* p, V* d,
-                                                          const typename Real<V>::T* __restrict__ dinv, double* red,
-                                                          double* scal, double tol2) {
-  using R = typename Real<V>::T;
-  double rr = 0.0, rz = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const V rv = mk(r0[i].x, r0[i].y, (V*)nullptr);
-    const R dd = dinv ? dinv[i] : (R)1;
-    r[i] = rv;
-    V pv;
-    pv.x = dd * rv.x;
-    pv.y = dd * rv.y;
-    p[i] = pv;
-    d[i] = mk(0.0, 0.0, (V*)nullptr);
-    const double q = (double)rv.x * rv.x + (double)rv.y * rv.y;
-    rr += q;
-    rz += q * (double)dd;
-  }
-  block_reduce2_last(rr, rz, red, &g_red_count[2], [&](double trr, double trz) {
-    scal[SC_RZ] = trz;
-    scal[SC_RN] = trr;
-    scal[SC_TOL2] = tol2;
-    scal[SC_DONE] = (trr <= tol2) ? 1.0 : 0.0;
-    scal[SC_ITER] = 0.0;
-  });
-}
-
-// r = b - A x in FP64 (x may be NULL for x = 0); ||r||^2 -> scal[slot].
-__global__ void __launch_bounds__(RED_THREADS) k_residual(int64_t n, const int64_t* __restrict__ rowptr,
-                                                          const int32_t* __restrict__ col,
-                                                          const double2* __restrict__ val,
-                                                          const double2* __restrict__ x, const double2* __restrict__ b,
-                                                          double2* r, double* red, double* scal, int slot) {
+__device__ __forceinline__ void block_precond(const SysView& S, int b, int precond, const V* __restrict__ r, V* z,
+                                              const typename RealOf<V>::T* __restrict__ dinv,
+                                              const V* __restrict__ binv, V* rs, double& rr, double& rz) {
+  using R = typename RealOf<V>::T;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double acc = 0.0;
-  for (int64_t row = warp; row < n; row += nwarps) {
-    double yr = 0.0, yi = 0.0;
-    if (x) {
-      const int64_t a = rowptr[row], bb = rowptr[row + 1];
-      for (int64_t k = a + lane; k < bb; k += 32) {
-        const double2 v = val[k];
-        const double2 xv = x[col[k]];
-        yr = fma(v.x, xv.x, fma(-v.y, xv.y, yr));
-        yi = fma(v.x, xv.y, fma(v.y, xv.x, yi));
+  const int4 B = S.blk[b];
+  if (precond == 2) {
+    for (int i = lane; i < B.y; i += 32) rs[i] = r[B.x + i];
+    __syncwarp();
+    const V* Bi = binv + S.binv_ptr[b];
+    for (int i0 = 0; i0 < B.y; i0 += 32) {
+      const int i = i0 + lane;
+      R zr = 0, zi = 0;
+      if (i < B.y) {
+        for (int j = 0; j < B.y; ++j) {
+          const V a = Bi[(size_t)j * B.y + i];  // conj of Binv[i][j]
+          const V rj = rs[j];
+          zr = fma(a.x, rj.x, fma(a.y, rj.y, zr));
+          zi = fma(a.x, rj.y, fma(-a.y, rj.x, zi));
+        }
+        const V ri = rs[i];
+        const V zv = mkv(zr, zi, (V*)nullptr);
+        z[B.x + i] = zv;
+        rr += (double)ri.x * ri.x + (double)ri.y * ri.y;
+        rz += (double)ri.x * zr + (double)ri.y * zi;
       }
-      yr = warp_sum(yr);
-      yi = warp_sum(yi);
     }
-    if (lane == 0) {
+    __syncwarp();
+    return;
+  }
+  for (int i = lane; i < B.y; i += 32) {
+    const int64_t row = B.x + i;
+    const V ri = r[row];
+    V zi = ri;
+    if (precond == 1) {
+      const R d = dinv[row];
+      zi.x = d * ri.x;
+      zi.y = d * ri.y;
+    }
+    z[row] = zi;
+    rr += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    rz += (double)ri.x * zi.x + (double)ri.y * zi.y;
+  }
+}
+
+// One whole CG solve of A x = r0 (x = 0 at entry, r holds r0 at entry).
+template <typename V>
+__global__ void __launch_bounds__(CG_THREADS) k_cg_persistent(SysView S, const V* __restrict__ val, V* x, V* r, V* p,
+                                                             V* Ap, V* z, int precond,
+                                                             const typename RealOf<V>::T* __restrict__ dinv,
+                                                             const V* __restrict__ binv, double* red, CgState* st) {
+  using R = typename RealOf<V>::T;
+  extern __shared__ unsigned char cg_smem[];
+  V* rs = reinterpret_cast<V*>(cg_smem) + (threadIdx.x >> 5) * S.dmax;
+  const int G = gridDim.x;
+  double* redA = red;          // pAp partials
+  double* redB0 = red + G;     // rr partials
+  double* redB1 = red + 2 * G; // rz partials
+  const int warps = G * (CG_THREADS / 32);
+  const int gw = blockIdx.x * (CG_THREADS / 32) + (threadIdx.x >> 5);
+  unsigned int gen = *((volatile unsigned int*)&st->bar[1]);
+  const double tol2 = st->tol2;
+  const int max_iter = st->max_iter;
+  // phase 0: z = M^{-1} r, p = z, x = 0
+  double rr = 0, rz = 0;
+  for (int b = gw; b < S.nblk; b += warps) {
+    block_precond<V>(S, b, precond, r, z, dinv, binv, rs, rr, rz);
+    __syncwarp();
+    const int4 B = S.blk[b];
+    for (int i = threadIdx.x & 31; i < B.y; i += 32) {
+      p[B.x + i] = z[B.x + i];
+      x[B.x + i] = mkv(0.0, 0.0, (V*)nullptr);
+    }
+  }
+  block_partial(rr, rz, redB0, redB1);
+  if (!grid_barrier(st, gen)) return;
+  grid_total(redB0, redB1, rr, rz);
+  int it = 0;
+  bool done = rr <= tol2;
+  while (!done && it < max_iter) {
+    // A: Ap = A p and Re(p^H A p)
+    double pap = 0;
+    for (int64_t row = gw; row < S.n; row += warps) {
+      const V y = row_spmv<V>(S, row, val, p);
+      if ((threadIdx.x & 31) == 0) {
+        Ap[row] = y;
+        const V pr = p[row];
+        pap += (double)pr.x * y.x + (double)pr.y * y.y;
+      }
+    }
+    block_partial(pap, 0.0, redA, nullptr);
+    if (!grid_barrier(st, gen)) return;
+    double tpap, dummy;
+    grid_total(redA, nullptr, tpap, dummy);
+    const R alpha = (R)(rz / tpap);
+    // B: x += alpha p, r -= alpha Ap, z = M^{-1} r
+    double rr2 = 0, rz2 = 0;
+    for (int b = gw; b < S.nblk; b += warps) {
+      const int4 B = S.blk[b];
+      for (int i = threadIdx.x & 31; i < B.y; i += 32) {
+        const int64_t row = B.x + i;
+        V xv = x[row], rv = r[row];
+        const V pv = p[row], av = Ap[row];
+        xv.x = fma(alpha, pv.x, xv.x);
+        xv.y = fma(alpha, pv.y, xv.y);
+        rv.x = fma(-alpha, av.x, rv.x);
+        rv.y = fma(-alpha, av.y, rv.y);
+        x[row] = xv;
+        r[row] = rv;
+      }
+      __syncwarp();
+      block_precond<V>(S, b, precond, r, z, dinv, binv, rs, rr2, rz2);
+    }
+    block_partial(rr2, rz2, redB0, redB1);
+    if (!grid_barrier(st, gen)) return;
+    double trr, trz;
+    grid_total(redB0, redB1, trr, trz);
+    const R beta = (R)(trz / rz);
+    rz = trz;
+    rr = trr;
+    ++it;
+    if (rr <= tol2) break;
+    // C: p = z + beta p
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)G * blockDim.x) {
+      const V zv = z[i];
+      V pv = p[i];
+      pv.x = fma(beta, pv.x, zv.x);
+      pv.y = fma(beta, pv.y, zv.y);
+      p[i] = pv;
+    }
+    if (!grid_barrier(st, gen)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->iters = it;
+    st->rr = rr;
+    st->rz = rz;
+  }
+}
+
+// r = b - A x in FP64 (x may be NULL for x = 0); ||r||^2 summed in block order.
+__global__ void __launch_bounds__(CG_THREADS) k_residual(SysView S, const double2* __restrict__ val,
+                                                         const double2* __restrict__ x, const double2* __restrict__ b,
+                                                         double2* r, double* red, double* out) {
+  const int warps = gridDim.x * (CG_THREADS / 32);
+  const int gw = blockIdx.x * (CG_THREADS / 32) + (threadIdx.x >> 5);
+  double acc = 0.0;
+  for (int64_t row = gw; row < S.n; row += warps) {
+    const double2 ax = x ? row_spmv<double2>(S, row, val, x) : make_double2(0.0, 0.0);
+    if ((threadIdx.x & 31) == 0) {
       const double2 bv = b[row];
-      const double2 rv = make_double2(bv.x - yr, bv.y - yi);
+      const double2 rv = make_double2(bv.x - ax.x, bv.y - ax.y);
       r[row] = rv;
       acc += rv.x * rv.x + rv.y * rv.y;
     }
   }
-  block_reduce2_last(acc, 0.0, red, &g_red_count[3], [&](double tot, double) { scal[slot] = tot; });
+  block_partial(acc, 0.0, red, nullptr);
+  // the caller sums red[0..G) with k_sum_red
+}
+
+__global__ void k_sum_red(int G, const double* __restrict__ red, double* out) {
+  __shared__ double sw[32];
+  double a = 0;
+  for (int k = threadIdx.x; k < G; k += blockDim.x) a += red[k];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sw[k];
+    *out = t;
+  }
 }
 
 __global__ void k_to_f32(int64_t n, const double2* __restrict__ a, float2* b) {
@@ -310,21 +426,10 @@ __global__ void k_to_f32(int64_t n, const double2* __restrict__ a, float2* b) {
     b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
-// inverse of the (real, positive) diagonal of the Hermitian matrix
-__global__ void k_diag_inv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           const double2* __restrict__ val, double* dinv, float* dinv32) {
+__global__ void k_add_correction64(int64_t n, double2* x, const double2* __restrict__ d) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t lo = rowptr[i], hi = rowptr[i + 1] - 1;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if (col[mid] < i)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    const double d = (col[lo] == i && val[lo].x > 0) ? 1.0 / val[lo].x : 1.0;
-    dinv[i] = d;
-    dinv32[i] = (float)d;
+    x[i].x += d[i].x;
+    x[i].y += d[i].y;
   }
 }
 
@@ -335,81 +440,175 @@ __global__ void k_add_correction(int64_t n, double2* x, const float2* __restrict
   }
 }
 
-static int ensure_cg_buffers(dpg_handle* h, bool fp32) {
-  const size_t n = h->n;
-  auto al = [&](void** p, size_t bytes) -> int {
-    if (*p) return DPG_OK;
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      h->err = "CG buffer allocation failed";
-      return DPG_ERR_NOMEM;
-    }
-    return DPG_OK;
-  };
-  int rc = 0;
-  rc |= al((void**)&h->d_r, sizeof(double2) * n);
-  rc |= al((void**)&h->d_p, sizeof(double2) * n);
-  rc |= al((void**)&h->d_Ap, sizeof(double2) * n);
-  rc |= al((void**)&h->d_red, sizeof(double) * 2 * RED_BLOCKS);
-  rc |= al((void**)&h->d_scal, sizeof(double) * SC_N);
-  rc |= al((void**)&h->d_dinv, sizeof(double) * n);
-  rc |= al((void**)&h->d_dinv32, sizeof(float) * n);
-  if (fp32) {
-    rc |= al((void**)&h->d_r32, sizeof(float2) * n);
-    rc |= al((void**)&h->d_p32, sizeof(float2) * n);
-    rc |= al((void**)&h->d_Ap32, sizeof(float2) * n);
-    rc |= al((void**)&h->d_x32, sizeof(float2) * n);
-    rc |= al((void**)&h->d_val32, sizeof(float2) * h->nnz);
+// Diagonal and entity-block inverses.  One CTA per entity block: the
+// diagonal sub-block (the block's own columns are contiguous in its list
+// from position blk.w) is inverted by Gauss-Jordan elimination (Hermitian
+// positive definite, no pivoting needed) in shared memory.
+__global__ void __launch_bounds__(128) k_block_inverse(SysView S, const double2* __restrict__ val, double2* binv,
+                                                       float2* binv32, double* dinv, float* dinv32) {
+  extern __shared__ double2 sm[];
+  const int b = blockIdx.x;
+  const int4 B = S.blk[b];
+  const int d = B.y;
+  double2* A = sm;          // d x d
+  double2* Iv = sm + d * d; // d x d
+  for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+    const int i = t / d, j = t - i * d;
+    A[t] = val[S.rowptr[B.x + i] + B.w + j];
+    Iv[t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
-  return rc ? DPG_ERR_NOMEM : DPG_OK;
+  __syncthreads();
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const double a = A[i * d + i].x;
+    const double di = a > 0 ? 1.0 / a : 1.0;
+    dinv[B.x + i] = di;
+    dinv32[B.x + i] = (float)di;
+  }
+  for (int k = 0; k < d; ++k) {
+    __syncthreads();
+    const double2 piv = A[k * d + k];
+    const double pm = piv.x * piv.x + piv.y * piv.y;
+    const double2 ip = make_double2(piv.x / pm, -piv.y / pm);
+    __syncthreads();
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      A[k * d + j] = c_mul(A[k * d + j], ip);
+      Iv[k * d + j] = c_mul(Iv[k * d + j], ip);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+      const int i = t / d, j = t - i * d;
+      if (i == k) continue;
+      const double2 f = A[i * d + k];
+      const double2 ak = A[k * d + j], ik = Iv[k * d + j];
+      // row i -= f * row k (A's column k is read before it is overwritten: f uses column k, j loops)
+      if (j != k) {
+        const double2 pa = c_mul(f, ak);
+        A[i * d + j] = make_double2(A[i * d + j].x - pa.x, A[i * d + j].y - pa.y);
+      }
+      const double2 pi = c_mul(f, ik);
+      Iv[i * d + j] = make_double2(Iv[i * d + j].x - pi.x, Iv[i * d + j].y - pi.y);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+      if (i != k) A[i * d + k] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int64_t o = S.binv_ptr[b];
+  for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+    binv[o + t] = Iv[t];
+    binv32[o + t] = make_float2((float)Iv[t].x, (float)Iv[t].y);
+  }
 }
 
-// Run CG iterations in graph-captured groups until the device flag says done
-// or max_iter is reached.  The solve vectors are (x, r, p, Ap) of type V.
+static SysView sys_view(dpg_handle* h) {
+  SysView v;
+  v.n = h->n;
+  v.nblk = h->nblk;
+  v.rowptr = h->d_rowptr;
+  v.row2blk = h->d_row2blk;
+  v.blk = h->d_blk;
+  v.colptr = h->d_blk_colptr;
+  v.cols = h->d_cols;
+  v.binv_ptr = h->d_binv_ptr;
+  v.dmax = h->blk_dmax;
+  return v;
+}
+
+static int ensure_buf(dpg_handle* h, void** p, size_t bytes) {
+  if (*p) return DPG_OK;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->err = "CG buffer allocation of " + std::to_string(bytes) + " bytes failed";
+    return DPG_ERR_NOMEM;
+  }
+  return DPG_OK;
+}
+
 template <typename V>
-static int run_cg_loop(dpg_handle* h, const V* val, V* x, V* r, V* p, V* Ap, const typename Real<V>::T* dinv,
-                       int max_iter, cudaStream_t s, int* iters_out) {
-  const int64_t n = h->n;
-  const int group = 32;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  // capture on a private stream ordered after the caller's stream
-  cudaStream_t cs;
-  DPG_CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaEvent_t ev;
-  DPG_CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  DPG_CUDA_TRY(h, cudaEventRecord(ev, s));
-  DPG_CUDA_TRY(h, cudaStreamWaitEvent(cs, ev, 0));
-  DPG_CUDA_TRY(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < group; ++k) {
-    k_spmv_dot<V><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, h->d_rowptr, h->d_col, val, p, Ap, h->d_red, h->d_scal);
-    k_cg_update<V><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, x, r, p, Ap, dinv, h->d_red, h->d_scal);
-    k_cg_p<V><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, r, p, dinv, h->d_scal);
+static int persistent_grid(dpg_handle* h, int* grid, size_t smem) {
+  int dev = 0, sms = 0, per = 0, coop = 0;
+  DPG_CUDA_TRY(h, cudaGetDevice(&dev));
+  DPG_CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DPG_CUDA_TRY(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) {
+    h->err = "device does not support cooperative launches";
+    return DPG_ERR_UNSUPPORTED;
   }
-  cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-  if (ce != cudaSuccess) {
-    h->err = std::string("graph capture: ") + cudaGetErrorString(ce);
-    return DPG_ERR_CUDA;
+  DPG_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<V>, CG_THREADS, smem));
+  *grid = std::max(1, std::min(per, 8) * sms);
+  return DPG_OK;
+}
+
+// One persistent solve of A d = r0 (d = 0 at entry; r holds r0 at entry).
+template <typename V>
+static int run_persistent(dpg_handle* h, const V* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
+                          const typename RealOf<V>::T* dinv, const V* binv, double tol2, int max_iter,
+                          cudaStream_t s, int* iters, double* rr_out) {
+  int grid = 0;
+  const size_t smem = sizeof(V) * (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax);
+  if (smem > 48 * 1024)
+    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_cg_persistent<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int rc = persistent_grid<V>(h, &grid, smem);
+  if (rc) return rc;
+  CgState host{};
+  host.tol2 = tol2;
+  host.max_iter = max_iter;
+  CgState* st = static_cast<CgState*>(h->d_cgstate);
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(st, &host, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  SysView S = sys_view(h);
+  double* red = h->d_red;
+  void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st};
+  DPG_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_cg_persistent<V>, dim3(grid), dim3(CG_THREADS), args, smem, s));
+  h->launches += 1;
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(&host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (host.status != 0) {
+    h->err = "a grid barrier of the CG kernel timed out";
+    return DPG_ERR_TIMEOUT;
   }
-  DPG_CUDA_TRY(h, cudaGraphInstantiate(&exec, graph, 0));
-  double scal[SC_N];
-  for (int launched = 0; launched < max_iter; launched += group) {
-    DPG_CUDA_TRY(h, cudaGraphLaunch(exec, cs));
-    h->launches += 3 * group;
-    // read the flag every fourth group so the device stays busy in between
-    if (((launched / group) & 3) == 3 || launched + group >= max_iter) {
-      DPG_CUDA_TRY(h, cudaMemcpyAsync(scal, h->d_scal, sizeof(scal), cudaMemcpyDeviceToHost, cs));
-      DPG_CUDA_TRY(h, cudaStreamSynchronize(cs));
-      if (scal[SC_DONE] != 0.0 || (int)scal[SC_ITER] >= max_iter) break;
+  *iters = host.iters;
+  *rr_out = host.rr;
+  return DPG_OK;
+}
+
+static int residual(dpg_handle* h, const double2* x, const double2* b, double2* r, cudaStream_t s, double* rr) {
+  SysView S = sys_view(h);
+  const int G = 1184;
+  k_residual<<<G, CG_THREADS, 0, s>>>(S, h->d_val, x, b, r, h->d_red, nullptr);
+  k_sum_red<<<1, 1024, 0, s>>>(G, h->d_red, h->d_red + 3 * 4096);
+  h->launches += 2;
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(rr, h->d_red + 3 * 4096, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  return DPG_OK;
+}
+
+static int prepare_preconditioner(dpg_handle* h, cudaStream_t s) {
+  if (h->have_binv) return DPG_OK;
+  if (!h->d_binv_ptr) {
+    std::vector<int64_t> ptr(h->nblk + 1, 0);
+    int dmax = 0;
+    for (int b = 0; b < h->nblk; ++b) {
+      ptr[b + 1] = ptr[b] + (int64_t)h->blk[b].y * h->blk[b].y;
+      dmax = std::max(dmax, h->blk[b].y);
     }
+    h->binv_dmax = dmax;
+    int rc = 0;
+    rc |= ensure_buf(h, (void**)&h->d_binv_ptr, sizeof(int64_t) * (h->nblk + 1));
+    rc |= ensure_buf(h, (void**)&h->d_binv, sizeof(double2) * ptr[h->nblk]);
+    rc |= ensure_buf(h, (void**)&h->d_binv32, sizeof(float2) * ptr[h->nblk]);
+    rc |= ensure_buf(h, (void**)&h->d_dinv, sizeof(double) * h->n);
+    rc |= ensure_buf(h, (void**)&h->d_dinv32, sizeof(float) * h->n);
+    if (rc) return DPG_ERR_NOMEM;
+    DPG_CUDA_TRY(h, cudaMemcpy(h->d_binv_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice));
   }
-  DPG_CUDA_TRY(h, cudaMemcpyAsync(scal, h->d_scal, sizeof(scal), cudaMemcpyDeviceToHost, cs));
-  DPG_CUDA_TRY(h, cudaStreamSynchronize(cs));
-  *iters_out = (int)scal[SC_ITER];
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  cudaEventDestroy(ev);
-  cudaStreamDestroy(cs);
+  const size_t smem = sizeof(double2) * 2 * (size_t)h->binv_dmax * h->binv_dmax;
+  if (smem > 48 * 1024)
+    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_block_inverse<<<h->nblk, 128, smem, s>>>(sys_view(h), h->d_val, h->d_binv, h->d_binv32, h->d_dinv, h->d_dinv32);
+  h->launches += 1;
+  DPG_CUDA_TRY(h, cudaGetLastError());
+  h->have_binv = true;
+  h->have_dinv = true;
   return DPG_OK;
 }
 
@@ -423,92 +622,103 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     h->err = "bad CG arguments";
     return DPG_ERR_ARG;
   }
-  const bool ir = (mode & DPG_CG_IR_FP32) != 0;
-  const bool jac = (mode & DPG_CG_JACOBI) != 0;
-  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI)) {
+  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI) ||
+      ((mode & DPG_CG_JACOBI) && (mode & DPG_CG_BLOCK_JACOBI))) {
     h->err = "unknown CG mode";
     return DPG_ERR_ARG;
   }
-  int rc = ensure_cg_buffers(h, ir);
-  if (rc) return rc;
-  const int64_t n = h->n;
+  const bool ir = (mode & DPG_CG_IR_FP32) != 0;
+  const int precond = (mode & DPG_CG_BLOCK_JACOBI) ? 2 : ((mode & DPG_CG_JACOBI) ? 1 : 0);
+  const size_t n = h->n;
+  int rc = 0;
+  rc |= ensure_buf(h, (void**)&h->d_r, sizeof(double2) * n);
+  rc |= ensure_buf(h, (void**)&h->d_p, sizeof(double2) * n);
+  rc |= ensure_buf(h, (void**)&h->d_Ap, sizeof(double2) * n);
+  rc |= ensure_buf(h, (void**)&h->d_zv, sizeof(double2) * n);
+  rc |= ensure_buf(h, (void**)&h->d_d64, sizeof(double2) * n);
+  rc |= ensure_buf(h, (void**)&h->d_red, sizeof(double) * (3 * 4096 + 8));
+  rc |= ensure_buf(h, (void**)&h->d_cgstate, sizeof(CgState));
+  if (ir) {
+    rc |= ensure_buf(h, (void**)&h->d_r32, sizeof(float2) * n);
+    rc |= ensure_buf(h, (void**)&h->d_p32, sizeof(float2) * n);
+    rc |= ensure_buf(h, (void**)&h->d_Ap32, sizeof(float2) * n);
+    rc |= ensure_buf(h, (void**)&h->d_x32, sizeof(float2) * n);
+    rc |= ensure_buf(h, (void**)&h->d_z32, sizeof(float2) * n);
+    rc |= ensure_buf(h, (void**)&h->d_val32, sizeof(float2) * h->nnz);
+  }
+  if (rc) return DPG_ERR_NOMEM;
   const double2* rhs = b ? b : h->d_b;
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   cudaEventRecord(t0, s);
-  if (!h->have_dinv) {
-    k_diag_inv<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->d_rowptr, h->d_col, h->d_val, h->d_dinv, h->d_dinv32);
-    h->launches += 1;
-    h->have_dinv = true;
+  if (precond) {
+    rc = prepare_preconditioner(h, s);
+    if (rc) return rc;
   }
   if (ir && !h->have_val32) {
-    k_to_f32<<<RED_BLOCKS, RED_THREADS, 0, s>>>(h->nnz, h->d_val, h->d_val32);
+    k_to_f32<<<1184, 256, 0, s>>>(h->nnz, h->d_val, h->d_val32);
     h->launches += 1;
     h->have_val32 = true;
   }
-  double scal[SC_N];
-  // r = b (x = 0), ||b||^2 -> SC_BB
-  k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->d_rowptr, h->d_col, h->d_val, nullptr, rhs, h->d_r, h->d_red,
-                                                 h->d_scal, SC_BB);
-  h->launches += 1;
-  DPG_CUDA_TRY(h, cudaMemcpyAsync(scal, h->d_scal, sizeof(scal), cudaMemcpyDeviceToHost, s));
-  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(scal[SC_BB]);
+  // r = b (x = 0)
+  double bb = 0;
+  rc = residual(h, nullptr, rhs, h->d_r, s, &bb);
+  if (rc) return rc;
+  const double bnorm = std::sqrt(bb);
   const double tol = std::max(rtol * bnorm, atol);
   int total_iters = 0, outer = 0;
+  // Outer loop: solve A d = r for the current true residual, x += d, recompute
+  // r = b - A x in FP64.  With FP32 inner solves this is iterative refinement
+  // (inner tolerance inner_rtol); with FP64 inner solves the first pass already
+  // targets the final tolerance and further passes only replace a recursive
+  // residual that drifted from the true one.
+  DPG_CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double2) * n, s));
   double rnorm = bnorm;
-  if (!ir) {
-    // FP64 solve directly on x
-    k_cg_start<double2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->d_r, h->d_r, h->d_p, x, jac ? h->d_dinv : nullptr,
-                                                           h->d_red, h->d_scal, tol * tol);
-    h->launches += 1;
-    rc = run_cg_loop<double2>(h, h->d_val, x, h->d_r, h->d_p, h->d_Ap, jac ? h->d_dinv : nullptr, max_iter, s,
-                              &total_iters);
-    if (rc) return rc;
-  } else {
-    DPG_CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double2) * n, s));
-    bool converged = rnorm <= tol;
-    while (!converged && total_iters < max_iter && outer < 100) {
-      // inner FP32 CG on A d = r to relative tolerance inner_rtol (not below the outer target)
+  bool conv = rnorm <= tol;
+  const int max_outer = ir ? 100 : 8;
+  while (!conv && total_iters < max_iter && outer < max_outer) {
+    int it = 0;
+    double rr = 0;
+    if (ir) {
       const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
-      k_cg_start<float2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->d_r, h->d_r32, h->d_p32, h->d_x32,
-                                                            jac ? h->d_dinv32 : nullptr, h->d_red, h->d_scal,
-                                                            itol * itol);
+      k_to_f32<<<1184, 256, 0, s>>>((int64_t)n, h->d_r, h->d_r32);
       h->launches += 1;
-      int it = 0;
-      rc = run_cg_loop<float2>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, jac ? h->d_dinv32 : nullptr,
-                               max_iter - total_iters, s, &it);
+      rc = run_persistent<float2>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32, precond,
+                                  h->d_dinv32, h->d_binv32, itol * itol, max_iter - total_iters, s, &it, &rr);
       if (rc) return rc;
-      total_iters += it;
-      ++outer;
-      // FP64 update and true residual
-      k_add_correction<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, h->d_x32);
-      k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->d_rowptr, h->d_col, h->d_val, x, rhs, h->d_r, h->d_red,
-                                                     h->d_scal, SC_BB);
-      h->launches += 2;
-      DPG_CUDA_TRY(h, cudaMemcpyAsync(scal, h->d_scal, sizeof(scal), cudaMemcpyDeviceToHost, s));
-      DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
-      rnorm = std::sqrt(scal[SC_BB]);
-      converged = rnorm <= tol;
-      if (it == 0) break;
+      k_add_correction<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_x32);
+    } else {
+      const double itol = 0.5 * tol;
+      rc = run_persistent<double2>(h, h->d_val, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond, h->d_dinv,
+                                   h->d_binv, itol * itol, max_iter - total_iters, s, &it, &rr);
+      if (rc) return rc;
+      k_add_correction64<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_d64);
     }
+    h->launches += 1;
+    total_iters += it;
+    ++outer;
+    double r2 = 0;
+    rc = residual(h, x, rhs, h->d_r, s, &r2);
+    if (rc) return rc;
+    rnorm = std::sqrt(r2);
+    conv = rnorm <= tol;
+    if (it == 0) break;
   }
-  // final true residual in FP64 (into Ap as scratch)
-  k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h->d_rowptr, h->d_col, h->d_val, x, rhs, h->d_Ap, h->d_red,
-                                                 h->d_scal, SC_PAP);
-  h->launches += 1;
+  // final true residual in FP64
+  double res2 = 0;
+  rc = residual(h, x, rhs, h->d_Ap, s, &res2);
+  if (rc) return rc;
   cudaEventRecord(t1, s);
-  DPG_CUDA_TRY(h, cudaMemcpyAsync(scal, h->d_scal, sizeof(scal), cudaMemcpyDeviceToHost, s));
-  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  cudaEventSynchronize(t1);
   float ms = 0;
   cudaEventElapsedTime(&ms, t0, t1);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  const double res = std::sqrt(scal[SC_PAP]);
+  const double res = std::sqrt(res2);
   const double rel = bnorm > 0 ? res / bnorm : 0.0;
   // the recursive residual of plain CG may sit a hair below the true one
-  const bool converged = res <= tol * (ir ? 1.0 : 1.0 + 1e-3) || (!ir && scal[SC_DONE] != 0.0 && res <= 2 * tol);
+  const bool converged = res <= tol;
   h->cg_ms += ms;
   h->cg_iters += total_iters;
   if (rep) {

@@ -107,6 +107,9 @@ class DPG:
         """Host -> device copy of per-element corners (n_elem x 8 x 3), eps, mu (use pinned tensors)."""
         check(_lib.lib().dpg_update_elements(self.h, ptr(corners), ptr(eps), ptr(mu), stream_handle(stream)), self.h)
 
+    def set_real_path(self, enable=True):
+        check(_lib.lib().dpg_set_real_path(self.h, int(enable)), self.h)
+
     def timing_enable(self, enable=True):
         check(_lib.lib().dpg_timing_enable(self.h, int(enable)), self.h)
 

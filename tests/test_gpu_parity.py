@@ -65,7 +65,7 @@ def _oracle_element(mesh, e):
 def test_element_matrices_match_oracle(dpg_mod, case):
     if case == "waveguide2d_p1":
         mesh = inputs.waveguide_2d_config(p=1)
-        ids = [0, 5, 31]
+        ids = [0, 9, 20, 31]  # 0, 31: port / impedance faces (complex path); 9, 20: lossless (real path)
     else:
         p = int(case[-1])
         mesh = _lossy_jittered(p)
@@ -163,15 +163,21 @@ def test_te10_waveguide_field_error(dpg_mod):
     d.destroy()
 
 
-def test_ir_fp32_matches_fp64(dpg_mod):
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5])
+def test_cg_modes_match_fp64(dpg_mod, mode):
+    """IR (FP32 inner), Jacobi and entity-block Jacobi reach the plain FP64 CG solution."""
     mesh = _lossy_jittered(1, n=(2, 2, 2))
     d = dpg_mod.DPG(mesh)
     d.element_batch()
     d.assemble()
     x64, r64 = d.cg_solve(rtol=1e-12)
-    x32, r32 = d.cg_solve(mode=1, rtol=1e-12, inner_rtol=1e-4)
-    assert r32['converged'] and r32['outer'] >= 1
-    assert rel(x32.cpu().numpy(), x64.cpu().numpy()) < 1e-9
+    xm, rm = d.cg_solve(mode=mode, rtol=1e-12, inner_rtol=1e-4)
+    assert rm['converged'] and rm['rel_residual'] <= 1e-12
+    if mode & 1:
+        assert rm['outer'] >= 1
+    if mode & 6:
+        assert rm['iterations'] < r64['iterations']
+    assert rel(xm.cpu().numpy(), x64.cpu().numpy()) < 1e-9
     d.destroy()
 
 
@@ -246,4 +252,30 @@ def test_adjoint_gradient_matches_gpu_finite_differences(dpg_mod):
                 fd = (Pfun(ep).item() - Pfun(em).item()) / (2 * h)
             an = g[e].real if part == 1.0 else g[e].imag
             assert abs(an - fd) < 1e-5 * scale + 1e-9 * abs(P.item()), (e, part, an, fd)
+    d.destroy()
+
+
+def test_real_path_matches_complex_path(dpg_mod):
+    """Lossless elements: the phase-scaled real factorisation gives the complex path's S_K, Z_K and field."""
+    mesh = inputs.waveguide_3d_config(4, 2, 6, p=2)
+    d = dpg_mod.DPG(mesh)
+    inner = [e for e in range(mesh.n_elem) if not (mesh.face_bc[e] == 2).any()][:6]
+    assert inner
+    d.set_real_path(True)
+    out_r = d.element_dump(inner)
+    d.element_batch()
+    d.assemble()
+    x_r, _ = d.cg_solve(rtol=1e-13)
+    u_r, eta_r, _ = d.estimate(x_r)
+    d.set_real_path(False)
+    out_c = d.element_dump(inner)
+    d.element_batch()
+    d.assemble()
+    x_c, _ = d.cg_solve(rtol=1e-13)
+    u_c, eta_c, _ = d.estimate(x_c)
+    for k in range(len(inner)):
+        assert rel(out_r['S'][k], out_c['S'][k]) < 1e-10
+    assert rel(x_r.cpu().numpy(), x_c.cpu().numpy()) < 1e-10
+    assert rel(u_r.cpu().numpy(), u_c.cpu().numpy()) < 1e-10
+    assert np.max(np.abs(eta_r.cpu().numpy() - eta_c.cpu().numpy())) < 1e-7 * eta_c.cpu().numpy().max()
     d.destroy()

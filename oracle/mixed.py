@@ -159,8 +159,6 @@ def dirichlet_values_mixed(mesh, order, gid):
             spec['omega'] = mesh.omega
             Et = system.dirichlet_Et(spec)
             d, sd = f // 2, f % 2
-            nv = np.linalg.inv(element.trilinear(X, np.array([[0.5, 0.5, 0.5]]))[1][0]).T @ system.face_normal_ref(f)
-            nv /= np.linalg.norm(nv)
             tang = [q for q in range(3) if q != d]
             dofs = []  # (global id, reference node, component)
             fkey = _face_key(mesh, e, d, sd)
@@ -190,6 +188,9 @@ def dirichlet_values_mixed(mesh, order, gid):
                 if has_data.get(g, False):
                     continue
                 x, J = element.trilinear(X, np.array([node]))
+                # unit normal of the (planar) face at the node: J^{-T} N_ref (Nanson)
+                nv = np.linalg.inv(J[0]).T @ system.face_normal_ref(f)
+                nv /= np.linalg.norm(nv)
                 fixed[g] = Et(x, nv[None, :])[0] @ J[0][:, c]
                 has_data[g] = True
     return fixed

@@ -16,6 +16,34 @@ def test_uniform_order_reproduces_the_uniform_solver():
     assert np.allclose(a['eta'], b['eta'], rtol=1e-9, atol=1e-15)
 
 
+def test_uniform_order_reproduces_the_uniform_solver_on_jittered_lossy_mesh():
+    """Non-affine elements, Dirichlet data, Robin port and lossy materials: same field as system.solve."""
+    nx, ny, nz = 2, 2, 1
+    vert, elem, ijk = inputs.structured_hex(0.3, 0.2, 0.1, nx, ny, nz)
+    rng = np.random.default_rng(11)
+    inner = (vert > 1e-12) & (vert < np.array([0.3, 0.2, 0.1]) - 1e-12)
+    vert = vert + inner * rng.uniform(-0.012, 0.012, vert.shape)
+    spec = {'x0': (inputs.BC_DIRICHLET, 0), 'x1': (inputs.BC_DIRICHLET, 1), 'y0': (inputs.BC_DIRICHLET, 0),
+            'y1': (inputs.BC_DIRICHLET, 0), 'z0': (inputs.BC_ROBIN, 0), 'z1': (inputs.BC_ROBIN, 1)}
+    bc, grp = inputs.box_boundary_tags(ijk, nx, ny, nz, spec)
+    ne = elem.shape[0]
+    omega = 9.0
+    m = inputs.Mesh(vert=vert, elem=elem, p=np.full(ne, 1, np.int8),
+                    eps=np.exp(rng.uniform(0, np.log(10), ne)) + 1j * rng.uniform(0, 3, ne),
+                    mu=1.0 + 0.2 * rng.uniform(0, 1, ne) + 0.1j * rng.uniform(0, 1, ne), face_bc=bc, face_grp=grp,
+                    omega=omega,
+                    robin=[{'zinv': inputs.te_zinv(omega, 0.3, 0.2, 1, 0), 'port': (0.3, 0.2, 1, 0, 1.0, 1.0)},
+                           {'zinv': 0.7 - 0.2j, 'port': None}],
+                    dirichlet=[{'kind': inputs.DIRICHLET_ZERO, 'port': None},
+                               {'kind': inputs.DIRICHLET_SIN_PI_X2, 'port': None}])
+    a = system.solve(m)
+    b = mixed.solve_mixed(m)
+    assert a['n'] == b['n']
+    for e in range(ne):
+        assert np.allclose(b['rec'][e]['u'], a['rec'][e]['u'], rtol=0, atol=1e-10 * np.abs(a['rec'][e]['u']).max())
+    assert np.allclose(a['eta'], b['eta'], rtol=1e-8, atol=1e-15)
+
+
 @pytest.mark.parametrize("orders", [(1, 2), (2, 1, 3, 1)])
 def test_manufactured_solution_exact_with_mixed_orders(orders, monkeypatch):
     """A polynomial solution inside every element's spaces is reproduced exactly across order jumps."""

@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "DPG elements/s (local solve+η_K) & CG time-to-1e-10; mixed/batched vs FP64"
 UNIT = "elements/s"
 CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3, "fp64-bjacobi": 4, "ir-bjacobi": 5}
+PRECISIONS = {"fp64": 0, "tf32": 1, "3xtf32": 2}
 
 
 def config_mesh(name):
@@ -39,8 +40,27 @@ def config_mesh(name):
         return inputs.waveguide_3d_config(32, 16, 64, 2)
     if name == "waveguide3d-small":
         return inputs.waveguide_3d_config(8, 4, 16, 2)
+    if name == "waveguide3d-medium":
+        return inputs.waveguide_3d_config(16, 8, 32, 2)
+    if name == "waveguide3d-profile":
+        # small enough for ncu captures (a few GB on the device), CSR larger than L2
+        return inputs.waveguide_3d_config(12, 6, 24, 2)
     if name == "waveguide2d":
         return inputs.waveguide_2d_config(p=1)
+    if name == "cavity3":
+        # jittered unit cavity, p = 3, random lossy permittivity; 24^3 elements
+        # (2^18 elements at p = 3 need ~1.3 TB of condensation data and CSR)
+        return inputs.cavity(24, 3, jitter=0.1, eps_mode='random', name="cavity3_24x24x24_p3_jitter0.1")
+    if name == "fichera":
+        # Fichera-corner cavity, graded toward the re-entrant corner, degrees
+        # 1..4 in a 40/30/20/10 % mix; 12 cells per unit length (13,824 elements)
+        m = inputs.fichera_cavity(12, grade=1.5, name="fichera_12_graded_p1234")
+        return m
+    if name == "obstacle":
+        # unit cavity 32^3, p = 2, dielectric sphere eps = 20 + 5i of radius 0.2
+        m = inputs.cavity(32, 2, name="obstacle_cavity_32x32x32_p2")
+        inputs.sphere_obstacle(m, radius=0.2, eps=20.0 + 5.0j)
+        return m
     raise ValueError(name)
 
 
@@ -171,11 +191,16 @@ def main():
     ap.add_argument("--config", default="waveguide3d")
     ap.add_argument("--cg", default="ir-bjacobi", choices=sorted(CG_MODES))
     ap.add_argument("--rtol", type=float, default=1e-10)
-    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--max-iter", type=int, default=200000)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
+    ap.add_argument("--chunk", type=int, default=0, help="elements per launch (0: library default)")
+    ap.add_argument("--autotune", action="store_true", help="measure chunk sizes per degree before the warm-up")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="after the timed steps, solve again with FP64 quadrature and report the differences")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -193,8 +218,9 @@ def main():
 
     from paper_2609_03155_b300 import dpg
     mesh = config_mesh(args.config)
-    d = dpg.DPG(mesh)
+    d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk)
     mode = CG_MODES[args.cg]
+    tuned = d.autotune() if args.autotune else None
     stream = torch.cuda.current_stream()
 
     def step():
@@ -204,7 +230,8 @@ def main():
         ev[1].record(stream)
         d.assemble()
         ev[2].record(stream)
-        x, rep = d.cg_solve(mode=mode, rtol=args.rtol, max_iter=args.max_iter, inner_rtol=args.inner_rtol)
+        x, rep = d.cg_solve(mode=mode, rtol=args.rtol, max_iter=args.max_iter, inner_rtol=args.inner_rtol,
+                            raise_on_nonconvergence=False)
         ev[3].record(stream)
         u, eta, etag = d.estimate(x)
         ev[4].record(stream)
@@ -281,33 +308,74 @@ def main():
     if rank != 0:
         return
     p = int(mesh.p[0])
+    pvals = sorted(set(int(q) for q in mesh.p))
+    # element factorisation kernel (FP64 pipe): complex elements cost fpe(p)
+    # flops, lossless (real-path) elements a quarter of that
     fpe = flops_factor_per_element(p)
+    is_real = (mesh.eps.imag == 0) & (mesh.mu.imag == 0) & ~(mesh.face_bc == 2).any(axis=1)
+    fpe_el = np.array([flops_factor_per_element(int(q)) for q in mesh.p]) * np.where(is_real, 0.25, 1.0)
+    n_real = tim["factor_elements_real"]
+    n_cplx = tim["factor_elements"] - n_real
     fac_avg_ms = tim["factor_ms"] / max(1, tim["factor_launches"])
-    fac_elems = tim["factor_elements"] / max(1, tim["factor_launches"])
-    achieved = fpe * fac_elems / (fac_avg_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": "k_factor (blocked partial Cholesky + condensation, FP64 pipe)",
-            "achieved": achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s", "frac": achieved / (fp64 / 1e12),
-            "peak_source": "FP64 FMA throughput measured live by dpg_probe_peaks (DFMA loop)",
-            "traffic": None, "flops_per_element": fpe, "elements_per_launch": fac_elems,
-            "avg_launch_ms": fac_avg_ms}
+    fac_flops = float(fpe_el.sum()) * tim["factor_elements"] / mesh.n_elem
+    fac_achieved = fac_flops / max(1e-9, tim["factor_ms"] / 1e3) / 1e12
+    roof_fac = {"bound": "alu", "kernel": "k_factor<double|double2> (blocked partial Cholesky + condensation, FP64 pipe)",
+                "achieved": fac_achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s", "frac": fac_achieved / (fp64 / 1e12),
+                "peak_source": "FP64 FMA throughput measured live by dpg_probe_peaks (DFMA loop)", "traffic": None,
+                "flops_per_element_complex": fpe if len(pvals) == 1 else {str(q): flops_factor_per_element(q)
+                                                                                for q in pvals},
+                "flops_per_element_real": fpe / 4 if len(pvals) == 1 else "a quarter of the complex figure",
+                "elements_real": n_real,
+                "elements_complex": n_cplx, "launches": tim["factor_launches"], "avg_launch_ms": fac_avg_ms,
+                "time_s": tim["factor_ms"] / 1e3}
+    # persistent CG kernel (HBM bound)
+    hbm_peak, hbm_src = 6400.0, "fallback 6.4 TB/s (no MEASURED_PEAKS.json)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak, hbm_src = float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    except Exception:
+        pass
+    bpi = d.cg_bytes_per_iteration(mode)
+    cg_ach = bpi * tim["cg_kernel_iterations"] / max(1e-9, tim["cg_kernel_ms"] / 1e3) / 1e9
+    roof_cg = {"bound": "hbm", "kernel": "k_cg_persistent<%s> (one cooperative CG solve per launch)"
+               % ("float2" if mode & 1 else "double2"),
+               "achieved": cg_ach, "peak": hbm_peak, "unit": "GB/s", "frac": cg_ach / hbm_peak, "traffic": None,
+               "peak_source": hbm_src, "bytes_per_iteration": bpi,
+               "iterations": tim["cg_kernel_iterations"], "launches": tim["cg_kernel_launches"],
+               "avg_launch_ms": tim["cg_kernel_ms"] / max(1, tim["cg_kernel_launches"]),
+               "time_s": tim["cg_kernel_ms"] / 1e3}
+    if roof_cg["time_s"] >= roof_fac["time_s"]:
+        roof, roof2 = roof_cg, roof_fac
+    else:
+        roof, roof2 = roof_fac, roof_cg
+    # per-iteration cost of the paper's plain FP64 CG on the same system (short capped run)
+    _, rep64 = d.cg_solve(mode=0, rtol=1e-30, max_iter=200, raise_on_nonconvergence=False)
+    fp64_ms_it = rep64["ms"] / max(1, rep64["iterations"])
     cg_iters = last_rep["iterations"]
-    cg_bytes_iter = (8 if mode & 1 else 16) * d.nnz
     rate, cores, dt, nsamp = cpu_oracle_rate(mesh, args.cpu_sample)
     line = {
         "metric": METRIC, "value": world * mesh.n_elem / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not (mode & 1) else "f64+f32(IR inner)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("f64" if not (mode & 1) else "f64+f32(IR inner)")
+        + ("" if args.precision == "fp64" else f"+{args.precision}(quadrature)"),
         "data": "synthetic",
-        "config": {"workload": mesh.name, "elements": int(mesh.n_elem), "p": p, "dp": 1,
+        "config": {"workload": mesh.name, "elements": int(mesh.n_elem),
+                   "p": p if len(pvals) == 1 else {str(q): int((mesh.p == q).sum()) for q in pvals}, "dp": 1,
+                   "quadrature": args.precision,
+                   "chunks": {str(g[0]): g[2] for g in d.group_info()} if d.h else None,
+                   "autotuned": tuned is not None,
                    "trace_unknowns": int(d.n), "nnz": int(d.nnz), "cg": args.cg, "cg_rtol": args.rtol,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-element stores and CSR are tens of GB)"},
         "breakdown": {**br, "element_pass_elements_per_s": mesh.n_elem / br["element_pass_s"],
                       "cg_time_to_rtol_s": br["cg_s"], "cg_iterations": cg_iters, "cg_outer": last_rep["outer"],
-                      "cg_rel_residual": last_rep["rel_residual"],
+                      "cg_rel_residual": last_rep["rel_residual"], "cg_converged": last_rep["converged"],
                       "cg_ms_per_iteration": 1e3 * br["cg_s"] / max(1, cg_iters),
-                      "cg_algorithmic_GBps": cg_bytes_iter * cg_iters / br["cg_s"] / 1e9 if cg_iters else None},
+                      "fp64_plain_cg_ms_per_iteration": fp64_ms_it,
+                      "mixed_vs_fp64_ms_per_iteration": fp64_ms_it / (1e3 * br["cg_s"] / max(1, cg_iters))},
         "roofline": roof,
+        "roofline_secondary": roof2,
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{nsamp} elements of {mesh.name} ({dt:.1f} s): element formation, condensation, "
                                    f"recovery and eta_K; CG not in the sample"},
@@ -316,9 +384,39 @@ def main():
         "gpu_launches": int(tim["kernel_launches"]),
         "peaks_measured": {"fp64_tflops": fp64 / 1e12, "fp32_tflops": fp32 / 1e12},
     }
+    if args.precision_report and args.precision != "fp64":
+        line["precision_report"] = precision_report(d, mesh, x, eta, mode, args)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def precision_report(d, mesh, x, eta, mode, args):
+    """Differences of the reduced-precision run against FP64 quadrature on the same mesh."""
+    import torch
+    from paper_2609_03155_b300 import dpg
+    ids = np.linspace(0, mesh.n_elem - 1, 8).astype(np.int32)
+    ids = ids[mesh.p[ids] == mesh.p[ids[0]]]
+    red = d.element_dump(ids)
+    x_red = x.cpu().numpy()
+    eta_red = eta.cpu().numpy()
+    d.destroy()
+    ref = dpg.DPG(mesh)
+    full = ref.element_dump(ids)
+    ref.element_batch()
+    ref.assemble()
+    t0 = time.perf_counter()
+    x64, _ = ref.cg_solve(mode=mode, rtol=args.rtol, max_iter=args.max_iter, inner_rtol=args.inner_rtol)
+    _, eta64, _ = ref.estimate(x64)
+    x64 = x64.cpu().numpy()
+    eta64 = eta64.cpu().numpy()
+    ref.destroy()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    return {"elements_sampled": int(len(ids)),
+            "G_rel_frobenius": rel(red["G"], full["G"]), "B_rel_frobenius": rel(red["B"], full["B"]),
+            "S_rel_frobenius": rel(red["S"], full["S"]),
+            "trace_solution_rel_l2": rel(x_red, x64), "eta_rel_l2": rel(eta_red, eta64),
+            "reference": "same mesh, FP64 quadrature, same CG mode and tolerance"}
 
 
 if __name__ == "__main__":

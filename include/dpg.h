@@ -30,6 +30,18 @@
  *         order r (component-major, x-index fastest) whose tangential trace is
  *         non-zero on some face, in that order;                n_h = 24 r^2.
  *
+ * Mixed trial degrees (the paper refines in h only, Sec. 4.2): each element
+ * computes at its own p; a mesh edge or face carries trace unknowns of order
+ * r_E = min over the elements containing it of (p + 1), so the trace lies in
+ * every neighbour's trace space.  Element K's trace coefficients are the
+ * global trace's nodal values at K's own nodes, uhat_K = R_K uhat (R_K: 1D
+ * Lagrange polynomials of the entity order at K's nodes).  Per-element arrays
+ * are then of varying length; dpg_element_layout gives their offsets.  The
+ * trace map and the stored S_K, s_K refer to the element's trace slots: the
+ * global unknowns of an entity sit in the element's slots of the same entity
+ * and index, the other slots are unused (-2), and S_K, s_K are R_K^H S_K R_K,
+ * R_K^H s_K in those slots.
+ *
  * Mesh conventions: hexahedra with trilinear geometry; element vertex
  * v = i + 2 j + 4 k sits at reference corner (i, j, k); every element's local
  * axes must agree with its neighbours' on shared edges and faces (the setup
@@ -74,7 +86,14 @@ enum {
 
 enum { DPG_BC_NONE = 0, DPG_BC_DIRICHLET = 1, DPG_BC_ROBIN = 2 };
 enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2 };
-enum { DPG_PREC_FP64 = 0 };
+/* Precision of the quadrature contractions M, C, P, Q (everything after them,
+ * G_K, B_K, the Cholesky factorisation, condensation and CG residuals, is
+ * FP64 in every mode).  FP64: FP64 FMA.  TF32: tcgen05 tensor cores, operands
+ * rounded to TF32, FP32 accumulation.  3XTF32: the same with each operand
+ * split as a = a_hi + a_lo (both TF32) and a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,
+ * about FP32 accuracy.  Reduced modes perturb G_K and B_K themselves; their
+ * error against FP64 is a reported quantity, not a parity bound. */
+enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
 enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4 };
 enum { DPG_FLAG_ADJOINT = 1 };
@@ -109,7 +128,7 @@ typedef struct {
   const double* vert;          /* n_vert x 3 */
   int32_t n_elem;
   const int32_t* elem;         /* n_elem x 8 vertex ids */
-  const int8_t* elem_p;        /* n_elem trial degree, 1..4 (uniform in this build) */
+  const int8_t* elem_p;        /* n_elem trial degree, 1..4 (may differ between elements) */
   const dpg_complex* elem_eps; /* n_elem relative permittivity, loss => Im > 0 */
   const dpg_complex* elem_mu;  /* n_elem relative permeability */
   const int8_t* face_bc;       /* n_elem x 6, DPG_BC_*; boundary faces only */
@@ -124,7 +143,7 @@ typedef struct {
   double omega;      /* dimensionless angular frequency (App. A, L = 1 m) */
   double alpha;      /* test-norm weight alpha of Eq. (test_inner_product), > 0 */
   int32_t dp;        /* enrichment, must be 1 in this build */
-  int32_t precision; /* DPG_PREC_FP64 */
+  int32_t precision; /* DPG_PREC_* */
   int32_t chunk;     /* elements per batched launch, 0 = automatic */
   int32_t flags;     /* DPG_FLAG_*: DPG_FLAG_ADJOINT keeps the M1 factors dpg_grad_eps needs */
 } dpg_params;
@@ -143,8 +162,9 @@ typedef struct {
  * unknowns that pair with nothing (Robin faces, end of Sec. 2.3), CSR pattern
  * of the condensed trace system, reference tables, and every device buffer.
  * Errors: DPG_ERR_ARG (null / out of range), DPG_ERR_MESH (bad ids,
- * inconsistent orientation, non-positive Jacobian at a corner, dp != 1,
- * mixed p), DPG_ERR_NOMEM, DPG_ERR_CUDA.  On error *h is NULL.
+ * inconsistent orientation, non-positive Jacobian at a corner, p outside
+ * 1..4), DPG_ERR_UNSUPPORTED (dp != 1), DPG_ERR_NOMEM, DPG_ERR_CUDA.
+ * On error *h is NULL.
  * Synchronises the stream before returning. */
 int dpg_setup_mesh(dpg_handle** h, const dpg_mesh_desc* mesh, const dpg_params* prm, dpg_stream s);
 
@@ -169,7 +189,8 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * system (Sec. 2.3 end): x0 = 0, stop when ||r|| <= max(rtol ||b||, atol).
  * mode DPG_CG_FP64: plain FP64 CG (the paper's solver).  DPG_CG_IR_FP32:
  * iterative refinement, FP64 residuals and updates around FP32 inner CG
- * solves on an FP32 copy of the matrix (inner relative tolerance inner_rtol).
+ * solves on an FP32 copy of the matrix (inner relative tolerance inner_rtol;
+ * about 1e-3 is fastest on the waveguide cases).
  * DPG_CG_JACOBI or DPG_CG_BLOCK_JACOBI may be or-ed to either: diagonal
  * preconditioning z = D^{-1} r, or the inverses of the entity diagonal blocks
  * (each mesh entity's E-hat and H-hat unknowns together).  The paper leaves
@@ -186,7 +207,9 @@ int dpg_cg_solve(dpg_handle* h, int32_t mode, double rtol, double atol, int32_t 
 
 /* Local recovery and residual estimator (Sec. 2.3): for the trace solution
  * xhat (device, n complex) compute per element u_K = M1^{-1}(M4 l - M2 uhat_K)
- * (u: device, n_elem x n_u complex, element-local order above, may be NULL)
+ * (u: device, element e's n_u(e) complex values at the offset u_off[e] of
+ * dpg_element_layout, n_elem x n_u for one degree; element-local order above;
+ * may be NULL)
  * and eta_K = ||Psi_K||_V with Psi_K = G^{-1}(l - B u - B-hat uhat)
  * (eta: device, n_elem doubles, may be NULL), evaluated as the minimum of the
  * element's residual quadratic, eta_K^2 = c_K - 2 Re(uhat^H s_K) + uhat^H S_K uhat.
@@ -230,8 +253,16 @@ typedef struct {
   int64_t kernel_launches;   /* kernels launched by the library since enable */
   double factor_ms_real;     /* part of factor_ms spent on real-path launches */
   int64_t factor_elements_real;
+  double cg_kernel_ms;       /* summed device time of the persistent CG kernel launches */
+  int64_t cg_kernel_launches;
+  int64_t cg_kernel_iterations;
 } dpg_timing;
 int dpg_timing_enable(dpg_handle* h, int32_t enable);
+
+/* Algorithmic bytes moved by one CG iteration of the given mode (matrix values,
+ * per-entity column lists, preconditioner data and vector traffic), for
+ * roofline reporting.  Host only. */
+int dpg_cg_bytes_per_iteration(dpg_handle* h, int32_t mode, int64_t* bytes);
 
 /* Real path for lossless elements (default on).  An element with real eps
  * and mu and no Robin face has an augmented system that the unitary diagonal
@@ -258,20 +289,56 @@ int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle
                  double* dP_deps_re, double* dP_deps_im, int32_t cg_mode, double cg_rtol, int32_t max_iter,
                  dpg_stream s);
 
-/* Sizes: n = free trace unknowns, nnz of the CSR matrix, per-element sizes. */
+/* The element pass runs as a fixed launch plan: per trial degree and
+ * arithmetic class (real path / complex), chunks of at most that degree's
+ * chunk size.  The plan (device element lists, Robin face sub-batches) is
+ * built on the first dpg_element_batch and captured into a CUDA graph that
+ * later passes replay (enable = 0: plain launches, no graph).  A change of
+ * chunk sizes, real-path switch or element classes rebuilds it. */
+int dpg_set_graph(dpg_handle* h, int32_t enable);
+
+/* Chunk-size autotuner (the paper has no counterpart; it serves the batched
+ * element pass): per trial-degree group, time one chunk of the group's larger
+ * arithmetic class at candidate sizes (multiples of the SM count whose chunk
+ * workspace fits max_workspace_bytes) and keep the fastest per element; the
+ * workspace is then reallocated for the chosen sizes.  caps (host out, one per
+ * group, may be NULL): chosen chunk sizes; ms_per_element (host out, may be
+ * NULL): their measured time per element.  Overwrites the element stores of
+ * the timed elements (run dpg_element_batch afterwards).  Synchronises.
+ * Errors: DPG_ERR_ARG, DPG_ERR_NOMEM, DPG_ERR_CUDA. */
+int dpg_autotune(dpg_handle* h, double max_workspace_bytes, int32_t* caps, float* ms_per_element, dpg_stream s);
+
+/* Order groups (host out, each may be NULL; arrays of length *n_groups <= 4):
+ * trial degree, number of elements and current chunk size of each group,
+ * ascending degree. */
+int dpg_group_info(dpg_handle* h, int32_t* n_groups, int32_t* p, int32_t* n_elem, int32_t* cap);
+
+/* Sizes: n = free trace unknowns, nnz of the CSR matrix, per-element sizes
+ * (the largest over the elements when the degrees differ). */
 int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_elem, int32_t* n_v,
               int32_t* n_u, int32_t* n_h);
 
-/* Element-local to global trace map (host out, n_elem x n_h int32):
- * >= 0 free unknown index, -1 fixed by Dirichlet data, -2 removed (unpaired H-hat).
- * fixed_val (host out, n_elem x n_h complex, may be NULL): value of fixed
+/* Per-element layout (host out, each may be NULL): p (n_elem trial degrees),
+ * u_off (n_elem + 1): offset of element e's interior values in the u vector of
+ * dpg_estimate, u_off[n_elem] = its length; h_off (n_elem + 1): offset of
+ * element e's entries in the trace map, h_off[n_elem] = its length.  For one
+ * degree u_off[e] = e n_u and h_off[e] = e n_h. */
+int dpg_element_layout(dpg_handle* h, int8_t* p, int64_t* u_off, int64_t* h_off);
+
+/* Element-local to global trace map (host out, h_off[n_elem] int32, element
+ * e's n_h(e) entries at h_off[e]): >= 0 free unknown index, -1 fixed by
+ * Dirichlet data, -2 removed (unpaired H-hat) or unused slot (mixed degrees).
+ * fixed_val (host out, same layout, complex, may be NULL): value of fixed
  * entries (0 elsewhere). */
 int dpg_trace_map(dpg_handle* h, int32_t* map, dpg_complex* fixed_val);
 
-/* Debug dump for parity tests: for n_ids element ids (host) write into host
- * buffers (each may be NULL) G (n_v x n_v, row-major), B (n_v x n_u),
- * B-hat (n_v x n_h), l (n_v), S (n_h x n_h), s (n_h).  Runs the element
- * formation and condensation for those elements only; synchronises. */
+/* Debug dump for parity tests: for n_ids element ids (host) of one trial
+ * degree write into host buffers (each may be NULL) G (n_v x n_v, row-major),
+ * B (n_v x n_u), B-hat (n_v x n_h), l (n_v), S (n_h x n_h), s (n_h), with the
+ * sizes of that degree (S, s in the element's trace slots, see above).  Runs
+ * the element formation and condensation for those elements only;
+ * synchronises.  Errors: DPG_ERR_ARG for ids out of range or of different
+ * degrees. */
 int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids, dpg_complex* G,
                      dpg_complex* B, dpg_complex* Bh, dpg_complex* l, dpg_complex* S,
                      dpg_complex* s, dpg_stream st);
@@ -280,6 +347,16 @@ int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids, dpg_compl
  * row_ptr (n + 1 int64), col (nnz int32), val (nnz complex), b (n complex). */
 int dpg_csr_copy(dpg_handle* h, int64_t* row_ptr, int32_t* col, dpg_complex* val,
                  dpg_complex* b, dpg_stream s);
+
+/* Check hook of the tensor-core contraction: C (Ma x Nb, row-major) = A^T B
+ * with A (Kd x Ma) and B (Kd x Nb) row-major FP64 host arrays, computed on the
+ * current device by the kernel the TF32 (split = 1) or 3XTF32 (split = 3)
+ * precision modes use.  upper_only != 0 computes only the 128 x 128 tiles on or
+ * above the diagonal (the rest of C is left untouched).  Synchronous.
+ * Errors: DPG_ERR_ARG, DPG_ERR_NOMEM, DPG_ERR_TIMEOUT (a bounded wait gave up),
+ * DPG_ERR_CUDA. */
+int dpg_tc_gemm(int32_t split, int32_t Ma, int32_t Nb, int32_t Kd, const double* A, const double* B, double* C,
+                int32_t upper_only);
 
 /* Device FP64 and FP32 fused-multiply-add throughput (FLOP/s) measured by a
  * short probe kernel on the current device (used to state roofline peaks). */

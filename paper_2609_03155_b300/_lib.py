@@ -18,6 +18,7 @@ ERRORS = {-1: "DPG_ERR_ARG", -2: "DPG_ERR_MESH", -3: "DPG_ERR_NOMEM", -4: "DPG_E
 DPG_BC_NONE, DPG_BC_DIRICHLET, DPG_BC_ROBIN = 0, 1, 2
 DPG_PASS_ASSEMBLE = 0
 DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI, DPG_CG_BLOCK_JACOBI = 0, 1, 2, 4
+DPG_PREC_FP64, DPG_PREC_TF32, DPG_PREC_3XTF32 = 0, 1, 2
 DPG_FLAG_ADJOINT = 1
 
 
@@ -57,7 +58,9 @@ class dpg_cg_report(C.Structure):
 class dpg_timing(C.Structure):
     _fields_ = [("factor_ms", C.c_double), ("factor_launches", C.c_int64), ("factor_elements", C.c_int64),
                 ("cg_ms", C.c_double), ("cg_iterations", C.c_int64), ("kernel_launches", C.c_int64),
-                ("factor_ms_real", C.c_double), ("factor_elements_real", C.c_int64)]
+                ("factor_ms_real", C.c_double), ("factor_elements_real", C.c_int64),
+                ("cg_kernel_ms", C.c_double), ("cg_kernel_launches", C.c_int64),
+                ("cg_kernel_iterations", C.c_int64)]
 
 
 class DPGError(RuntimeError):
@@ -87,6 +90,11 @@ def lib():
     L.dpg_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                             C.POINTER(i32)]
     L.dpg_trace_map.argtypes = [vp, vp, vp]
+    L.dpg_element_layout.argtypes = [vp, vp, vp, vp]
+    L.dpg_tc_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, i32]
+    L.dpg_set_graph.argtypes = [vp, i32]
+    L.dpg_autotune.argtypes = [vp, dbl, vp, vp, vp]
+    L.dpg_group_info.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_element_dump.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.dpg_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp]
     L.dpg_probe_peaks.argtypes = [C.POINTER(dbl), C.POINTER(dbl), vp]
@@ -94,6 +102,7 @@ def lib():
     L.dpg_grad_eps.argtypes = [vp, vp, vp, C.POINTER(dbl), vp, vp, i32, dbl, i32, vp]
     L.dpg_timing_enable.argtypes = [vp, i32]
     L.dpg_set_real_path.argtypes = [vp, i32]
+    L.dpg_cg_bytes_per_iteration.argtypes = [vp, i32, C.POINTER(i64)]
     L.dpg_timing_get.argtypes = [vp, C.POINTER(dpg_timing)]
     L.dpg_last_error.argtypes = [vp]
     L.dpg_last_error.restype = C.c_char_p
@@ -103,7 +112,8 @@ def lib():
                  "dpg_estimate_noalloc",
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
                  "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps",
-                 "dpg_set_real_path"):
+                 "dpg_set_real_path", "dpg_cg_bytes_per_iteration", "dpg_element_layout", "dpg_tc_gemm", "dpg_set_graph", "dpg_autotune",
+                 "dpg_group_info"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

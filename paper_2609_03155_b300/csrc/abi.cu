@@ -11,8 +11,16 @@ static cudaStream_t S_(dpg_stream s) { return reinterpret_cast<cudaStream_t>(s);
 static thread_local std::string g_setup_err;
 
 static void free_all(dpg_handle* h) {
-  void* bufs[] = {h->d_X,     h->d_eps,   h->d_mu,   h->d_fbc,   h->d_Xref,  h->d_Tf,   h->d_Tall,
-                  h->d_trfun, h->d_l2g,   h->d_xfix, h->d_color_elems, h->d_robin, h->d_status, h->d_S,
+  free_plan(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
+  for (Group& G : h->grp) {
+    void* gb[] = {G.d_Xref, G.d_Tf, G.d_Tall, G.d_trfun, G.d_elems, G.d_color_elems};
+    for (void* b : gb)
+      if (b) cudaFree(b);
+  }
+  void* bufs[] = {h->d_X,     h->d_eps,   h->d_mu,   h->d_fbc,   h->d_off,   h->d_sig,  h->d_rsig,
+                  h->d_rint,  h->d_l2g,   h->d_xfix, h->d_rdbl,  h->d_robin, h->d_status, h->d_S,
                   h->d_s,     h->d_c,     h->d_Z,    h->d_z,     h->d_rowptr, h->d_row2blk, h->d_val,
                   h->d_b,     h->d_val32, h->d_r,    h->d_p,     h->d_Ap,    h->d_r32,  h->d_p32,
                   h->d_Ap32,  h->d_x32,   h->d_red,  h->d_cgstate,  h->ws.K,    h->ws.V,   h->ws.Cu,
@@ -32,18 +40,11 @@ extern "C" int dpg_setup_mesh(dpg_handle** out, const dpg_mesh_desc* m, const dp
   cudaStream_t s = S_(st);
   int rc = build_mesh(h, m, prm, s);
   if (rc == DPG_OK) {
-    const Sizes& S = h->sz;
-    size_t per = sizeof(double2) * (size_t)S.N * S.N + sizeof(double) * 3 * (size_t)S.nq * (2 * S.n_f + 3 * S.nL) +
-                 sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL);
-    size_t budget = (size_t)12 << 30;
-    int cap = (int)std::max<size_t>(1, budget / per);
-    if (prm->chunk > 0) cap = prm->chunk;
-    if (cap >= 148 && prm->chunk <= 0) cap = cap / 148 * 148;
-    cap = std::min(cap, h->ne);
-    cap = std::max(cap, 1);
-    rc = alloc_workspace(h, cap);
-    if (rc == DPG_OK) rc = compute_reference_matrices(h, s);
+    set_default_caps(h, prm->chunk);
+    rc = alloc_workspace(h);
   }
+  if (rc == DPG_OK) rc = init_kernel_attributes(h);
+  for (int g = 0; rc == DPG_OK && g < (int)h->grp.size(); ++g) rc = compute_reference_matrices(h, g, s);
   if (rc != DPG_OK) {
     // keep the message on a static buffer for dpg_last_error(NULL)
     free_all(h);
@@ -62,56 +63,42 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
     return DPG_ERR_ARG;
   }
   cudaStream_t s = S_(st);
-  const int cap = h->ws.cap;
-  // lossless elements in real arithmetic, the others in complex arithmetic
-  std::vector<int> all;
-  const std::vector<int>* lists[2];
-  if (h->allow_real) {
-    lists[0] = &h->real_elems;
-    lists[1] = &h->cplx_elems;
-  } else {
-    all.resize(h->ne);
-    for (int e = 0; e < h->ne; ++e) all[e] = e;
-    lists[0] = &all;
-    lists[1] = nullptr;
-  }
-  for (int li = 0; li < 2; ++li) {
-    if (!lists[li]) continue;
-    const std::vector<int>& L = *lists[li];
-    const bool real = h->allow_real && li == 0;
-    for (size_t c0 = 0; c0 < L.size(); c0 += cap) {
-      const int cnt = (int)std::min<size_t>(cap, L.size() - c0);
-      int rc = run_element_chunk(h, L.data() + c0, cnt, s, true, true, real);
-      if (rc) return rc;
-    }
-  }
+  // the launch plan of every order group (lossless elements in real
+  // arithmetic, the others in complex arithmetic), replayed as a CUDA graph
+  int rc = element_pass(h, s);
+  if (rc) return rc;
   h->have_elements = true;
   h->have_system = false;
   // pivot check
   std::vector<int> status(h->ne);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(status.data(), h->d_status, sizeof(int) * h->ne, cudaMemcpyDeviceToHost, s));
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
-  for (size_t k = 0; k < h->factor_events.size(); ++k) {
-    float ms = 0;
-    cudaEventElapsedTime(&ms, h->factor_events[k].first, h->factor_events[k].second);
-    h->factor_ms += ms;
-    h->factor_launches += 1;
-    h->factor_elements += h->factor_counts[k];
-    if (h->factor_real[k]) {
-      h->factor_ms_real += ms;
-      h->factor_elements_real += h->factor_counts[k];
+  if (h->timing) {
+    for (const ChunkPlan& cp : h->plan) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, cp.ev0, cp.ev1);
+      h->factor_ms += ms;
+      h->factor_launches += 1;
+      h->factor_elements += cp.count;
+      if (cp.real) {
+        h->factor_ms_real += ms;
+        h->factor_elements_real += cp.count;
+      }
     }
-    cudaEventDestroy(h->factor_events[k].first);
-    cudaEventDestroy(h->factor_events[k].second);
   }
-  h->factor_events.clear();
-  h->factor_counts.clear();
-  h->factor_real.clear();
   for (int e = 0; e < h->ne; ++e)
     if (status[e]) {
       h->err = "non-positive pivot in element " + std::to_string(e);
       return DPG_ERR_NOT_HPD;
     }
+  if (h->prec != DPG_PREC_FP64) {
+    int terr = 0;
+    DPG_CUDA_TRY(h, cudaMemcpy(&terr, h->d_status + h->ne, sizeof(int), cudaMemcpyDeviceToHost));
+    if (terr) {
+      h->err = "a tensor-core contraction gave up waiting for its MMAs";
+      return DPG_ERR_TIMEOUT;
+    }
+  }
   return DPG_OK;
 }
 
@@ -159,9 +146,20 @@ extern "C" int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_ele
   if (n) *n = h->n;
   if (nnz) *nnz = h->nnz;
   if (n_elem) *n_elem = h->ne;
-  if (n_v) *n_v = h->sz.n_v;
-  if (n_u) *n_u = h->sz.n_u;
-  if (n_h) *n_h = h->sz.n_h;
+  if (n_v) *n_v = h->szmax.n_v;
+  if (n_u) *n_u = h->szmax.n_u;
+  if (n_h) *n_h = h->szmax.n_h;
+  return DPG_OK;
+}
+
+extern "C" int dpg_element_layout(dpg_handle* h, int8_t* p, int64_t* u_off, int64_t* h_off) {
+  if (!h) return DPG_ERR_ARG;
+  for (int e = 0; e < h->ne; ++e)
+    if (p) p[e] = (int8_t)h->grp[h->elem_grp[e]].p;
+  for (int e = 0; e <= h->ne; ++e) {
+    if (u_off) u_off[e] = h->off[e].u;
+    if (h_off) h_off[e] = h->off[e].h;
+  }
   return DPG_OK;
 }
 
@@ -177,17 +175,24 @@ extern "C" int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids
                                 dpg_complex* Bh, dpg_complex* l, dpg_complex* Sout, dpg_complex* sout, dpg_stream st) {
   if (!h || !ids || n_ids <= 0) return DPG_ERR_ARG;
   cudaStream_t s = S_(st);
-  const Sizes& S = h->sz;
-  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h;
   for (int k = 0; k < n_ids; ++k)
     if (ids[k] < 0 || ids[k] >= h->ne) {
       h->err = "element id out of range";
       return DPG_ERR_ARG;
     }
+  const int g = h->elem_grp[ids[0]];
+  for (int k = 0; k < n_ids; ++k)
+    if (h->elem_grp[ids[k]] != g) {
+      h->err = "dpg_element_dump: the elements must share one trial degree";
+      return DPG_ERR_ARG;
+    }
+  const Sizes& S = h->grp[g].sz;
+  const int cap = h->grp[g].cap;
+  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h;
   std::vector<double2> Kh((size_t)N * N);
-  for (int k0 = 0; k0 < n_ids; k0 += h->ws.cap) {
-    const int cnt = std::min(h->ws.cap, n_ids - k0);
-    int rc = run_element_chunk(h, ids + k0, cnt, s, false, false);
+  for (int k0 = 0; k0 < n_ids; k0 += cap) {
+    const int cnt = std::min(cap, n_ids - k0);
+    int rc = run_element_chunk(h, g, ids + k0, cnt, s, false, false);
     if (rc) return rc;
     for (int k = 0; k < cnt; ++k) {
       DPG_CUDA_TRY(h, cudaMemcpyAsync(Kh.data(), h->ws.K + (size_t)k * N * N, sizeof(double2) * N * N,
@@ -223,20 +228,20 @@ extern "C" int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids
       std::vector<int> re, cx;
       for (int k = 0; k < cnt; ++k) (h->allow_real && h->is_real[ids[k0 + k]] ? re : cx).push_back(ids[k0 + k]);
       if (!re.empty()) {
-        rc = run_element_chunk(h, re.data(), (int)re.size(), s, true, true, true);
+        rc = run_element_chunk(h, g, re.data(), (int)re.size(), s, true, true, true);
         if (rc) return rc;
       }
       if (!cx.empty()) {
-        rc = run_element_chunk(h, cx.data(), (int)cx.size(), s, true, true, false);
+        rc = run_element_chunk(h, g, cx.data(), (int)cx.size(), s, true, true, false);
         if (rc) return rc;
       }
       for (int k = 0; k < cnt; ++k) {
         const size_t q = (size_t)(k0 + k);
         if (Sout)
-          DPG_CUDA_TRY(h, cudaMemcpyAsync(Sout + q * nh * nh, h->d_S + (size_t)ids[k0 + k] * nh * nh,
+          DPG_CUDA_TRY(h, cudaMemcpyAsync(Sout + q * nh * nh, h->d_S + h->off[ids[k0 + k]].S,
                                           sizeof(double2) * nh * nh, cudaMemcpyDeviceToHost, s));
         if (sout)
-          DPG_CUDA_TRY(h, cudaMemcpyAsync(sout + q * nh, h->d_s + (size_t)ids[k0 + k] * nh, sizeof(double2) * nh,
+          DPG_CUDA_TRY(h, cudaMemcpyAsync(sout + q * nh, h->d_s + h->off[ids[k0 + k]].h, sizeof(double2) * nh,
                                           cudaMemcpyDeviceToHost, s));
       }
       DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -324,6 +329,39 @@ extern "C" int dpg_probe_peaks(double* fp64, double* fp32, dpg_stream st) {
   return DPG_OK;
 }
 
+extern "C" int dpg_tc_gemm(int32_t split, int32_t Ma, int32_t Nb, int32_t Kd, const double* A, const double* B,
+                           double* C, int32_t upper_only) {
+  if ((split != 1 && split != 3) || Ma <= 0 || Nb <= 0 || Kd <= 0 || !A || !B || !C) return DPG_ERR_ARG;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  int* derr = nullptr;
+  const size_t nA = (size_t)Kd * Ma, nB = (size_t)Kd * Nb, nC = (size_t)Ma * Nb;
+  if (cudaMalloc(&dA, nA * 8) != cudaSuccess || cudaMalloc(&dB, nB * 8) != cudaSuccess ||
+      cudaMalloc(&dC, nC * 8) != cudaSuccess || cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dC);
+    cudaFree(derr);
+    return DPG_ERR_NOMEM;
+  }
+  int rc = tc_init(), herr = 0;
+  if (rc == DPG_OK && (cudaMemcpy(dA, A, nA * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dB, B, nB * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dC, C, nC * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(derr, 0, sizeof(int)) != cudaSuccess))
+    rc = DPG_ERR_CUDA;
+  if (rc == DPG_OK) rc = gemm_tn_tc(split, Ma, Nb, Kd, dA, Ma, 0, dB, Nb, 0, dC, Nb, 0, 1, upper_only, derr, nullptr);
+  if (rc == DPG_OK && cudaDeviceSynchronize() != cudaSuccess) rc = DPG_ERR_CUDA;
+  if (rc == DPG_OK && cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = DPG_ERR_CUDA;
+  if (rc == DPG_OK && herr) rc = DPG_ERR_TIMEOUT;
+  if (rc == DPG_OK && cudaMemcpy(C, dC, nC * 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = DPG_ERR_CUDA;
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dC);
+  cudaFree(derr);
+  return rc;
+}
+
 extern "C" int dpg_update_elements(dpg_handle* h, const double* corners, const dpg_complex* eps, const dpg_complex* mu,
                                    dpg_stream st) {
   if (!h) return DPG_ERR_ARG;
@@ -335,12 +373,15 @@ extern "C" int dpg_update_elements(dpg_handle* h, const double* corners, const d
   if (eps || mu) {  // re-classify lossless elements (host copies read now)
     if (eps) h->eps_host.assign(eps, eps + h->ne);
     if (mu) h->mu_host.assign(mu, mu + h->ne);
-    h->real_elems.clear();
-    h->cplx_elems.clear();
+    bool changed = false;
     for (int e = 0; e < h->ne; ++e) {
-      const bool real = h->eps_host[e].im == 0.0 && h->mu_host[e].im == 0.0 && !h->robin_face[e];
-      h->is_real[e] = real;
-      (real ? h->real_elems : h->cplx_elems).push_back(e);
+      const char r = h->eps_host[e].im == 0.0 && h->mu_host[e].im == 0.0 && !h->robin_face[e];
+      changed |= r != h->is_real[e];
+      h->is_real[e] = r;
+    }
+    if (changed) {
+      classify_elements(h);
+      h->plan_valid = false;  // the real / complex chunks change
     }
   }
   h->have_elements = false;
@@ -351,14 +392,48 @@ extern "C" int dpg_update_elements(dpg_handle* h, const double* corners, const d
 extern "C" int dpg_timing_enable(dpg_handle* h, int32_t enable) {
   if (!h) return DPG_ERR_ARG;
   h->timing = enable != 0;
-  h->factor_ms = h->cg_ms = h->factor_ms_real = 0;
+  h->factor_ms = h->cg_ms = h->factor_ms_real = h->cgk_ms = 0;
   h->factor_launches = h->factor_elements = h->cg_iters = h->launches = h->factor_elements_real = 0;
+  h->cgk_launches = h->cgk_iters = 0;
+  return DPG_OK;
+}
+
+extern "C" int dpg_cg_bytes_per_iteration(dpg_handle* h, int32_t mode, int64_t* bytes) {
+  if (!h || !bytes) return DPG_ERR_ARG;
+  *bytes = cg_bytes_per_iteration(h, mode);
   return DPG_OK;
 }
 
 extern "C" int dpg_set_real_path(dpg_handle* h, int32_t enable) {
   if (!h) return DPG_ERR_ARG;
+  if (h->allow_real != (enable != 0)) h->plan_valid = false;
   h->allow_real = enable != 0;
+  return DPG_OK;
+}
+
+extern "C" int dpg_set_graph(dpg_handle* h, int32_t enable) {
+  if (!h) return DPG_ERR_ARG;
+  h->use_graph = enable != 0;
+  return DPG_OK;
+}
+
+extern "C" int dpg_autotune(dpg_handle* h, double max_workspace_bytes, int32_t* caps, float* ms_per_element,
+                            dpg_stream st) {
+  if (!h || !(max_workspace_bytes > 0)) return DPG_ERR_ARG;
+  int rc = autotune(h, max_workspace_bytes, caps, ms_per_element, S_(st));
+  h->have_elements = false;
+  h->have_system = false;
+  return rc;
+}
+
+extern "C" int dpg_group_info(dpg_handle* h, int32_t* n_groups, int32_t* p, int32_t* n_elem, int32_t* cap) {
+  if (!h) return DPG_ERR_ARG;
+  if (n_groups) *n_groups = (int32_t)h->grp.size();
+  for (size_t g = 0; g < h->grp.size(); ++g) {
+    if (p) p[g] = h->grp[g].p;
+    if (n_elem) n_elem[g] = (int32_t)h->grp[g].elems.size();
+    if (cap) cap[g] = h->grp[g].cap;
+  }
   return DPG_OK;
 }
 
@@ -372,6 +447,9 @@ extern "C" int dpg_timing_get(dpg_handle* h, dpg_timing* out) {
   out->kernel_launches = h->launches;
   out->factor_ms_real = h->factor_ms_real;
   out->factor_elements_real = h->factor_elements_real;
+  out->cg_kernel_ms = h->cgk_ms;
+  out->cg_kernel_launches = h->cgk_launches;
+  out->cg_kernel_iterations = h->cgk_iters;
   return DPG_OK;
 }
 

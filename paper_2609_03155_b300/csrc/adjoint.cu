@@ -41,20 +41,22 @@ __device__ __forceinline__ double2 gather_trace(const int32_t* l2g, const double
 // zg = M1^{-1} g_u (through the stored Cholesky factor L1 of M1) and the
 // condensed adjoint load gc = -Z^H g_u.  Elements outside the obstacle get zeros.
 __global__ void __launch_bounds__(256) k_adj_source(const __grid_constant__ Tables T, Sizes S, double omega,
+                                                    const int* __restrict__ elems, const ElemOff* __restrict__ off,
                                                     const double* __restrict__ Xall, const double2* __restrict__ eps_all,
                                                     const uint8_t* __restrict__ mask, const double2* __restrict__ u,
                                                     const double2* __restrict__ L1st, const double2* __restrict__ Zst,
                                                     double2* zg, double2* gc, double* Pk, double* ek) {
   extern __shared__ double2 sh[];
-  const int e = blockIdx.x;
+  const int e = elems[blockIdx.x];
+  const ElemOff of = off[e];
   const int nu = S.n_u, nh = S.n_h, nL = S.nL, nq = S.nq, nq1 = S.nq1, p1 = S.p + 1;
   double2* g = sh;            // n_u
   double2* Eq = g + nu;       // 3 nq (E at the points, times w det J)
   __shared__ double sX[24];
   __shared__ double sred[8];
   if (!mask[e]) {
-    for (int t = threadIdx.x; t < nu; t += blockDim.x) zg[(size_t)e * nu + t] = make_double2(0.0, 0.0);
-    for (int t = threadIdx.x; t < nh; t += blockDim.x) gc[(size_t)e * nh + t] = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < nu; t += blockDim.x) zg[of.u + t] = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < nh; t += blockDim.x) gc[of.h + t] = make_double2(0.0, 0.0);
     if (threadIdx.x == 0) {
       Pk[e] = 0.0;
       ek[e] = 0.0;
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(256) k_adj_source(const __grid_constant__ Tabl
   }
   if (threadIdx.x < 24) sX[threadIdx.x] = Xall[(size_t)e * 24 + threadIdx.x];
   __syncthreads();
-  const double2* ue = u + (size_t)e * nu;
+  const double2* ue = u + of.u;
   // E(q) w det J
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     const int qi[3] = {q % nq1, (q / nq1) % nq1, q / (nq1 * nq1)};
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(256) k_adj_source(const __grid_constant__ Tabl
     Pk[e] = eps.y * half_w * tot;
   }
   // gc = -Z^H g  (Z: n_u x n_h row-major)
-  const double2* Ze = Zst + (size_t)e * nu * nh;
+  const double2* Ze = Zst + of.Z;
   for (int t = threadIdx.x; t < nh; t += blockDim.x) {
     double2 acc = make_double2(0.0, 0.0);
     for (int k = 0; k < nu; ++k) {
@@ -134,13 +136,13 @@ __global__ void __launch_bounds__(256) k_adj_source(const __grid_constant__ Tabl
       acc.x += z.x * gk.x + z.y * gk.y;  // conj(z) g
       acc.y += z.x * gk.y - z.y * gk.x;
     }
-    gc[(size_t)e * nh + t] = make_double2(-acc.x, -acc.y);
+    gc[of.h + t] = make_double2(-acc.x, -acc.y);
   }
   __syncthreads();
   // zg = L1^{-H} L1^{-1} g  (L1 row-major lower, n_u x n_u), one thread
   if (threadIdx.x == 0) {
-    const double2* L = L1st + (size_t)e * nu * nu;
-    double2* z = zg + (size_t)e * nu;
+    const double2* L = L1st + of.L1;
+    double2* z = zg + of.u;
     for (int i = 0; i < nu; ++i) {  // forward
       double2 v = g[i];
       for (int k = 0; k < i; ++k) {
@@ -165,13 +167,14 @@ __global__ void __launch_bounds__(256) k_adj_source(const __grid_constant__ Tabl
 }
 
 // rhs[g_i] += gc[e][i] for the elements of one colour (free entries only)
-__global__ void k_adj_scatter(int nh, const int* __restrict__ elems, const int32_t* __restrict__ l2g,
-                              const double2* __restrict__ gc, double2* rhs) {
+__global__ void k_adj_scatter(int nh, const int* __restrict__ elems, const ElemOff* __restrict__ off,
+                              const int32_t* __restrict__ l2g, const double2* __restrict__ gc, double2* rhs) {
   const int e = elems[blockIdx.x];
+  const int64_t o = off[e].h;
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
-    const int g = l2g[(size_t)e * nh + i];
+    const int g = l2g[o + i];
     if (g >= 0) {
-      const double2 v = gc[(size_t)e * nh + i];
+      const double2 v = gc[o + i];
       rhs[g].x += v.x;
       rhs[g].y += v.y;
     }
@@ -213,6 +216,9 @@ __device__ void block_sum2(double& a, double& b, double* red) {
 // Gradient of one element (one CTA).  K holds the formed augmented matrix with
 // its G block replaced by the Cholesky factor L (lower, column-major, ld N).
 __global__ void __launch_bounds__(256) k_adj_grad(Sizes S, double omega, const int* __restrict__ ids,
+                                                  const ElemOff* __restrict__ off, const int* __restrict__ sig,
+                                                  const RSig* __restrict__ rsig, const int32_t* __restrict__ rint,
+                                                  const double* __restrict__ rdbl,
                                                   const double2* __restrict__ eps_all, const double2* __restrict__ K,
                                                   const double* __restrict__ MC, const double* __restrict__ Xref,
                                                   const int32_t* __restrict__ l2g, const double2* __restrict__ xfix,
@@ -223,6 +229,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(Sizes S, double omega, const i
   extern __shared__ double2 sh[];
   const int slot = blockIdx.x;
   const int e = ids[slot];
+  const ElemOff of = off[e];
   const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h, nf = S.n_f, m = nu + nh, nL3 = 3 * S.nL;
   double2* w = sh;          // m
   double2* lm = w + m;      // m
@@ -231,15 +238,15 @@ __global__ void __launch_bounds__(256) k_adj_grad(Sizes S, double omega, const i
   __shared__ double red[16];
   const double2* A = K + (size_t)slot * N * N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // 1. w = (u, uhat), lambda = (zg - Z lambda_h, lambda_h)
+  // 1. w = (u, uhat), lambda = (zg - Z lambda_h, lambda_h), in the trace slots
   for (int t = threadIdx.x; t < nh; t += blockDim.x) {
-    const size_t k = (size_t)e * nh + t;
+    const size_t k = (size_t)of.h + t;
     w[nu + t] = gather_trace(l2g, xfix, xhat, k);
     lm[nu + t] = gather_trace(l2g, nullptr, lam, k);
   }
-  for (int t = threadIdx.x; t < nu; t += blockDim.x) w[t] = u[(size_t)e * nu + t];
+  for (int t = threadIdx.x; t < nu; t += blockDim.x) w[t] = u[of.u + t];
   __syncthreads();
-  const double2* Ze = Zst + (size_t)e * nu * nh;
+  const double2* Ze = Zst + of.Z;
   for (int i = wid; i < nu; i += nw) {
     double ar = 0.0, ai = 0.0;
     for (int j = lane; j < nh; j += 32) {
@@ -250,11 +257,39 @@ __global__ void __launch_bounds__(256) k_adj_grad(Sizes S, double omega, const i
     ar = a_wsum(ar);
     ai = a_wsum(ai);
     if (lane == 0) {
-      const double2 zgi = zg[(size_t)e * nu + i];
+      const double2 zgi = zg[of.u + i];
       lm[i] = make_double2(zgi.x - ar, zgi.y - ai);
     }
   }
   __syncthreads();
+  // restricted elements: element trace coefficients from the slots, uhat_K = R uhat
+  const int sg = sig[e];
+  if (sg >= 0) {
+    const RSig R = rsig[sg];
+    const int32_t* rp = rint + R.rptr;
+    const int32_t* ri = rint + R.ridx;
+    const double* rw = rdbl + R.rw;
+    const int nt = nh / 2;
+    for (int t = threadIdx.x; t < nh; t += blockDim.x) {
+      r[t] = w[nu + t];
+      bl[t] = lm[nu + t];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nh; t += blockDim.x) {
+      const int tt = t < nt ? t : t - nt, base = t < nt ? 0 : nt;
+      double2 aw = make_double2(0.0, 0.0), al = make_double2(0.0, 0.0);
+      for (int k = rp[tt]; k < rp[tt + 1]; ++k) {
+        const double2 x = r[base + ri[k]], y = bl[base + ri[k]];
+        aw.x = fma(rw[k], x.x, aw.x);
+        aw.y = fma(rw[k], x.y, aw.y);
+        al.x = fma(rw[k], y.x, al.x);
+        al.y = fma(rw[k], y.y, al.y);
+      }
+      w[nu + t] = aw;
+      lm[nu + t] = al;
+    }
+    __syncthreads();
+  }
   // 2. r = l - B_K w, bl = B_K lambda;  B_K[i][j] = conj(A[nv + j][i]), l_i = conj(A[N-1][i])
   for (int i = wid; i < nv; i += nw) {
     double rr = 0, ri = 0, br = 0, bi = 0;
@@ -333,7 +368,7 @@ __global__ void __launch_bounds__(256) k_adj_grad(Sizes S, double omega, const i
       pw.y += pv * w[k].y;
     }
     for (int k = 0; k < nf; ++k) {
-      const double mv = M[(size_t)k * nf + i];        // M symmetric
+      const double mv = M[(size_t)min(k, i) * nf + max(k, i)];  // M symmetric, upper triangle stored
       const double xt_ = Xref[(size_t)k * nf + i];    // (X^T)[i][k] = X[k][i]
       const double x_ = Xref[(size_t)i * nf + k];     // X[i][k]
       mp.x += mv * r[k].x;
@@ -406,12 +441,12 @@ int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_
     h->err = "bad dpg_grad_eps arguments";
     return DPG_ERR_ARG;
   }
-  const Sizes& S = h->sz;
   const size_t ne = h->ne;
+  const ElemOff tot = h->off[ne];
   int rc = 0;
-  rc |= ensure(h, (void**)&h->d_u, sizeof(double2) * ne * S.n_u);
-  rc |= ensure(h, (void**)&h->d_zg, sizeof(double2) * ne * S.n_u);
-  rc |= ensure(h, (void**)&h->d_gc, sizeof(double2) * ne * S.n_h);
+  rc |= ensure(h, (void**)&h->d_u, sizeof(double2) * tot.u);
+  rc |= ensure(h, (void**)&h->d_zg, sizeof(double2) * tot.u);
+  rc |= ensure(h, (void**)&h->d_gc, sizeof(double2) * tot.h);
   rc |= ensure(h, (void**)&h->d_Pk, sizeof(double) * (2 * ne + 1));
   rc |= ensure(h, (void**)&h->d_lam, sizeof(double2) * h->n);
   rc |= ensure(h, (void**)&h->d_rhs_adj, sizeof(double2) * h->n);
@@ -420,11 +455,17 @@ int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_
   if (rc) return rc;
   double* Pk = h->d_Pk;
   double* ekv = h->d_Pk + ne;
-  const size_t sh_src = sizeof(double2) * (S.n_u + 3 * (size_t)S.nq);
-  k_adj_source<<<(int)ne, 256, sh_src, s>>>(h->tab, S, h->omega, h->d_X, h->d_eps, mask, h->d_u, h->d_L1, h->d_Z,
-                                             h->d_zg, h->d_gc, Pk, ekv);
+  for (const Group& G : h->grp) {
+    const Sizes& S = G.sz;
+    const size_t sh_src = sizeof(double2) * (S.n_u + 3 * (size_t)S.nq);
+    if (sh_src > 48 * 1024)
+      DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_adj_source, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_src));
+    k_adj_source<<<(int)G.elems.size(), 256, sh_src, s>>>(G.tab, S, h->omega, G.d_elems, h->d_off, h->d_X, h->d_eps,
+                                                          mask, h->d_u, h->d_L1, h->d_Z, h->d_zg, h->d_gc, Pk, ekv);
+    h->launches += 1;
+  }
   k_sum_serial<<<1, 1024, 0, s>>>((int)ne, Pk, h->d_Pk + 2 * ne);
-  h->launches += 2;
+  h->launches += 1;
   DPG_CUDA_TRY(h, cudaGetLastError());
   if (P_host) {
     DPG_CUDA_TRY(h, cudaMemcpyAsync(P_host, h->d_Pk + 2 * ne, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -433,33 +474,37 @@ int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_
   if (!dre) return DPG_OK;
   // condensed adjoint load, colour by colour (deterministic)
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_rhs_adj, 0, sizeof(double2) * h->n, s));
-  const int ncol = (int)h->color_off.size() - 1;
-  for (int c = 0; c < ncol; ++c) {
-    const int cnt = h->color_off[c + 1] - h->color_off[c];
-    if (cnt == 0) continue;
-    k_adj_scatter<<<cnt, 256, 0, s>>>(S.n_h, h->d_color_elems + h->color_off[c], h->d_l2g, h->d_gc, h->d_rhs_adj);
-    h->launches += 1;
-  }
+  for (int c = 0; c < h->ncolor; ++c)
+    for (const Group& G : h->grp) {
+      const int cnt = G.color_off[c + 1] - G.color_off[c];
+      if (cnt == 0) continue;
+      k_adj_scatter<<<cnt, 256, 0, s>>>(G.sz.n_h, G.d_color_elems + G.color_off[c], h->d_off, h->d_l2g, h->d_gc,
+                                        h->d_rhs_adj);
+      h->launches += 1;
+    }
   dpg_cg_report rep{};
   rc = cg_solve(h, cg_mode, cg_rtol, 0.0, max_iter, 1e-4, h->d_lam, h->d_rhs_adj, &rep, s);
   if (rc) return rc;
   // gradient pass: re-form K, factor G only, evaluate the derivative terms
   Workspace& wsp = h->ws;
-  std::vector<int> ids(wsp.cap);
-  const size_t smem_grad = sizeof(double2) * (2 * (size_t)(S.n_u + S.n_h) + 2 * (size_t)S.n_v);
-  if (smem_grad > 48 * 1024)
-    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_adj_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_grad));
-  for (int c0 = 0; c0 < (int)ne; c0 += wsp.cap) {
-    const int cnt = std::min(wsp.cap, (int)ne - c0);
-    for (int k = 0; k < cnt; ++k) ids[k] = c0 + k;
-    rc = run_element_chunk(h, ids.data(), cnt, s, false, false);
-    if (rc) return rc;
-    rc = factor_gram_only(h, cnt, s);
-    if (rc) return rc;
-    k_adj_grad<<<cnt, 256, smem_grad, s>>>(S, h->omega, wsp.ids, h->d_eps, wsp.K, wsp.MC, h->d_Xref, h->d_l2g,
-                                           h->d_xfix, xhat, h->d_lam, h->d_u, h->d_zg, h->d_Z, ekv, mask, dre, dim);
-    h->launches += 1;
-    DPG_CUDA_TRY(h, cudaGetLastError());
+  for (int gi = 0; gi < (int)h->grp.size(); ++gi) {
+    const Group& G = h->grp[gi];
+    const Sizes& S = G.sz;
+    const size_t smem_grad = sizeof(double2) * (2 * (size_t)(S.n_u + S.n_h) + 2 * (size_t)S.n_v);
+    if (smem_grad > 48 * 1024)
+      DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_adj_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_grad));
+    for (size_t c0 = 0; c0 < G.elems.size(); c0 += G.cap) {
+      const int cnt = (int)std::min<size_t>(G.cap, G.elems.size() - c0);
+      rc = run_element_chunk(h, gi, G.elems.data() + c0, cnt, s, false, false);
+      if (rc) return rc;
+      rc = factor_gram_only(h, gi, cnt, s);
+      if (rc) return rc;
+      k_adj_grad<<<cnt, 256, smem_grad, s>>>(S, h->omega, wsp.ids, h->d_off, h->d_sig, h->d_rsig, h->d_rint,
+                                             h->d_rdbl, h->d_eps, wsp.K, wsp.MC, G.d_Xref, h->d_l2g, h->d_xfix, xhat,
+                                             h->d_lam, h->d_u, h->d_zg, h->d_Z, ekv, mask, dre, dim);
+      h->launches += 1;
+      DPG_CUDA_TRY(h, cudaGetLastError());
+    }
   }
   return DPG_OK;
 }

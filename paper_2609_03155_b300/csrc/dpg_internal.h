@@ -64,44 +64,102 @@ struct Workspace {
   int* rent = nullptr;       // rcap x 4 (elem slot, face, grp, elem id)
 };
 
+// Per-element offsets into the pooled element stores (in entries of each
+// array).  Elements of different trial degrees have different store sizes.
+struct ElemOff {
+  int64_t S;   // d_S: n_h x n_h
+  int64_t Z;   // d_Z: n_u x n_h
+  int64_t L1;  // d_L1: n_u x n_u
+  int64_t h;   // d_s, trace map, fixed values: n_h
+  int64_t u;   // d_z, interior solution u: n_u
+};
+
+// Trace restriction R_K of one signature (element degree and the orders of its
+// 18 entities), one field: element trace function j (rows) from the element's
+// trace-map slots t (columns).  Column- and row-compressed; offsets into the
+// handle's integer and double pools.
+struct RSig {
+  int nt;              // trace functions per field at the element's degree
+  int64_t cptr, cidx;  // column pointers (nt + 1, relative to cidx) and row indices
+  int64_t rptr, ridx;  // row pointers (nt + 1, relative to ridx) and column indices
+  int64_t cw, rw;      // weights of the two forms (double pool)
+};
+
+// One launch group of the element pass: elements of one degree and one
+// arithmetic class (real / complex), at most the group's chunk size.  The
+// element ids and the Robin face sub-batches live in device buffers built once,
+// so the whole pass is a fixed sequence of launches (captured as a CUDA graph).
+struct ChunkPlan {
+  int g = 0;
+  bool real = false;
+  bool restricted = false;     // some element needs the trace restriction
+  int64_t ids_off = 0;         // into d_plan_ids
+  int count = 0;
+  std::vector<int4> robin;     // sub-batches: (entries offset, entries, element list offset, elements) in d_plan_rent
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the factorisation (timing)
+};
+
+// Elements of one trial degree: sizes, tables, reference matrices.
+struct Group {
+  int p = 0;
+  Sizes sz{};
+  Tables tab{};
+  std::vector<int> elems;                 // global element ids
+  std::vector<int> real_elems, cplx_elems;
+  std::vector<int> color_off;             // elems sorted by colour: offsets per colour
+  std::vector<int> color_elems_host;      // the sorted list
+  int* d_color_elems = nullptr;           // the sorted list on the device
+  int* d_elems = nullptr;                 // elems on the device
+  double* d_Xref = nullptr;               // n_f x n_f  int curl psi_i . psi_j (metric free)
+  double* d_Tf = nullptr;                 // 6 x n_f x nt  int_f psi_i . (N x phi_t) (metric free)
+  double* d_Tall = nullptr;               // n_f x nt
+  int* d_trfun = nullptr;                 // nt packed trace functions
+  int cap = 0;                            // elements per chunk
+};
+
 }  // namespace dpg
 
 struct dpg_handle {
   std::string err;
-  dpg::Sizes sz{};
-  dpg::Tables tab{};
+  std::vector<dpg::Group> grp;    // one per trial degree present, ascending p
+  std::vector<int8_t> elem_grp;   // group of each element
+  dpg::Sizes szmax{};             // largest sizes over the groups
   int ne = 0;
+  int prec = DPG_PREC_FP64;       // quadrature contraction precision
   double omega = 0, alpha = 1;
   // host copies used by setup / dumps
   std::vector<dpg_robin_group> robin;
   std::vector<dpg_dirichlet_group> dirichlet;
   std::vector<dpg::RobinEntry> robin_entries;  // sorted by element
   std::vector<int> robin_first;                // per element: first entry index or -1
-  std::vector<int> color_off;                  // element ids sorted by colour: offsets
-  std::vector<int> color_elems;
+  int ncolor = 0;
   int64_t n = 0, nnz = 0;
-  std::vector<int32_t> l2g;                    // ne x n_h
+  std::vector<int32_t> l2g;                    // element-major, n_h(K) per element (offsets ElemOff::h)
+  std::vector<dpg::ElemOff> off;               // ne + 1 (the last holds the totals)
+  dpg::ElemOff* d_off = nullptr;
+  // trace restrictions of elements with a lower-order entity (-1: identity)
+  std::vector<int> elem_sig;
+  std::vector<dpg::RSig> rsig;
+  int* d_sig = nullptr;
+  dpg::RSig* d_rsig = nullptr;
+  int32_t* d_rint = nullptr;
+  double* d_rdbl = nullptr;
   // device buffers
   double* d_X = nullptr;        // ne x 24 corner coordinates
   double2* d_eps = nullptr;     // ne
   double2* d_mu = nullptr;      // ne
   int8_t* d_fbc = nullptr;      // ne x 6
-  double* d_Xref = nullptr;     // n_f x n_f  int curl psi_i . psi_j (metric free)
-  double* d_Tf = nullptr;       // 6 x n_f x nt  int_f psi_i . (N x phi_t) (metric free)
-  double* d_Tall = nullptr;     // n_f x nt
-  int* d_trfun = nullptr;       // nt packed trace functions
-  int32_t* d_l2g = nullptr;     // ne x n_h
-  double2* d_xfix = nullptr;    // ne x n_h
-  int* d_color_elems = nullptr; // ne
+  int32_t* d_l2g = nullptr;     // trace map (offsets ElemOff::h)
+  double2* d_xfix = nullptr;    // fixed trace values (offsets ElemOff::h)
   dpg_robin_group* d_robin = nullptr;
   int* d_status = nullptr;      // ne
-  // per-element stores
-  double2* d_S = nullptr;       // ne x n_h x n_h
-  double2* d_s = nullptr;       // ne x n_h
+  // per-element stores, pooled over the elements at the offsets in off
+  double2* d_S = nullptr;       // n_h x n_h   (R_K^H S_K R_K for restricted elements)
+  double2* d_s = nullptr;       // n_h
   double* d_c = nullptr;        // ne
-  double2* d_Z = nullptr;       // ne x n_u x n_h  (M1^{-1} M2)
-  double2* d_z = nullptr;       // ne x n_u        (M1^{-1} M4 l)
-  double2* d_L1 = nullptr;      // ne x n_u x n_u  Cholesky factor of M1 (only with DPG_FLAG_ADJOINT)
+  double2* d_Z = nullptr;       // n_u x n_h   (M1^{-1} M2, times R_K)
+  double2* d_z = nullptr;       // n_u         (M1^{-1} M4 l)
+  double2* d_L1 = nullptr;      // n_u x n_u   Cholesky factor of M1 (only with DPG_FLAG_ADJOINT)
   // adjoint scratch (allocated on the first dpg_grad_eps)
   double2 *d_u = nullptr, *d_zg = nullptr, *d_gc = nullptr, *d_lam = nullptr, *d_rhs_adj = nullptr;
   double* d_Pk = nullptr;
@@ -132,19 +190,28 @@ struct dpg_handle {
   float* d_dinv32 = nullptr;
   // instrumentation
   bool timing = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> factor_events;
-  std::vector<int> factor_counts;
-  std::vector<int> factor_real;
+  // launch plan of the element pass and its CUDA graph
+  std::vector<dpg::ChunkPlan> plan;
+  bool plan_valid = false;
+  int* d_plan_ids = nullptr;
+  int* d_plan_rent = nullptr;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false, graph_timing = false;
+  int64_t graph_launches = 0;
+  cudaStream_t cap_stream = nullptr;
   int64_t factor_elements_real = 0;
   double factor_ms_real = 0;
   // lossless elements (real eps and mu, no Robin face) take the real path
-  std::vector<int> real_elems, cplx_elems;
   std::vector<char> is_real;
   bool allow_real = true;
   std::vector<dpg_complex> eps_host, mu_host;
   std::vector<char> robin_face;
   double factor_ms = 0, cg_ms = 0;
   int64_t factor_launches = 0, factor_elements = 0, cg_iters = 0, launches = 0;
+  double cgk_ms = 0;              // persistent CG kernel launches
+  int64_t cgk_launches = 0, cgk_iters = 0;
+  bool cgk_fp32 = false;
   // CG scratch
   double2 *d_r = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_zv = nullptr, *d_d64 = nullptr;
   float2 *d_r32 = nullptr, *d_p32 = nullptr, *d_Ap32 = nullptr, *d_x32 = nullptr, *d_z32 = nullptr;
@@ -156,12 +223,23 @@ struct dpg_handle {
 namespace dpg {
 // setup.cpp
 int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cudaStream_t s);
+void classify_elements(dpg_handle* h);
 // element.cu
-int alloc_workspace(dpg_handle* h, int cap);
-int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor,
-                      bool extract, bool real = false);
-int compute_reference_matrices(dpg_handle* h, cudaStream_t s);
-int factor_gram_only(dpg_handle* h, int count, cudaStream_t s);
+void set_default_caps(dpg_handle* h, int chunk);
+int alloc_workspace(dpg_handle* h);
+int init_kernel_attributes(dpg_handle* h);
+int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s, bool factor,
+                      bool extract, bool real = false, const ChunkPlan* cp = nullptr);
+int build_plan(dpg_handle* h);
+void free_plan(dpg_handle* h);
+int element_pass(dpg_handle* h, cudaStream_t s);
+int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem, cudaStream_t s);
+int compute_reference_matrices(dpg_handle* h, int g, cudaStream_t s);
+int factor_gram_only(dpg_handle* h, int g, int count, cudaStream_t s);
+// quad_tc.cu
+int tc_init();
+int gemm_tn_tc(int split, int Ma, int Nb, int Kd, const double* A, int lda, long long sA, const double* B, int ldb,
+               long long sB, double* C, int ldc, long long sC, int batch, int upper_only, int* err, cudaStream_t s);
 // adjoint.cu
 int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_host, double* dre, double* dim,
              int cg_mode, double cg_rtol, int max_iter, cudaStream_t s);
@@ -171,6 +249,7 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
              double2* x, const double2* b, dpg_cg_report* rep, cudaStream_t s);
 int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
              cudaStream_t s);
+int64_t cg_bytes_per_iteration(const dpg_handle* h, int mode);
 int estimate_noalloc(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
                      cudaStream_t s);
 }  // namespace dpg

@@ -336,7 +336,7 @@ constexpr int GT = 64, GK = 16;
 
 __global__ void __launch_bounds__(256) k_gemm_tn(int Ma, int Nb, int Kd, const double* __restrict__ A, int lda, long long sA,
                                                  const double* __restrict__ B, int ldb, long long sB, double* C, int ldc,
-                                                 long long sC) {
+                                                 long long sC, int upper_only) {
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   const int b = blockIdx.z;
@@ -344,6 +344,8 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int Ma, int Nb, int Kd, const d
   const double* Bb = B + b * sB;
   double* Cb = C + b * sC;
   const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  // symmetric products: tiles strictly below the diagonal are never read
+  if (upper_only && n0 + GT <= m0) return;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[4][4];
 #pragma unroll
@@ -385,9 +387,9 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int Ma, int Nb, int Kd, const d
 }
 
 static void gemm_tn(int Ma, int Nb, int Kd, const double* A, int lda, long long sA, const double* B, int ldb,
-                    long long sB, double* C, int ldc, long long sC, int batch, cudaStream_t s) {
+                    long long sB, double* C, int ldc, long long sC, int batch, cudaStream_t s, int upper_only = 0) {
   dim3 grid((Nb + GT - 1) / GT, (Ma + GT - 1) / GT, batch);
-  k_gemm_tn<<<grid, 256, 0, s>>>(Ma, Nb, Kd, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  k_gemm_tn<<<grid, 256, 0, s>>>(Ma, Nb, Kd, A, lda, sA, B, ldb, sB, C, ldc, sC, upper_only);
 }
 
 // ------------------------------------------------------ build K matrix --
@@ -419,11 +421,14 @@ __global__ void __launch_bounds__(256) k_build_K(Sizes S, double omega, double a
     const int j = (int)(idx / N), i = (int)(idx - (size_t)j * N);
     double2 v = make_double2(0.0, 0.0);
     if (j < nv && i < nv) {
-      // M and C are symmetric: read [j][i] so that consecutive rows i coalesce
+      // M and C are symmetric and only their upper triangle (row <= col) is
+      // computed: read [min][max] (coalesced over rows i for the lower part of K)
       if (i < nf && j < nf) {
-        v.x = Cm[(size_t)j * nf + i] + a1 * M[(size_t)j * nf + i];
+        const size_t q = (size_t)min(i, j) * nf + max(i, j);
+        v.x = Cm[q] + a1 * M[q];
       } else if (i >= nf && j >= nf) {
-        v.x = Cm[(size_t)(j - nf) * nf + (i - nf)] + a2 * M[(size_t)(j - nf) * nf + (i - nf)];
+        const size_t q = (size_t)min(i - nf, j - nf) * nf + max(i - nf, j - nf);
+        v.x = Cm[q] + a2 * M[q];
       } else if (i >= nf) {
         // G_IF[i'][j] = -i w mu X[j][i'] - i w conj(eps) X[i'][j]
         const int ip = i - nf;
@@ -500,9 +505,11 @@ __global__ void __launch_bounds__(256) k_build_K_real(Sizes S, double omega, dou
     double v = 0.0;
     if (j < nv && i < nv) {
       if (i < nf && j < nf) {
-        v = Cm[(size_t)j * nf + i] + a1 * M[(size_t)j * nf + i];
+        const size_t q = (size_t)min(i, j) * nf + max(i, j);
+        v = Cm[q] + a1 * M[q];
       } else if (i >= nf && j >= nf) {
-        v = Cm[(size_t)(j - nf) * nf + (i - nf)] + a2 * M[(size_t)(j - nf) * nf + (i - nf)];
+        const size_t q = (size_t)min(i - nf, j - nf) * nf + max(i - nf, j - nf);
+        v = Cm[q] + a2 * M[q];
       } else if (i >= nf) {  // rows I, cols F: w (mu X[j][i'] + eps X[i'][j])
         const int ip = i - nf;
         v = omega * (mu * Xref[(size_t)j * nf + ip] + eps * Xref[(size_t)ip * nf + j]);
@@ -762,22 +769,25 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
 // ---------------------------------------------------------- extraction --
 // From the factored K of one element: S (n_h x n_h full), s, c, Z = M1^{-1} M2, z = M1^{-1} M4 l.
 __global__ void __launch_bounds__(256) k_extract(Sizes S, const int* __restrict__ ids, const double2* __restrict__ K,
-                                                 double2* Sst, double2* sst, double* cst, double2* Zst, double2* zst,
-                                                 double2* L1st) {
+                                                 const ElemOff* __restrict__ off, double2* Sst, double2* sst,
+                                                 double* cst, double2* Zst, double2* zst, double2* L1st) {
   const int slot = blockIdx.x;
   const int e = ids[slot];
+  const ElemOff of = off[e];
   const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h;
   const double2* A = K + (size_t)slot * N * N;
   const int o = nv + nu;  // first trace row
-  double2* Se = Sst + (size_t)e * nh * nh;
+  double2* Se = Sst + of.S;
+  sst += of.h;
+  zst += of.u;
   for (int t = threadIdx.x; t < nh * nh; t += blockDim.x) {
     int i = t / nh, j = t - i * nh;
     Se[t] = (i >= j) ? A[(size_t)(o + i) + (size_t)(o + j) * N] : cconj(A[(size_t)(o + j) + (size_t)(o + i) * N]);
   }
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) sst[(size_t)e * nh + t] = cconj(A[(size_t)(N - 1) + (size_t)(o + t) * N]);
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) sst[t] = cconj(A[(size_t)(N - 1) + (size_t)(o + t) * N]);
   if (threadIdx.x == 0) cst[e] = A[(size_t)(N - 1) + (size_t)(N - 1) * N].x;
   if (L1st) {  // Cholesky factor of M1 (row-major, lower; upper zero), kept for the adjoint
-    double2* Le = L1st + (size_t)e * nu * nu;
+    double2* Le = L1st + of.L1;
     for (int t = threadIdx.x; t < nu * nu; t += blockDim.x) {
       const int i = t / nu, j = t - i * nu;
       Le[t] = (i >= j) ? A[(size_t)(nv + i) + (size_t)(nv + j) * N] : make_double2(0.0, 0.0);
@@ -785,13 +795,13 @@ __global__ void __launch_bounds__(256) k_extract(Sizes S, const int* __restrict_
   }
   // Z: for each column t in [0, nh] (t = nh is the load) solve L1^H z = y with
   // y[u] = conj(A[o + t][nv + u]), L1[a][b] = A[nv + a][nv + b].
-  double2* Ze = Zst + (size_t)e * nu * nh;
+  double2* Ze = Zst + of.Z;
   for (int t = threadIdx.x; t <= nh; t += blockDim.x) {
     const int rowt = (t < nh) ? o + t : N - 1;
     for (int u = nu - 1; u >= 0; --u) {
       double2 v = cconj(A[(size_t)rowt + (size_t)(nv + u) * N]);
       for (int k = u + 1; k < nu; ++k) {
-        double2 zk = (t < nh) ? Ze[(size_t)k * nh + t] : zst[(size_t)e * nu + k];
+        double2 zk = (t < nh) ? Ze[(size_t)k * nh + t] : zst[k];
         // (L1^H)[u][k] = conj(L1[k][u])
         v = csub(v, cmul(cconj(A[(size_t)(nv + k) + (size_t)(nv + u) * N]), zk));
       }
@@ -799,7 +809,7 @@ __global__ void __launch_bounds__(256) k_extract(Sizes S, const int* __restrict_
       if (t < nh)
         Ze[(size_t)u * nh + t] = v;
       else
-        zst[(size_t)e * nu + u] = v;
+        zst[u] = v;
     }
   }
 }
@@ -816,24 +826,26 @@ __device__ __forceinline__ double2 phase_apply(double v, bool a_imag, bool b_ima
 }
 
 __global__ void __launch_bounds__(256) k_extract_real(Sizes S, const int* __restrict__ ids, const double* __restrict__ K,
-                                                      double2* Sst, double2* sst, double* cst, double2* Zst,
-                                                      double2* zst, double2* L1st, double* Zscratch) {
+                                                      const ElemOff* __restrict__ off, double2* Sst, double2* sst,
+                                                      double* cst, double2* Zst, double2* zst, double2* L1st,
+                                                      double* Zscratch) {
   const int slot = blockIdx.x;
   const int e = ids[slot];
+  const ElemOff of = off[e];
   const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h, nt = S.nt, nE = 3 * S.nL;
   const double* A = K + (size_t)slot * N * N;
   const int o = nv + nu;
-  double2* Se = Sst + (size_t)e * nh * nh;
+  double2* Se = Sst + of.S;
   for (int t = threadIdx.x; t < nh * nh; t += blockDim.x) {
     const int i = t / nh, j = t - i * nh;
     const double v = (i >= j) ? A[(size_t)(o + i) + (size_t)(o + j) * N] : A[(size_t)(o + j) + (size_t)(o + i) * N];
     Se[t] = phase_apply(v, i < nt, j < nt);
   }
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) sst[(size_t)e * nh + t] = make_double2(0.0, 0.0);
-  for (int t = threadIdx.x; t < nu; t += blockDim.x) zst[(size_t)e * nu + t] = make_double2(0.0, 0.0);
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) sst[of.h + t] = make_double2(0.0, 0.0);
+  for (int t = threadIdx.x; t < nu; t += blockDim.x) zst[of.u + t] = make_double2(0.0, 0.0);
   if (threadIdx.x == 0) cst[e] = 0.0;
   if (L1st) {
-    double2* Le = L1st + (size_t)e * nu * nu;
+    double2* Le = L1st + of.L1;
     for (int t = threadIdx.x; t < nu * nu; t += blockDim.x) {
       const int i = t / nu, j = t - i * nu;
       Le[t] = (i >= j) ? phase_apply(A[(size_t)(nv + i) + (size_t)(nv + j) * N], i < nE, j < nE)
@@ -850,40 +862,141 @@ __global__ void __launch_bounds__(256) k_extract_real(Sizes S, const int* __rest
     }
   }
   __syncthreads();
-  double2* Ze = Zst + (size_t)e * nu * nh;
+  double2* Ze = Zst + of.Z;
   for (int q = threadIdx.x; q < nu * nh; q += blockDim.x) {
     const int u = q / nh, t = q - u * nh;
     Ze[q] = phase_apply(Zr[q], u < nE, t < nt);
   }
 }
 
+// ----------------------------------------------------- trace restriction --
+// Elements with an entity of lower order than their own: the stored condensed
+// matrices become those of the element's trace slots, S <- R^T S R,
+// s <- R^T s, Z <- Z R, with R = diag(R1, R1) over the E-hat and H-hat halves
+// (R1 real, nt x nt, column-compressed).  The element's K slot serves as scratch
+// (N^2 >= n_h^2 + n_u n_h entries).
+__global__ void __launch_bounds__(256) k_restrict(int nt, int nu, const int* __restrict__ ids,
+                                                  const ElemOff* __restrict__ off, const int* __restrict__ sig,
+                                                  const RSig* __restrict__ rsig, const int32_t* __restrict__ rint,
+                                                  const double* __restrict__ rdbl, double2* Sst, double2* sst,
+                                                  double2* Zst, double2* scratch, size_t scratch_stride) {
+  extern __shared__ double2 s_in[];  // n_h
+  const int slot = blockIdx.x, e = ids[slot];
+  const int sg = sig[e];
+  if (sg < 0) return;
+  const RSig R = rsig[sg];
+  const int32_t* cp = rint + R.cptr;
+  const int32_t* ci = rint + R.cidx;
+  const double* cw = rdbl + R.cw;
+  const int nh = 2 * nt;
+  const ElemOff of = off[e];
+  double2* Se = Sst + of.S;
+  double2* Ze = Zst + of.Z;
+  double2* se = sst + of.h;
+  double2* T = scratch + (size_t)slot * scratch_stride;
+  double2* Zn = T + (size_t)nh * nh;
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) s_in[t] = se[t];
+  // T = S R and Zn = Z R: column c of R (half base) combines columns base + ci[k]
+  for (int q = threadIdx.x; q < nh * nh; q += blockDim.x) {
+    const int i = q / nh, c = q - i * nh;
+    const int cc = c < nt ? c : c - nt, base = c < nt ? 0 : nt;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = cp[cc]; k < cp[cc + 1]; ++k) {
+      const double2 v = Se[(size_t)i * nh + base + ci[k]];
+      acc.x = fma(v.x, cw[k], acc.x);
+      acc.y = fma(v.y, cw[k], acc.y);
+    }
+    T[q] = acc;
+  }
+  for (int q = threadIdx.x; q < nu * nh; q += blockDim.x) {
+    const int i = q / nh, c = q - i * nh;
+    const int cc = c < nt ? c : c - nt, base = c < nt ? 0 : nt;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = cp[cc]; k < cp[cc + 1]; ++k) {
+      const double2 v = Ze[(size_t)i * nh + base + ci[k]];
+      acc.x = fma(v.x, cw[k], acc.x);
+      acc.y = fma(v.y, cw[k], acc.y);
+    }
+    Zn[q] = acc;
+  }
+  __syncthreads();
+  // S = R^T T: row r of the result combines rows base + ci[k] of T
+  for (int q = threadIdx.x; q < nh * nh; q += blockDim.x) {
+    const int r = q / nh, c = q - r * nh;
+    const int rr = r < nt ? r : r - nt, base = r < nt ? 0 : nt;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = cp[rr]; k < cp[rr + 1]; ++k) {
+      const double2 v = T[(size_t)(base + ci[k]) * nh + c];
+      acc.x = fma(v.x, cw[k], acc.x);
+      acc.y = fma(v.y, cw[k], acc.y);
+    }
+    Se[q] = acc;
+  }
+  for (int q = threadIdx.x; q < nu * nh; q += blockDim.x) Ze[q] = Zn[q];
+  for (int r = threadIdx.x; r < nh; r += blockDim.x) {
+    const int rr = r < nt ? r : r - nt, base = r < nt ? 0 : nt;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = cp[rr]; k < cp[rr + 1]; ++k) {
+      const double2 v = s_in[base + ci[k]];
+      acc.x = fma(v.x, cw[k], acc.x);
+      acc.y = fma(v.y, cw[k], acc.y);
+    }
+    se[r] = acc;
+  }
+}
+
 // ------------------------------------------------------- orchestration --
-int alloc_workspace(dpg_handle* h, int cap) {
+// Per-element bytes of the chunk workspace of one group.
+static size_t chunk_bytes(const Sizes& S) {
+  return sizeof(double2) * (size_t)S.N * S.N + sizeof(double) * 3 * (size_t)S.nq * (2 * S.n_f + 3 * S.nL) +
+         sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) + sizeof(int);
+}
+
+// Default chunk capacity per group: a byte budget of 12 GB, raised to one
+// element per SM when a single chunk of the group is larger (high degrees), at
+// most 48 GB; a multiple of the SM count when large enough; or the caller's
+// fixed chunk.
+void set_default_caps(dpg_handle* h, int chunk) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (Group& G : h->grp) {
+    const size_t per = chunk_bytes(G.sz);
+    const size_t budget = std::max((size_t)12 << 30, std::min((size_t)48 << 30, per * (size_t)sms));
+    int cap = (int)std::max<size_t>(1, budget / per);
+    if (chunk > 0) cap = chunk;
+    if (cap >= sms && chunk <= 0) cap = cap / sms * sms;
+    G.cap = std::max(1, std::min(cap, (int)G.elems.size()));
+  }
+}
+
+// One workspace sized for the largest group chunk (frees the previous one).
+int alloc_workspace(dpg_handle* h) {
   Workspace& w = h->ws;
-  if (w.cap >= cap) return DPG_OK;
-  cudaFree(w.K);
-  cudaFree(w.V);
-  cudaFree(w.Cu);
-  cudaFree(w.PhiL);
-  cudaFree(w.MC);
-  cudaFree(w.ids);
-  cudaFree(w.FV);
-  cudaFree(w.FR);
-  cudaFree(w.rent);
+  void* old[] = {w.K, w.V, w.Cu, w.PhiL, w.MC, w.ids, w.FV, w.FR, w.rent};
+  for (void* b : old)
+    if (b) cudaFree(b);
   w = Workspace{};
-  const Sizes& S = h->sz;
-  const size_t nq3 = 3 * (size_t)S.nq;
-  const int Wf = 2 * S.n_f + 2 * S.nt + 2;
-  w.rcap = std::max(6, std::min(cap * 2, std::max(6, (int)h->robin_entries.size())));
-  size_t bytes[] = {sizeof(double2) * (size_t)S.N * S.N * cap,
-                    sizeof(double) * nq3 * S.n_f * cap,
-                    sizeof(double) * nq3 * S.n_f * cap,
-                    sizeof(double) * nq3 * 3 * S.nL * cap,
-                    sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) * cap,
-                    sizeof(int) * (size_t)cap,
-                    sizeof(double) * 3 * (size_t)S.nqf * Wf * w.rcap,
-                    sizeof(double) * (size_t)S.n_f * Wf * w.rcap,
-                    sizeof(int) * 4 * (size_t)w.rcap};
+  size_t bK = 0, bV = 0, bP = 0, bMC = 0, bFV = 0, bFR = 0;
+  int capmax = 1;
+  for (Group& G : h->grp) {
+    const Sizes& S = G.sz;
+    const int cap = G.cap;
+    capmax = std::max(capmax, cap);
+    const size_t nq3 = 3 * (size_t)S.nq;
+    bK = std::max(bK, sizeof(double2) * (size_t)S.N * S.N * cap);
+    bV = std::max(bV, sizeof(double) * nq3 * S.n_f * cap);
+    bP = std::max(bP, sizeof(double) * nq3 * 3 * S.nL * cap);
+    bMC = std::max(bMC, sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) * cap);
+  }
+  w.rcap = std::max(6, std::min(capmax * 2, std::max(6, (int)h->robin_entries.size())));
+  for (Group& G : h->grp) {
+    const Sizes& S = G.sz;
+    const int Wf = 2 * S.n_f + 2 * S.nt + 2;
+    bFV = std::max(bFV, sizeof(double) * 3 * (size_t)S.nqf * Wf * w.rcap);
+    bFR = std::max(bFR, sizeof(double) * (size_t)S.n_f * Wf * w.rcap);
+  }
+  size_t bytes[] = {bK, bV, bV, bP, bMC, sizeof(int) * (size_t)capmax, bFV, bFR, sizeof(int) * 4 * (size_t)w.rcap};
   void** ptrs[] = {(void**)&w.K, (void**)&w.V, (void**)&w.Cu, (void**)&w.PhiL, (void**)&w.MC, (void**)&w.ids,
                    (void**)&w.FV, (void**)&w.FR, (void**)&w.rent};
   for (int k = 0; k < 9; ++k) {
@@ -893,34 +1006,37 @@ int alloc_workspace(dpg_handle* h, int cap) {
       return DPG_ERR_NOMEM;
     }
   }
-  w.cap = cap;
+  w.cap = capmax;
+  h->plan_valid = false;
+  h->graph_valid = false;
   return DPG_OK;
 }
 
-// Robin sub-batches: whole elements, at most rcap entries.
-static int run_robin(dpg_handle* h, const int* ids_host, int count, cudaStream_t s) {
-  Workspace& w = h->ws;
-  const Sizes& S = h->sz;
-  const int Wf = 2 * S.n_f + 2 * S.nt + 2;
+// Kernel attributes set once (never inside a stream capture).
+int init_kernel_attributes(dpg_handle* h) {
+  const int s64 = (int)(sizeof(double) * (NB * NB + 2 * NB * TT));
+  const int s128 = (int)(sizeof(double2) * (NB * NB + 2 * NB * TT));
+  DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64));
+  DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128));
+  if (tc_init() != DPG_OK) {
+    h->err = "tensor-core kernel attribute setup failed";
+    return DPG_ERR_CUDA;
+  }
+  return DPG_OK;
+}
+
+// Robin sub-batches of a chunk: whole elements, at most rcap / 2 entries.
+// Each sub-batch is (entries: slot, face, group, element id; per element:
+// first entry, count).
+static void robin_batches(const dpg_handle* h, const int* ids_host, int count,
+                          std::vector<std::vector<int>>& rents, std::vector<std::vector<int>>& rlists) {
   std::vector<int> rent, rlist;
-  auto flush = [&]() -> int {
-    if (rlist.empty()) return DPG_OK;
-    const int nent = (int)rent.size() / 4;
-    DPG_CUDA_TRY(h, cudaMemcpyAsync(w.rent, rent.data(), sizeof(int) * rent.size(), cudaMemcpyHostToDevice, s));
-    // rlist rides after the entries in the same buffer region (rcap*4 ints suffice: 2 per element)
-    int* d_rlist = w.rent + 4 * nent;
-    DPG_CUDA_TRY(h, cudaMemcpyAsync(d_rlist, rlist.data(), sizeof(int) * rlist.size(), cudaMemcpyHostToDevice, s));
-    k_face_arrays<<<dim3(1, nent), 256, 0, s>>>(h->tab, S, h->d_X, w.rent, h->d_robin, h->d_trfun, h->omega, 0, w.FV);
-    gemm_tn(S.n_f, Wf, 3 * S.nqf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FR, Wf,
-            (long long)S.n_f * Wf, nent, s);
-    k_robin_add<<<(int)rlist.size() / 2, 256, 0, s>>>(S, d_rlist, w.rent, h->d_robin, w.FR, w.K);
-    DPG_CUDA_TRY(h, cudaGetLastError());
-    h->launches += 3;
-    // the host vectors are reused: wait for the copies of this sub-batch
-    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  auto flush = [&]() {
+    if (rlist.empty()) return;
+    rents.push_back(rent);
+    rlists.push_back(rlist);
     rent.clear();
     rlist.clear();
-    return DPG_OK;
   };
   for (int slot = 0; slot < count; ++slot) {
     const int e = ids_host[slot];
@@ -928,11 +1044,7 @@ static int run_robin(dpg_handle* h, const int* ids_host, int count, cudaStream_t
     if (first < 0) continue;
     int cnt = 0;
     while (first + cnt < (int)h->robin_entries.size() && h->robin_entries[first + cnt].elem == e) ++cnt;
-    // entries + 2 ints of rlist per element must fit in the 4*rcap int buffer
-    if ((int)rent.size() / 4 + cnt > w.rcap / 2) {
-      int rc = flush();
-      if (rc) return rc;
-    }
+    if ((int)rent.size() / 4 + cnt > h->ws.rcap / 2) flush();
     rlist.push_back((int)rent.size() / 4);
     rlist.push_back(cnt);
     for (int k = 0; k < cnt; ++k) {
@@ -943,82 +1055,325 @@ static int run_robin(dpg_handle* h, const int* ids_host, int count, cudaStream_t
       rent.push_back(e);
     }
   }
-  return flush();
+  flush();
 }
 
-int run_element_chunk(dpg_handle* h, const int* ids_host, int count, cudaStream_t s, bool factor, bool extract,
-                      bool real) {
+// Face arrays, face GEMM and Robin terms of one sub-batch (device lists).
+static int robin_launch(dpg_handle* h, int g, const int* d_rent, int nent, const int* d_rlist, int nel,
+                        cudaStream_t s) {
   Workspace& w = h->ws;
-  const Sizes& S = h->sz;
-  if (count > w.cap) return DPG_ERR_ARG;
-  DPG_CUDA_TRY(h, cudaMemcpyAsync(w.ids, ids_host, sizeof(int) * count, cudaMemcpyHostToDevice, s));
-  const size_t nq3 = 3 * (size_t)S.nq;
-  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(h->tab, S, h->d_X, w.ids, w.V, w.Cu, w.PhiL);
-  const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
-  const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
-  const int nL3 = 3 * S.nL;
-  // M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL
-  gemm_tn(S.n_f, S.n_f, (int)nq3, w.V, S.n_f, sV, w.V, S.n_f, sV, w.MC, S.n_f, (long long)mcs, count, s);
-  gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f, S.n_f,
-          (long long)mcs, count, s);
-  gemm_tn(S.n_f, nL3, (int)nq3, w.V, S.n_f, sV, w.PhiL, nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f, nL3,
-          (long long)mcs, count, s);
-  gemm_tn(S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
-          w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, s);
-  double* Kr = reinterpret_cast<double*>(w.K);
-  if (real) {
-    k_build_K_real<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, w.ids, h->d_eps, h->d_mu, w.MC, h->d_Xref,
-                                                    h->d_Tall, Kr);
-  } else {
-    k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, w.ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
-                                               h->d_Xref, h->d_Tf, h->d_Tall, w.K);
-  }
+  const Group& G = h->grp[g];
+  const Sizes& S = G.sz;
+  const int Wf = 2 * S.n_f + 2 * S.nt + 2;
+  k_face_arrays<<<dim3(1, nent), 256, 0, s>>>(G.tab, S, h->d_X, d_rent, h->d_robin, G.d_trfun, h->omega, 0, w.FV);
+  gemm_tn(S.n_f, Wf, 3 * S.nqf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FR, Wf,
+          (long long)S.n_f * Wf, nent, s);
+  k_robin_add<<<nel, 256, 0, s>>>(S, d_rlist, d_rent, h->d_robin, w.FR, w.K);
   DPG_CUDA_TRY(h, cudaGetLastError());
-  h->launches += 6;  // basis arrays, four GEMMs, K
-  if (!real) {
-    int rc = run_robin(h, ids_host, count, s);
+  h->launches += 3;
+  return DPG_OK;
+}
+
+// Robin terms of a chunk given by host ids (paths outside the plan): the
+// sub-batch lists are copied to the workspace one at a time.
+static int run_robin(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s) {
+  Workspace& w = h->ws;
+  std::vector<std::vector<int>> rents, rlists;
+  robin_batches(h, ids_host, count, rents, rlists);
+  for (size_t k = 0; k < rents.size(); ++k) {
+    const int nent = (int)rents[k].size() / 4;
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(w.rent, rents[k].data(), sizeof(int) * rents[k].size(), cudaMemcpyHostToDevice, s));
+    // the element list rides after the entries (rcap / 2 entries and 2 ints per element fit 4 rcap ints)
+    int* d_rlist = w.rent + 4 * nent;
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(d_rlist, rlists[k].data(), sizeof(int) * rlists[k].size(), cudaMemcpyHostToDevice,
+                                    s));
+    int rc = robin_launch(h, g, w.rent, nent, d_rlist, (int)rlists[k].size() / 2, s);
     if (rc) return rc;
-  }
-  if (factor) {
-    const size_t smem = (real ? sizeof(double) : sizeof(double2)) * (NB * NB + 2 * NB * TT);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->timing) {
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      cudaEventRecord(e0, s);
-    }
-    if (real) {
-      DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_factor<double><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, w.ids, Kr, h->d_status);
-    } else {
-      DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_factor<double2><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, w.ids, w.K, h->d_status);
-    }
-    DPG_CUDA_TRY(h, cudaGetLastError());
-    h->launches += 1;
-    if (h->timing) {
-      cudaEventRecord(e1, s);
-      h->factor_events.push_back({e0, e1});
-      h->factor_counts.push_back(count);
-      h->factor_real.push_back(real ? 1 : 0);
-    }
-  }
-  if (extract) {
-    if (real)
-      k_extract_real<<<count, 256, 0, s>>>(S, w.ids, Kr, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1, w.V);
-    else
-      k_extract<<<count, 256, 0, s>>>(S, w.ids, w.K, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
-    DPG_CUDA_TRY(h, cudaGetLastError());
-    h->launches += 1;
+    // the workspace list buffer is reused: wait for this sub-batch
+    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
   }
   return DPG_OK;
 }
 
+int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s, bool factor,
+                      bool extract, bool real, const ChunkPlan* cp) {
+  Workspace& w = h->ws;
+  const Group& G = h->grp[g];
+  const Sizes& S = G.sz;
+  if (count > G.cap) return DPG_ERR_ARG;
+  // element ids of the chunk: the plan's device list, or a copy of the host list
+  const int* ids = cp ? h->d_plan_ids + cp->ids_off : w.ids;
+  if (!cp) DPG_CUDA_TRY(h, cudaMemcpyAsync(w.ids, ids_host, sizeof(int) * count, cudaMemcpyHostToDevice, s));
+  const size_t nq3 = 3 * (size_t)S.nq;
+  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(G.tab, S, h->d_X, ids, w.V, w.Cu, w.PhiL);
+  const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
+  const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
+  const int nL3 = 3 * S.nL;
+  // M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL (FP64, or the tensor cores)
+  if (h->prec == DPG_PREC_FP64) {
+    gemm_tn(S.n_f, S.n_f, (int)nq3, w.V, S.n_f, sV, w.V, S.n_f, sV, w.MC, S.n_f, (long long)mcs, count, s, 1);
+    gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f, S.n_f,
+            (long long)mcs, count, s, 1);
+    gemm_tn(S.n_f, nL3, (int)nq3, w.V, S.n_f, sV, w.PhiL, nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f, nL3,
+            (long long)mcs, count, s);
+    gemm_tn(S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
+            w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, s);
+  } else {
+    const int split = h->prec == DPG_PREC_3XTF32 ? 3 : 1;
+    int* terr = h->d_status + h->ne;
+    int rc = 0;
+    rc |= gemm_tn_tc(split, S.n_f, S.n_f, (int)nq3, w.V, S.n_f, sV, w.V, S.n_f, sV, w.MC, S.n_f, (long long)mcs,
+                     count, 1, terr, s);
+    rc |= gemm_tn_tc(split, S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f,
+                     S.n_f, (long long)mcs, count, 1, terr, s);
+    rc |= gemm_tn_tc(split, S.n_f, nL3, (int)nq3, w.V, S.n_f, sV, w.PhiL, nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f,
+                     nL3, (long long)mcs, count, 0, terr, s);
+    rc |= gemm_tn_tc(split, S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
+                     w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, 0, terr, s);
+    if (rc) {
+      h->err = "tensor-core contraction launch failed";
+      return DPG_ERR_CUDA;
+    }
+  }
+  double* Kr = reinterpret_cast<double*>(w.K);
+  if (real) {
+    k_build_K_real<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, ids, h->d_eps, h->d_mu, w.MC, G.d_Xref,
+                                                    G.d_Tall, Kr);
+  } else {
+    k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
+                                               G.d_Xref, G.d_Tf, G.d_Tall, w.K);
+  }
+  DPG_CUDA_TRY(h, cudaGetLastError());
+  h->launches += 6;  // basis arrays, four GEMMs, K
+  if (!real) {
+    if (cp) {
+      for (const int4& rb : cp->robin) {
+        int rc = robin_launch(h, g, h->d_plan_rent + rb.x, rb.y, h->d_plan_rent + rb.z, rb.w, s);
+        if (rc) return rc;
+      }
+    } else {
+      int rc = run_robin(h, g, ids_host, count, s);
+      if (rc) return rc;
+    }
+  }
+  if (factor) {
+    const size_t smem = (real ? sizeof(double) : sizeof(double2)) * (NB * NB + 2 * NB * TT);
+    const bool timed = cp && h->timing;
+    if (timed) DPG_CUDA_TRY(h, cudaEventRecord(cp->ev0, s));
+    if (real)
+      k_factor<double><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, Kr, h->d_status);
+    else
+      k_factor<double2><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, w.K, h->d_status);
+    DPG_CUDA_TRY(h, cudaGetLastError());
+    h->launches += 1;
+    if (timed) DPG_CUDA_TRY(h, cudaEventRecord(cp->ev1, s));
+  }
+  if (extract) {
+    if (real)
+      k_extract_real<<<count, 256, 0, s>>>(S, ids, Kr, h->d_off, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1,
+                                           w.V);
+    else
+      k_extract<<<count, 256, 0, s>>>(S, ids, w.K, h->d_off, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
+    DPG_CUDA_TRY(h, cudaGetLastError());
+    h->launches += 1;
+    bool any = cp ? cp->restricted : false;
+    for (int k = 0; !cp && k < count && !any; ++k) any = h->elem_sig[ids_host[k]] >= 0;
+    if (any) {
+      k_restrict<<<count, 256, sizeof(double2) * S.n_h, s>>>(S.nt, S.n_u, ids, h->d_off, h->d_sig, h->d_rsig,
+                                                            h->d_rint, h->d_rdbl, h->d_S, h->d_s, h->d_Z, w.K,
+                                                            (size_t)S.N * S.N);
+      DPG_CUDA_TRY(h, cudaGetLastError());
+      h->launches += 1;
+    }
+  }
+  return DPG_OK;
+}
+
+// ------------------------------------------------------ pass plan / graph --
+void free_plan(dpg_handle* h) {
+  for (ChunkPlan& c : h->plan) {
+    if (c.ev0) cudaEventDestroy(c.ev0);
+    if (c.ev1) cudaEventDestroy(c.ev1);
+  }
+  h->plan.clear();
+  if (h->d_plan_ids) cudaFree(h->d_plan_ids);
+  if (h->d_plan_rent) cudaFree(h->d_plan_rent);
+  h->d_plan_ids = nullptr;
+  h->d_plan_rent = nullptr;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->plan_valid = false;
+  h->graph_valid = false;
+}
+
+// Chunks of every group (lossless elements on the real path first), their
+// device id lists and Robin sub-batches.  Synchronous (setup-time work).
+int build_plan(dpg_handle* h) {
+  free_plan(h);
+  std::vector<int> ids_all, rent_all;
+  for (int g = 0; g < (int)h->grp.size(); ++g) {
+    const Group& G = h->grp[g];
+    const std::vector<int>* lists[2] = {&G.real_elems, &G.cplx_elems};
+    if (!h->allow_real) {
+      lists[0] = &G.elems;
+      lists[1] = nullptr;
+    }
+    for (int li = 0; li < 2; ++li) {
+      if (!lists[li]) continue;
+      const std::vector<int>& L = *lists[li];
+      for (size_t c0 = 0; c0 < L.size(); c0 += G.cap) {
+        ChunkPlan cp;
+        cp.g = g;
+        cp.real = h->allow_real && li == 0;
+        cp.count = (int)std::min<size_t>(G.cap, L.size() - c0);
+        cp.ids_off = (int64_t)ids_all.size();
+        ids_all.insert(ids_all.end(), L.begin() + c0, L.begin() + c0 + cp.count);
+        for (int k = 0; k < cp.count && !cp.restricted; ++k) cp.restricted = h->elem_sig[L[c0 + k]] >= 0;
+        if (!cp.real) {
+          std::vector<std::vector<int>> rents, rlists;
+          robin_batches(h, L.data() + c0, cp.count, rents, rlists);
+          for (size_t k = 0; k < rents.size(); ++k) {
+            int4 rb;
+            rb.x = (int)rent_all.size();
+            rb.y = (int)rents[k].size() / 4;
+            rent_all.insert(rent_all.end(), rents[k].begin(), rents[k].end());
+            rb.z = (int)rent_all.size();
+            rb.w = (int)rlists[k].size() / 2;
+            rent_all.insert(rent_all.end(), rlists[k].begin(), rlists[k].end());
+            cp.robin.push_back(rb);
+          }
+        }
+        DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev0));
+        DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev1));
+        h->plan.push_back(std::move(cp));
+      }
+    }
+  }
+  DPG_CUDA_TRY(h, cudaMalloc(&h->d_plan_ids, sizeof(int) * std::max<size_t>(1, ids_all.size())));
+  DPG_CUDA_TRY(h, cudaMalloc(&h->d_plan_rent, sizeof(int) * std::max<size_t>(1, rent_all.size())));
+  if (!ids_all.empty())
+    DPG_CUDA_TRY(h, cudaMemcpy(h->d_plan_ids, ids_all.data(), sizeof(int) * ids_all.size(), cudaMemcpyHostToDevice));
+  if (!rent_all.empty())
+    DPG_CUDA_TRY(h, cudaMemcpy(h->d_plan_rent, rent_all.data(), sizeof(int) * rent_all.size(),
+                               cudaMemcpyHostToDevice));
+  h->plan_valid = true;
+  h->graph_valid = false;
+  return DPG_OK;
+}
+
+// The whole element pass: the plan's launches, captured once into a CUDA
+// graph (re-captured when the plan or the timing switch changes) and replayed
+// on the caller's stream.  Capture runs on a private stream, since the legacy
+// default stream cannot be captured.
+int element_pass(dpg_handle* h, cudaStream_t s) {
+  if (!h->plan_valid) {
+    int rc = build_plan(h);
+    if (rc) return rc;
+  }
+  if (!h->use_graph) {
+    for (const ChunkPlan& cp : h->plan) {
+      int rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, true, true, cp.real, &cp);
+      if (rc) return rc;
+    }
+    return DPG_OK;
+  }
+  if (!h->graph_valid || h->graph_timing != h->timing) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    if (!h->cap_stream) DPG_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    DPG_CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = h->launches;
+    int rc = DPG_OK;
+    for (const ChunkPlan& cp : h->plan) {
+      rc = run_element_chunk(h, cp.g, nullptr, cp.count, h->cap_stream, true, true, cp.real, &cp);
+      if (rc) break;
+    }
+    cudaGraph_t gr = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &gr);
+    if (rc == DPG_OK && ee != cudaSuccess) {
+      h->err = std::string("element pass capture: ") + cudaGetErrorString(ee);
+      rc = DPG_ERR_CUDA;
+    }
+    if (rc == DPG_OK && cudaGraphInstantiate(&h->graph, gr, 0) != cudaSuccess) {
+      h->err = "element pass graph instantiation failed";
+      rc = DPG_ERR_CUDA;
+    }
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    h->graph_launches = h->launches - l0;
+    h->launches = l0;
+    if (rc) {
+      if (h->graph) cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+      return rc;
+    }
+    h->graph_valid = true;
+    h->graph_timing = h->timing;
+  }
+  DPG_CUDA_TRY(h, cudaGraphLaunch(h->graph, s));
+  h->launches += h->graph_launches;
+  return DPG_OK;
+}
+
+// Chunk-size autotuner: per group, time one chunk of the group's larger
+// arithmetic class at each candidate size (multiples of the SM count up to the
+// byte budget) and keep the fastest per element.  Stores of the timed elements
+// are overwritten (a full element pass rewrites them).
+int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaEvent_t e0, e1;
+  DPG_CUDA_TRY(h, cudaEventCreate(&e0));
+  DPG_CUDA_TRY(h, cudaEventCreate(&e1));
+  int rc = DPG_OK;
+  for (int g = 0; g < (int)h->grp.size() && rc == DPG_OK; ++g) {
+    Group& G = h->grp[g];
+    const bool real = h->allow_real && G.real_elems.size() >= G.cplx_elems.size();
+    const std::vector<int>& L = !h->allow_real ? G.elems : (real ? G.real_elems : G.cplx_elems);
+    const int n = (int)L.size();
+    const size_t per = chunk_bytes(G.sz);
+    std::vector<int> cand;
+    for (int k : {1, 2, 3, 4, 6, 8, 12, 16})
+      if (k * sms <= n && (double)per * k * sms <= max_bytes) cand.push_back(k * sms);
+    if (cand.empty()) cand.push_back(std::max(1, std::min(n, (int)(max_bytes / per))));
+    const int keep = G.cap;
+    int best = keep;
+    float best_ms = 1e30f;
+    for (int c : cand) {
+      G.cap = c;
+      rc = alloc_workspace(h);
+      if (rc) break;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2 && rc == DPG_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = run_element_chunk(h, g, L.data(), c, s, true, true, real);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = DPG_ERR_CUDA;
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep == 1) ms = t;
+      }
+      if (rc) break;
+      if (ms / c < best_ms) {
+        best_ms = ms / c;
+        best = c;
+      }
+    }
+    G.cap = rc ? keep : best;
+    if (caps) caps[g] = G.cap;
+    if (ms_per_elem) ms_per_elem[g] = best_ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc2 = alloc_workspace(h);
+  return rc ? rc : rc2;
+}
+
 // Cholesky of the G block alone for the current chunk (rows below untouched).
-int factor_gram_only(dpg_handle* h, int count, cudaStream_t s) {
-  const Sizes& S = h->sz;
+int factor_gram_only(dpg_handle* h, int g, int count, cudaStream_t s) {
+  const Sizes& S = h->grp[g].sz;
   const size_t smem = sizeof(double2) * (NB * NB + 2 * NB * TT);
-  DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_factor<double2><<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status);
   h->launches += 1;
   DPG_CUDA_TRY(h, cudaGetLastError());
@@ -1044,8 +1399,9 @@ __global__ void k_copy_cols(int rows, int ncol, const double* src, int lds, long
   }
 }
 
-int compute_reference_matrices(dpg_handle* h, cudaStream_t s) {
-  const Sizes& S = h->sz;
+int compute_reference_matrices(dpg_handle* h, int g, cudaStream_t s) {
+  Group& G = h->grp[g];
+  const Sizes& S = G.sz;
   Workspace& w = h->ws;
   // unit cube as a temporary element: reuse d_X slot of element 0 is not allowed;
   // allocate a private corner array
@@ -1059,9 +1415,9 @@ int compute_reference_matrices(dpg_handle* h, cudaStream_t s) {
   int zeros[32] = {0};
   DPG_CUDA_TRY(h, cudaMemcpyAsync(dXu, Xu, sizeof(Xu), cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(dids, zeros, sizeof(zeros), cudaMemcpyHostToDevice, s));
-  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, 1), 256, 0, s>>>(h->tab, S, dXu, dids, w.V, w.Cu, w.PhiL);
+  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, 1), 256, 0, s>>>(G.tab, S, dXu, dids, w.V, w.Cu, w.PhiL);
   const size_t nq3 = 3 * (size_t)S.nq;
-  gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, 0, w.V, S.n_f, 0, h->d_Xref, S.n_f, 0, 1, s);
+  gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, 0, w.V, S.n_f, 0, G.d_Xref, S.n_f, 0, 1, s);
   // faces of the unit cube
   int rent[24];
   for (int f = 0; f < 6; ++f) {
@@ -1072,13 +1428,13 @@ int compute_reference_matrices(dpg_handle* h, cudaStream_t s) {
   }
   DPG_CUDA_TRY(h, cudaMemcpyAsync(w.rent, rent, sizeof(rent), cudaMemcpyHostToDevice, s));
   const int Wf = 2 * S.n_f + 2 * S.nt + 2;
-  k_face_arrays<<<dim3(1, 6), 256, 0, s>>>(h->tab, S, dXu, w.rent, h->d_robin, h->d_trfun, h->omega, 1, w.FV);
+  k_face_arrays<<<dim3(1, 6), 256, 0, s>>>(G.tab, S, dXu, w.rent, h->d_robin, G.d_trfun, h->omega, 1, w.FV);
   gemm_tn(S.n_f, Wf, 3 * S.nqf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FR, Wf,
           (long long)S.n_f * Wf, 6, s);
   // T_f = columns [2 n_f + nt, 2 n_f + 2 nt) of FR
-  k_copy_cols<<<dim3(64, 6), 256, 0, s>>>(S.n_f, S.nt, w.FR, Wf, (long long)S.n_f * Wf, 2 * S.n_f + S.nt, h->d_Tf,
+  k_copy_cols<<<dim3(64, 6), 256, 0, s>>>(S.n_f, S.nt, w.FR, Wf, (long long)S.n_f * Wf, 2 * S.n_f + S.nt, G.d_Tf,
                                          (long long)S.n_f * S.nt);
-  k_sum_faces<<<64, 256, 0, s>>>(S.n_f * S.nt, h->d_Tf, h->d_Tall);
+  k_sum_faces<<<64, 256, 0, s>>>(S.n_f * S.nt, G.d_Tf, G.d_Tall);
   DPG_CUDA_TRY(h, cudaGetLastError());
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
   cudaFree(dXu);

@@ -8,6 +8,17 @@
 // identified by their vertex ids: an edge by (start, end) along the local
 // axis, a face by its sorted vertex ids, with the corner order of the first
 // element that meets it stored to check that neighbours agree.
+//
+// Mixed trial degrees: an entity carries trace unknowns of order
+// r_E = min over the elements that contain it of (p_K + 1), so that the trace
+// lies in every neighbour's own trace space; each element still computes at
+// its own degree.  Element K's trace coefficients are the global trace's values
+// at K's own nodes, uhat_K = R_K uhat, and R_K's entries are 1D Lagrange
+// polynomials of the entity order evaluated at K's nodes (on a face the edge
+// unknowns enter through the closed Lagrange factor of the face order at the
+// face's two edges).  The global unknowns an element touches sit in its own
+// trace slots (same entity, same index) and the slots without one are marked
+// unused (-2), so R_K is a square matrix over the element's trace slots.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -125,20 +136,15 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     h->err = "alpha and omega must be positive";
     return DPG_ERR_ARG;
   }
-  if (prm->precision != DPG_PREC_FP64) {
+  if (prm->precision < DPG_PREC_FP64 || prm->precision > DPG_PREC_3XTF32) {
     h->err = "unsupported precision mode";
     return DPG_ERR_UNSUPPORTED;
   }
   const int ne = m->n_elem;
-  const int p = m->elem_p[0];
-  if (p < 1 || p > MAXP) {
-    h->err = "trial degree must be in 1..4";
-    return DPG_ERR_MESH;
-  }
   for (int e = 0; e < ne; ++e)
-    if (m->elem_p[e] != p) {
-      h->err = "mixed trial degrees are not implemented in this build";
-      return DPG_ERR_UNSUPPORTED;
+    if (m->elem_p[e] < 1 || m->elem_p[e] > MAXP) {
+      h->err = "trial degree must be in 1..4 (element " + std::to_string(e) + ")";
+      return DPG_ERR_MESH;
     }
   for (int64_t k = 0; k < (int64_t)ne * 8; ++k)
     if (m->elem[k] < 0 || m->elem[k] >= m->n_vert) {
@@ -161,15 +167,33 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     }
   }
   h->ne = ne;
+  h->prec = prm->precision;
   h->omega = prm->omega;
   h->alpha = prm->alpha;
-  h->sz = make_sizes(p);
-  build_tables(p, &h->tab);
-  const Sizes& S = h->sz;
-  const int r = S.r;
   h->robin.assign(m->robin, m->robin + m->n_robin);
   h->dirichlet.assign(m->dirichlet, m->dirichlet + m->n_dirichlet);
-
+  // ---- order groups ------------------------------------------------------
+  {
+    int slot_of_p[MAXP + 1];
+    for (int q = 0; q <= MAXP; ++q) slot_of_p[q] = -1;
+    for (int e = 0; e < ne; ++e) slot_of_p[m->elem_p[e]] = 0;
+    h->grp.clear();
+    for (int q = 1; q <= MAXP; ++q)
+      if (slot_of_p[q] == 0) {
+        slot_of_p[q] = (int)h->grp.size();
+        Group G;
+        G.p = q;
+        G.sz = make_sizes(q);
+        build_tables(q, &G.tab);
+        h->grp.push_back(std::move(G));
+      }
+    h->elem_grp.assign(ne, 0);
+    for (int e = 0; e < ne; ++e) {
+      h->elem_grp[e] = (int8_t)slot_of_p[m->elem_p[e]];
+      h->grp[h->elem_grp[e]].elems.push_back(e);
+    }
+    h->szmax = h->grp.back().sz;
+  }
   // ---- geometry: corner coordinates and corner Jacobians ---------------
   std::vector<double> X((size_t)ne * 24);
   for (int e = 0; e < ne; ++e)
@@ -253,8 +277,15 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
       }
   }
   const int n_ent = n_edges + n_faces;  // entity id: edges [0, n_edges), faces after
-  const int dof_edge = r, dof_face = 2 * r * (r - 1);
-  auto ent_dofs = [&](int ent) { return ent < n_edges ? dof_edge : dof_face; };
+  // entity trace order: min over the containing elements of p + 1
+  std::vector<int> ent_r(n_ent, MAXP + 1);
+  for (int e = 0; e < ne; ++e) {
+    const int re = m->elem_p[e] + 1;
+    for (int k = 0; k < 12; ++k) ent_r[elem_edge[(size_t)e * 12 + k]] = std::min(ent_r[elem_edge[(size_t)e * 12 + k]], re);
+    for (int k = 0; k < 6; ++k)
+      ent_r[n_edges + elem_face[(size_t)e * 6 + k]] = std::min(ent_r[n_edges + elem_face[(size_t)e * 6 + k]], re);
+  }
+  auto ent_dofs = [&](int ent) { return ent < n_edges ? ent_r[ent] : 2 * ent_r[ent] * (ent_r[ent] - 1); };
 
   // ---- boundary classification ------------------------------------------
   // Dirichlet: every entity on a Dirichlet face; data groups win over zero groups.
@@ -326,50 +357,114 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   }
   h->n = nfree;
 
-  // ---- element-local map -------------------------------------------------
-  const std::vector<int> trf = trace_functions(r);
-  const int nt = S.nt;
-  std::vector<int> loc_ent(nt), loc_idx(nt);  // per local trace function: element entity slot, index
-  for (int t = 0; t < nt; ++t) {
-    int pk = trf[t];
-    int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
-    int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
-    bool b1 = ii[d1] == 0 || ii[d1] == r, b2 = ii[d2] == 0 || ii[d2] == r;
-    if (b1 && b2) {
-      loc_ent[t] = c * 4 + (ii[d1] == r) + 2 * (ii[d2] == r);  // element edge slot 0..11
-      loc_idx[t] = ii[c];
-    } else {
-      int dn = b1 ? d1 : d2;  // face normal
-      int sd = ii[dn] == r;
-      int a = (dn == 0) ? 1 : 0, b = (dn == 2) ? 1 : 2;
-      int eo = (c == a) ? b : a;  // other tangential axis
-      loc_ent[t] = 12 + 2 * dn + sd;
-      loc_idx[t] = (c == a ? 0 : 1) * r * (r - 1) + ii[c] * (r - 1) + (ii[eo] - 1);
+  // ---- element-local map, per-element offsets, trace restrictions ----------
+  // Per group: for each local trace function its element entity slot (edges
+  // 0..11, faces 12..17) and its (component, open index, closed index), and
+  // the inverse lookup (slot, within-entity index at the group's order) -> t.
+  struct LocalMap {
+    std::vector<int> pk, ent, c, ia, ib, idx;  // ib: closed index along the face's other axis (faces)
+    std::vector<std::vector<int>> lookup;  // [slot][within-entity index] -> t
+  };
+  std::vector<LocalMap> lmap(h->grp.size());
+  for (size_t gi = 0; gi < h->grp.size(); ++gi) {
+    const int r = h->grp[gi].sz.r, nt = h->grp[gi].sz.nt;
+    const std::vector<int> trf = trace_functions(r);
+    LocalMap& L = lmap[gi];
+    L.pk = trf;
+    L.ent.resize(nt);
+    L.c.resize(nt);
+    L.ia.resize(nt);
+    L.ib.resize(nt);
+    L.idx.resize(nt);
+    L.lookup.assign(18, std::vector<int>(2 * r * r, -1));
+    for (int t = 0; t < nt; ++t) {
+      int pk = trf[t];
+      int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
+      int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+      bool b1 = ii[d1] == 0 || ii[d1] == r, b2 = ii[d2] == 0 || ii[d2] == r;
+      L.c[t] = c;
+      L.ia[t] = ii[c];
+      if (b1 && b2) {
+        L.ent[t] = c * 4 + (ii[d1] == r) + 2 * (ii[d2] == r);  // element edge slot 0..11
+        L.idx[t] = ii[c];
+        L.ib[t] = -1;
+      } else {
+        int dn = b1 ? d1 : d2;  // face normal
+        int sd = ii[dn] == r;
+        int a = (dn == 0) ? 1 : 0, b = (dn == 2) ? 1 : 2;
+        int eo = (c == a) ? b : a;  // other tangential axis
+        L.ent[t] = 12 + 2 * dn + sd;
+        L.ib[t] = ii[eo];
+        L.idx[t] = (c == a ? 0 : 1) * r * (r - 1) + ii[c] * (r - 1) + (ii[eo] - 1);
+      }
+      L.lookup[L.ent[t]][L.idx[t]] = t;
     }
   }
-  h->l2g.assign((size_t)ne * S.n_h, 0);
-  std::vector<double2> xfix((size_t)ne * S.n_h, make_double2(0.0, 0.0));
-  // Dirichlet values by nodal interpolation: coefficient = E_t(x_node) . (J(node) e_c)
-  double onode[MAXF1D], cnode[MAXF1D], dummy[MAXF1D];
-  gauss_legendre01(r, onode, dummy);
-  gauss_lobatto01(r + 1, cnode);
+  auto elem_entity = [&](int e, int slot) {
+    return slot < 12 ? elem_edge[(size_t)e * 12 + slot] : n_edges + elem_face[(size_t)e * 6 + slot - 12];
+  };
+  // offsets into the pooled stores
+  h->off.assign(ne + 1, ElemOff{0, 0, 0, 0, 0});
   for (int e = 0; e < ne; ++e) {
+    const Sizes& Z = h->grp[h->elem_grp[e]].sz;
+    ElemOff o = h->off[e];
+    o.S += (int64_t)Z.n_h * Z.n_h;
+    o.Z += (int64_t)Z.n_u * Z.n_h;
+    o.L1 += (int64_t)Z.n_u * Z.n_u;
+    o.h += Z.n_h;
+    o.u += Z.n_u;
+    h->off[e + 1] = o;
+  }
+  const ElemOff tot = h->off[ne];
+  h->l2g.assign((size_t)tot.h, -2);
+  std::vector<double2> xfix((size_t)tot.h, make_double2(0.0, 0.0));
+  h->elem_sig.assign(ne, -1);
+  h->rsig.clear();
+  std::vector<int32_t> rint;
+  std::vector<double> rdbl;
+  std::map<std::vector<int>, int> sig_id;
+  for (int e = 0; e < ne; ++e) {
+    const Group& G = h->grp[h->elem_grp[e]];
+    const LocalMap& L = lmap[h->elem_grp[e]];
+    const int r = G.sz.r, nt = G.sz.nt;
+    const int64_t o = h->off[e].h;
+    double onode[MAXF1D], cnode[MAXF1D], wdum[MAXF1D];
+    bool restricted = false;
     for (int t = 0; t < nt; ++t) {
-      int slot = loc_ent[t];
-      int en = slot < 12 ? elem_edge[(size_t)e * 12 + slot] : n_edges + elem_face[(size_t)e * 6 + slot - 12];
-      int32_t gE = dir_grp[en] >= 0 ? -1 : (int32_t)(startE[en] + loc_idx[t]);
-      int32_t gH = h_drop[en] ? -2 : (int32_t)(startH[en] + loc_idx[t]);
-      h->l2g[(size_t)e * S.n_h + t] = gE;
-      h->l2g[(size_t)e * S.n_h + nt + t] = gH;
+      const int en = elem_entity(e, L.ent[t]);
+      const int rE = ent_r[en];
+      if (rE < r) restricted = true;
+      int q;  // index within the entity at its own order, or -1 (slot unused)
+      if (L.ent[t] < 12) {
+        q = L.ia[t] < rE ? L.ia[t] : -1;
+      } else {
+        const int comp = L.idx[t] / (r * (r - 1));
+        q = (L.ia[t] < rE && L.ib[t] <= rE - 1) ? comp * rE * (rE - 1) + L.ia[t] * (rE - 1) + (L.ib[t] - 1) : -1;
+      }
+      if (q < 0) continue;
+      int32_t gE = dir_grp[en] >= 0 ? -1 : (int32_t)(startE[en] + q);
+      int32_t gH = h_drop[en] ? -2 : (int32_t)(startH[en] + q);
+      h->l2g[o + t] = gE;
+      h->l2g[o + nt + t] = gH;
       if (gE == -1) {
         const dpg_dirichlet_group& g = h->dirichlet[dir_grp[en]];
         double2 val = make_double2(0.0, 0.0);
         if (g.kind != DPG_DIRICHLET_ZERO) {
-          // evaluate in this element (the node and J e_c agree between neighbours)
-          int pk = trf[t];
-          int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
+          // nodal interpolation at the entity's own nodes: open node q of
+          // order rE along c, closed nodes of order rE across (the element's
+          // corner coordinates 0 / 1 on the entity); evaluated in this element
+          // (the node and J e_c agree between neighbours)
+          gauss_legendre01(rE, onode, wdum);
+          gauss_lobatto01(rE + 1, cnode);
+          const int pk = L.pk[t];
+          const int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
           double xi[3];
-          for (int d = 0; d < 3; ++d) xi[d] = (d == c) ? onode[ii[d]] : cnode[ii[d]];
+          for (int d = 0; d < 3; ++d) {
+            if (d == c)
+              xi[d] = onode[L.ia[t]];
+            else
+              xi[d] = ii[d] == 0 ? 0.0 : (ii[d] == r ? 1.0 : cnode[ii[d]]);
+          }
           double J[3][3], x[3];
           trilinear(&X[(size_t)e * 24], xi, J, x);
           // outward unit normal of the deciding Dirichlet face, at its centre
@@ -407,9 +502,105 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
             val.y += Et[a].im * J[a][c];
           }
         }
-        xfix[(size_t)e * S.n_h + t] = val;
+        xfix[o + t] = val;
       }
     }
+    if (!restricted) continue;
+    // signature: degree and the orders of the 18 entities
+    std::vector<int> key(19);
+    key[0] = r;
+    for (int k = 0; k < 18; ++k) key[1 + k] = ent_r[elem_entity(e, k)];
+    auto it = sig_id.find(key);
+    if (it != sig_id.end()) {
+      h->elem_sig[e] = it->second;
+      continue;
+    }
+    // R (nt x nt, one field): row t = element trace function, column = slot
+    std::vector<double> R((size_t)nt * nt, 0.0);
+    double oK[MAXF1D], cK[MAXF1D];
+    gauss_legendre01(r, oK, wdum);
+    gauss_lobatto01(r + 1, cK);
+    double val[MAXF1D], der[MAXF1D], vo[MAXF1D], vc[MAXF1D];
+    for (int t = 0; t < nt; ++t) {
+      const int slot = L.ent[t];
+      const int c = L.c[t];
+      const double xc = oK[L.ia[t]];
+      auto add_edge = [&](int eslot, double scale) {
+        const int re = key[1 + eslot];
+        double on[MAXF1D];
+        gauss_legendre01(re, on, wdum);
+        lagrange1d(on, re, xc, val, der);
+        for (int q = 0; q < re; ++q) {
+          const int col = L.lookup[eslot][q];
+          R[(size_t)t * nt + col] += scale * val[q];
+        }
+      };
+      if (slot < 12) {
+        add_edge(slot, 1.0);
+        continue;
+      }
+      const int rF = key[1 + slot];
+      const int dn = (slot - 12) / 2, sd = (slot - 12) % 2;
+      const int a = (dn == 0) ? 1 : 0, b = (dn == 2) ? 1 : 2;
+      const int eo = (c == a) ? b : a;
+      const int comp = (c == a) ? 0 : 1;
+      const double xe = cK[L.ib[t]];
+      double on[MAXF1D], cn[MAXF1D];
+      gauss_legendre01(rF, on, wdum);
+      gauss_lobatto01(rF + 1, cn);
+      lagrange1d(on, rF, xc, vo, der);
+      lagrange1d(cn, rF + 1, xe, vc, der);
+      for (int ia = 0; ia < rF; ++ia)
+        for (int ib = 1; ib < rF; ++ib) {
+          const int col = L.lookup[slot][comp * r * (r - 1) + ia * (r - 1) + (ib - 1)];
+          R[(size_t)t * nt + col] += vo[ia] * vc[ib];
+        }
+      // the face's two edges along c, at eo = 0 (closed end 0) and eo = 1 (end rF)
+      for (int send = 0; send < 2; ++send) {
+        int pos[3];
+        pos[dn] = sd;
+        pos[eo] = send;
+        const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+        const int eslot = c * 4 + pos[d1] + 2 * pos[d2];
+        add_edge(eslot, vc[send ? rF : 0]);
+      }
+    }
+    RSig rs{};
+    rs.nt = nt;
+    rs.cptr = (int64_t)rint.size();
+    std::vector<int> cnt(nt + 1, 0);
+    for (int t = 0; t < nt; ++t)
+      for (int col = 0; col < nt; ++col)
+        if (R[(size_t)t * nt + col] != 0.0) cnt[col + 1]++;
+    for (int col = 0; col < nt; ++col) cnt[col + 1] += cnt[col];
+    rint.insert(rint.end(), cnt.begin(), cnt.end());
+    rs.cidx = (int64_t)rint.size();
+    rs.cw = (int64_t)rdbl.size();
+    for (int col = 0; col < nt; ++col)
+      for (int t = 0; t < nt; ++t)
+        if (R[(size_t)t * nt + col] != 0.0) {
+          rint.push_back(t);
+          rdbl.push_back(R[(size_t)t * nt + col]);
+        }
+    rs.rptr = (int64_t)rint.size();
+    std::vector<int> rc(nt + 1, 0);
+    for (int t = 0; t < nt; ++t)
+      for (int col = 0; col < nt; ++col)
+        if (R[(size_t)t * nt + col] != 0.0) rc[t + 1]++;
+    for (int t = 0; t < nt; ++t) rc[t + 1] += rc[t];
+    rint.insert(rint.end(), rc.begin(), rc.end());
+    rs.ridx = (int64_t)rint.size();
+    rs.rw = (int64_t)rdbl.size();
+    for (int t = 0; t < nt; ++t)
+      for (int col = 0; col < nt; ++col)
+        if (R[(size_t)t * nt + col] != 0.0) {
+          rint.push_back(col);
+          rdbl.push_back(R[(size_t)t * nt + col]);
+        }
+    const int id = (int)h->rsig.size();
+    h->rsig.push_back(rs);
+    sig_id.emplace(key, id);
+    h->elem_sig[e] = id;
   }
 
   // ---- colouring (elements sharing a vertex get different colours) ----------
@@ -430,12 +621,16 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
       color[e] = c;
       if (c == ncol) ++ncol;
     }
-    h->color_off.assign(ncol + 1, 0);
-    for (int e = 0; e < ne; ++e) h->color_off[color[e] + 1]++;
-    for (int c = 0; c < ncol; ++c) h->color_off[c + 1] += h->color_off[c];
-    h->color_elems.assign(ne, 0);
-    std::vector<int> fill(h->color_off.begin(), h->color_off.end() - 1);
-    for (int e = 0; e < ne; ++e) h->color_elems[fill[color[e]]++] = e;
+    // per group: its elements sorted by colour
+    h->ncolor = ncol;
+    for (Group& G : h->grp) {
+      G.color_off.assign(ncol + 1, 0);
+      for (int e : G.elems) G.color_off[color[e] + 1]++;
+      for (int c = 0; c < ncol; ++c) G.color_off[c + 1] += G.color_off[c];
+      G.color_elems_host.assign(G.elems.size(), 0);
+      std::vector<int> fill(G.color_off.begin(), G.color_off.end() - 1);
+      for (int e : G.elems) G.color_elems_host[fill[color[e]]++] = e;
+    }
   }
 
   // ---- CSR pattern: the rows of one entity share their column list ----------
@@ -499,15 +694,13 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
       if (m->face_bc[6 * (size_t)e + f] == DPG_BC_ROBIN) real = false;
     h->is_real[e] = real;
   }
-  h->real_elems.clear();
-  h->cplx_elems.clear();
-  for (int e = 0; e < ne; ++e) (h->is_real[e] ? h->real_elems : h->cplx_elems).push_back(e);
   h->eps_host.assign(m->elem_eps, m->elem_eps + ne);
   h->mu_host.assign(m->elem_mu, m->elem_mu + ne);
   h->robin_face.assign(ne, 0);
   for (int e = 0; e < ne; ++e)
     for (int f = 0; f < 6; ++f)
       if (m->face_bc[6 * (size_t)e + f] == DPG_BC_ROBIN) h->robin_face[e] = 1;
+  classify_elements(h);
 
   // ---- Robin entries ---------------------------------------------------------
   h->robin_entries.clear();
@@ -535,22 +728,25 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     int rc_ = alloc((void**)&(ptr), (size_t)(bytes));          \
     if (rc_) return rc_;                                       \
   } while (0)
-  const size_t nh = S.n_h, nu = S.n_u;
   DPG_ALLOC(h->d_X, sizeof(double) * 24 * (size_t)ne);
   DPG_ALLOC(h->d_eps, sizeof(double2) * ne);
   DPG_ALLOC(h->d_mu, sizeof(double2) * ne);
   DPG_ALLOC(h->d_fbc, 6 * (size_t)ne);
-  DPG_ALLOC(h->d_l2g, sizeof(int32_t) * nh * ne);
-  DPG_ALLOC(h->d_xfix, sizeof(double2) * nh * ne);
-  DPG_ALLOC(h->d_color_elems, sizeof(int) * ne);
+  DPG_ALLOC(h->d_off, sizeof(ElemOff) * (ne + 1));
+  DPG_ALLOC(h->d_l2g, sizeof(int32_t) * tot.h);
+  DPG_ALLOC(h->d_xfix, sizeof(double2) * tot.h);
   DPG_ALLOC(h->d_robin, sizeof(dpg_robin_group) * std::max<size_t>(1, h->robin.size()));
-  DPG_ALLOC(h->d_status, sizeof(int) * ne);
-  DPG_ALLOC(h->d_S, sizeof(double2) * nh * nh * ne);
-  DPG_ALLOC(h->d_s, sizeof(double2) * nh * ne);
+  DPG_ALLOC(h->d_status, sizeof(int) * (ne + 1));  // [ne]: tensor-core wait timeout flag
+  DPG_ALLOC(h->d_S, sizeof(double2) * tot.S);
+  DPG_ALLOC(h->d_s, sizeof(double2) * tot.h);
   DPG_ALLOC(h->d_c, sizeof(double) * ne);
-  DPG_ALLOC(h->d_Z, sizeof(double2) * nu * nh * ne);
-  DPG_ALLOC(h->d_z, sizeof(double2) * nu * ne);
-  if (prm->flags & DPG_FLAG_ADJOINT) DPG_ALLOC(h->d_L1, sizeof(double2) * nu * nu * ne);
+  DPG_ALLOC(h->d_Z, sizeof(double2) * tot.Z);
+  DPG_ALLOC(h->d_z, sizeof(double2) * tot.u);
+  if (prm->flags & DPG_FLAG_ADJOINT) DPG_ALLOC(h->d_L1, sizeof(double2) * tot.L1);
+  DPG_ALLOC(h->d_sig, sizeof(int) * ne);
+  DPG_ALLOC(h->d_rsig, sizeof(RSig) * std::max<size_t>(1, h->rsig.size()));
+  DPG_ALLOC(h->d_rint, sizeof(int32_t) * std::max<size_t>(1, rint.size()));
+  DPG_ALLOC(h->d_rdbl, sizeof(double) * std::max<size_t>(1, rdbl.size()));
   DPG_ALLOC(h->d_rowptr, sizeof(int64_t) * (nfree + 1));
   DPG_ALLOC(h->d_row2blk, sizeof(int32_t) * nfree);
   DPG_ALLOC(h->d_blk, sizeof(int4) * h->nblk);
@@ -558,10 +754,15 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   DPG_ALLOC(h->d_cols, sizeof(int32_t) * h->cols.size());
   DPG_ALLOC(h->d_val, sizeof(double2) * h->nnz);
   DPG_ALLOC(h->d_b, sizeof(double2) * nfree);
-  DPG_ALLOC(h->d_trfun, sizeof(int) * nt);
-  DPG_ALLOC(h->d_Xref, sizeof(double) * S.n_f * S.n_f);
-  DPG_ALLOC(h->d_Tf, sizeof(double) * 6 * S.n_f * nt);
-  DPG_ALLOC(h->d_Tall, sizeof(double) * S.n_f * nt);
+  for (Group& G : h->grp) {
+    const Sizes& Z = G.sz;
+    DPG_ALLOC(G.d_trfun, sizeof(int) * Z.nt);
+    DPG_ALLOC(G.d_Xref, sizeof(double) * Z.n_f * Z.n_f);
+    DPG_ALLOC(G.d_Tf, sizeof(double) * 6 * Z.n_f * Z.nt);
+    DPG_ALLOC(G.d_Tall, sizeof(double) * Z.n_f * Z.nt);
+    DPG_ALLOC(G.d_elems, sizeof(int) * G.elems.size());
+    DPG_ALLOC(G.d_color_elems, sizeof(int) * G.elems.size());
+  }
 #undef DPG_ALLOC
   std::vector<double2> eps(ne), mu(ne);
   for (int e = 0; e < ne; ++e) {
@@ -572,9 +773,24 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_eps, eps.data(), sizeof(double2) * ne, cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_mu, mu.data(), sizeof(double2) * ne, cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_fbc, m->face_bc, 6 * (size_t)ne, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_off, h->off.data(), sizeof(ElemOff) * (ne + 1), cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_l2g, h->l2g.data(), sizeof(int32_t) * h->l2g.size(), cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_xfix, xfix.data(), sizeof(double2) * xfix.size(), cudaMemcpyHostToDevice, s));
-  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_color_elems, h->color_elems.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, s));
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_sig, h->elem_sig.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, s));
+  if (!h->rsig.empty()) {
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_rsig, h->rsig.data(), sizeof(RSig) * h->rsig.size(), cudaMemcpyHostToDevice, s));
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_rint, rint.data(), sizeof(int32_t) * rint.size(), cudaMemcpyHostToDevice, s));
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_rdbl, rdbl.data(), sizeof(double) * rdbl.size(), cudaMemcpyHostToDevice, s));
+  }
+  for (Group& G : h->grp) {
+    const std::vector<int> trf = trace_functions(G.sz.r);
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(G.d_trfun, trf.data(), sizeof(int) * trf.size(), cudaMemcpyHostToDevice, s));
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(G.d_elems, G.elems.data(), sizeof(int) * G.elems.size(), cudaMemcpyHostToDevice, s));
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(G.d_color_elems, G.color_elems_host.data(), sizeof(int) * G.elems.size(),
+                                    cudaMemcpyHostToDevice, s));
+    // the per-group host vector trf dies here: wait for its copy
+    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
   if (!h->robin.empty())
     DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_robin, h->robin.data(), sizeof(dpg_robin_group) * h->robin.size(),
                                     cudaMemcpyHostToDevice, s));
@@ -585,11 +801,19 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
                                   cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_cols, h->cols.data(), sizeof(int32_t) * h->cols.size(), cudaMemcpyHostToDevice,
                                   s));
-  DPG_CUDA_TRY(h, cudaMemcpyAsync(h->d_trfun, trf.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
-  DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * ne, s));
+  DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * (ne + 1), s));
   // the host vectors above die at return: wait for the copies
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
   return DPG_OK;
+}
+
+// Split every group's elements into lossless (real path) and the others.
+void classify_elements(dpg_handle* h) {
+  for (Group& G : h->grp) {
+    G.real_elems.clear();
+    G.cplx_elems.clear();
+    for (int e : G.elems) (h->is_real[e] ? G.real_elems : G.cplx_elems).push_back(e);
+  }
 }
 
 }  // namespace dpg

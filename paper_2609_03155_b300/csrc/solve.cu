@@ -37,15 +37,19 @@ __device__ __forceinline__ int64_t csr_pos(const int64_t* __restrict__ rowptr, c
 // One block per element of one colour: elements of a colour share no
 // unknowns, so the plain read-modify-write below has no race and the sum
 // order per entry is the fixed colour order.
-__global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict__ elems, const int32_t* __restrict__ l2g,
-                                                  const double2* __restrict__ xfix, const double2* __restrict__ Sst,
-                                                  const double2* __restrict__ sst, const int64_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict__ elems, const ElemOff* __restrict__ off,
+                                                  const int32_t* __restrict__ l2g, const double2* __restrict__ xfix,
+                                                  const double2* __restrict__ Sst, const double2* __restrict__ sst,
+                                                  const int64_t* __restrict__ rowptr,
                                                   const int32_t* __restrict__ row2blk, const int4* __restrict__ blk,
                                                   const int64_t* __restrict__ colptr, const int32_t* __restrict__ cols,
                                                   double2* val, double2* b) {
   const int e = elems[blockIdx.x];
-  const int32_t* g = l2g + (size_t)e * nh;
-  const double2* Se = Sst + (size_t)e * nh * nh;
+  const ElemOff of = off[e];
+  const int32_t* g = l2g + of.h;
+  const double2* Se = Sst + of.S;
+  sst += of.h;
+  xfix += of.h;
   for (int t = threadIdx.x; t < nh * nh; t += blockDim.x) {
     const int i = t / nh, j = t - i * nh;
     const int gi = g[i], gj = g[j];
@@ -56,10 +60,10 @@ __global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict_
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     const int gi = g[i];
     if (gi < 0) continue;
-    double2 acc = sst[(size_t)e * nh + i];
+    double2 acc = sst[i];
     for (int j = 0; j < nh; ++j)
       if (g[j] == -1) {  // Dirichlet lifting: b -= S_{i,fixed} x_D
-        double2 pr = c_mul(Se[(size_t)i * nh + j], xfix[(size_t)e * nh + j]);
+        double2 pr = c_mul(Se[(size_t)i * nh + j], xfix[j]);
         acc.x -= pr.x;
         acc.y -= pr.y;
       }
@@ -68,18 +72,19 @@ __global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict_
 }
 
 int assemble_system(dpg_handle* h, cudaStream_t s) {
-  const Sizes& S = h->sz;
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_val, 0, sizeof(double2) * h->nnz, s));
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_b, 0, sizeof(double2) * h->n, s));
-  const int ncol = (int)h->color_off.size() - 1;
-  for (int c = 0; c < ncol; ++c) {
-    int cnt = h->color_off[c + 1] - h->color_off[c];
-    if (cnt == 0) continue;
-    k_assemble<<<cnt, 256, 0, s>>>(S.n_h, h->d_color_elems + h->color_off[c], h->d_l2g, h->d_xfix, h->d_S, h->d_s,
-                                   h->d_rowptr, h->d_row2blk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_val,
-                                   h->d_b);
-    h->launches += 1;
-  }
+  // colour by colour; within a colour one launch per order group (the
+  // elements of one colour share no unknowns, whatever their group)
+  for (int c = 0; c < h->ncolor; ++c)
+    for (const Group& G : h->grp) {
+      const int cnt = G.color_off[c + 1] - G.color_off[c];
+      if (cnt == 0) continue;
+      k_assemble<<<cnt, 256, 0, s>>>(G.sz.n_h, G.d_color_elems + G.color_off[c], h->d_off, h->d_l2g, h->d_xfix,
+                                     h->d_S, h->d_s, h->d_rowptr, h->d_row2blk, h->d_blk, h->d_blk_colptr, h->d_cols,
+                                     h->d_val, h->d_b);
+      h->launches += 1;
+    }
   DPG_CUDA_TRY(h, cudaGetLastError());
   h->have_system = true;
   h->have_val32 = false;
@@ -204,36 +209,39 @@ __device__ __forceinline__ double2 mkv(double a, double b, double2*) { return ma
 __device__ __forceinline__ float2 mkv(double a, double b, float2*) { return make_float2((float)a, (float)b); }
 
 // y_row = (A x)_row by one warp; the row's columns are its entity's list.
-// Returns, on lane 0, y_row; the caller accumulates Re(x_row^* y_row).
-template <typename V>
-__device__ __forceinline__ V row_spmv(const SysView& S, int64_t row, const V* __restrict__ val, const V* __restrict__ x) {
-  using R = typename RealOf<V>::T;
+// Products and the row sum in the matrix precision Mv.
+template <typename V, typename Mv>
+__device__ __forceinline__ V row_spmv(const SysView& S, int64_t row, const Mv* __restrict__ val, const V* __restrict__ x) {
+  using R = typename RealOf<Mv>::T;
   const int lane = threadIdx.x & 31;
   const int b = S.row2blk[row];
   const int W = S.blk[b].z;
   const int32_t* c = S.cols + S.colptr[b];
-  const V* v = val + S.rowptr[row];
-  R yr = 0, yi = 0;
+  const Mv* v = val + S.rowptr[row];
+  R ar = 0, ai = 0;
   int k = lane;
   // four independent column chains in flight per lane
   for (; k + 96 < W; k += 128) {
     const int c0 = c[k], c1 = c[k + 32], c2 = c[k + 64], c3 = c[k + 96];
-    const V a0 = v[k], a1 = v[k + 32], a2 = v[k + 64], a3 = v[k + 96];
+    const Mv a0 = v[k], a1 = v[k + 32], a2 = v[k + 64], a3 = v[k + 96];
     const V x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
-    yr = fma(a0.x, x0.x, fma(-a0.y, x0.y, yr));
-    yi = fma(a0.x, x0.y, fma(a0.y, x0.x, yi));
-    yr = fma(a1.x, x1.x, fma(-a1.y, x1.y, yr));
-    yi = fma(a1.x, x1.y, fma(a1.y, x1.x, yi));
-    yr = fma(a2.x, x2.x, fma(-a2.y, x2.y, yr));
-    yi = fma(a2.x, x2.y, fma(a2.y, x2.x, yi));
-    yr = fma(a3.x, x3.x, fma(-a3.y, x3.y, yr));
-    yi = fma(a3.x, x3.y, fma(a3.y, x3.x, yi));
+    ar = fma(a0.x, (R)x0.x, fma(-a0.y, (R)x0.y, ar));
+    ai = fma(a0.x, (R)x0.y, fma(a0.y, (R)x0.x, ai));
+    ar = fma(a1.x, (R)x1.x, fma(-a1.y, (R)x1.y, ar));
+    ai = fma(a1.x, (R)x1.y, fma(a1.y, (R)x1.x, ai));
+    ar = fma(a2.x, (R)x2.x, fma(-a2.y, (R)x2.y, ar));
+    ai = fma(a2.x, (R)x2.y, fma(a2.y, (R)x2.x, ai));
+    ar = fma(a3.x, (R)x3.x, fma(-a3.y, (R)x3.y, ar));
+    ai = fma(a3.x, (R)x3.y, fma(a3.y, (R)x3.x, ai));
   }
   for (; k < W; k += 32) {
-    const V a = v[k], xv = x[c[k]];
-    yr = fma(a.x, xv.x, fma(-a.y, xv.y, yr));
-    yi = fma(a.x, xv.y, fma(a.y, xv.x, yi));
+    const Mv a = v[k];
+    const V xv = x[c[k]];
+    ar = fma(a.x, (R)xv.x, fma(-a.y, (R)xv.y, ar));
+    ai = fma(a.x, (R)xv.y, fma(a.y, (R)xv.x, ai));
   }
+  R yr = ar, yi = ai;
+  // warp sum in the matrix precision
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     yr += __shfl_xor_sync(0xffffffffu, yr, o);
@@ -294,13 +302,16 @@ __device__ __forceinline__ void block_precond(const SysView& S, int b, int preco
 }
 
 // One whole CG solve of A x = r0 (x = 0 at entry, r holds r0 at entry).
-template <typename V>
-__global__ void __launch_bounds__(CG_THREADS) k_cg_persistent(SysView S, const V* __restrict__ val, V* x, V* r, V* p,
+// V: precision of the vectors and recurrences; Mv: precision of the stored
+// matrix and of the SpMV products (FP32 values with FP64 recurrences keeps the
+// convergence rate of FP64 CG at the bandwidth of an FP32 matrix).
+template <typename V, typename Mv>
+__global__ void __launch_bounds__(CG_THREADS) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
                                                              V* Ap, V* z, int precond,
                                                              const typename RealOf<V>::T* __restrict__ dinv,
                                                              const V* __restrict__ binv, double* red, CgState* st) {
   using R = typename RealOf<V>::T;
-  extern __shared__ unsigned char cg_smem[];
+  extern __shared__ __align__(16) unsigned char cg_smem[];
   V* rs = reinterpret_cast<V*>(cg_smem) + (threadIdx.x >> 5) * S.dmax;
   const int G = gridDim.x;
   double* redA = red;          // pAp partials
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_persistent(SysView S, const V
     // A: Ap = A p and Re(p^H A p)
     double pap = 0;
     for (int64_t row = gw; row < S.n; row += warps) {
-      const V y = row_spmv<V>(S, row, val, p);
+      const V y = row_spmv<V, Mv>(S, row, val, p);
       if ((threadIdx.x & 31) == 0) {
         Ap[row] = y;
         const V pr = p[row];
@@ -395,7 +406,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_residual(SysView S, const double
   const int gw = blockIdx.x * (CG_THREADS / 32) + (threadIdx.x >> 5);
   double acc = 0.0;
   for (int64_t row = gw; row < S.n; row += warps) {
-    const double2 ax = x ? row_spmv<double2>(S, row, val, x) : make_double2(0.0, 0.0);
+    const double2 ax = x ? row_spmv<double2, double2>(S, row, val, x) : make_double2(0.0, 0.0);
     if ((threadIdx.x & 31) == 0) {
       const double2 bv = b[row];
       const double2 rv = make_double2(bv.x - ax.x, bv.y - ax.y);
@@ -524,7 +535,7 @@ static int ensure_buf(dpg_handle* h, void** p, size_t bytes) {
   return DPG_OK;
 }
 
-template <typename V>
+template <typename V, typename Mv>
 static int persistent_grid(dpg_handle* h, int* grid, size_t smem) {
   int dev = 0, sms = 0, per = 0, coop = 0;
   DPG_CUDA_TRY(h, cudaGetDevice(&dev));
@@ -534,21 +545,22 @@ static int persistent_grid(dpg_handle* h, int* grid, size_t smem) {
     h->err = "device does not support cooperative launches";
     return DPG_ERR_UNSUPPORTED;
   }
-  DPG_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<V>, CG_THREADS, smem));
+  DPG_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<V, Mv>, CG_THREADS, smem));
   *grid = std::max(1, std::min(per, 8) * sms);
   return DPG_OK;
 }
 
 // One persistent solve of A d = r0 (d = 0 at entry; r holds r0 at entry).
-template <typename V>
-static int run_persistent(dpg_handle* h, const V* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
+template <typename V, typename Mv>
+static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
                           const typename RealOf<V>::T* dinv, const V* binv, double tol2, int max_iter,
                           cudaStream_t s, int* iters, double* rr_out) {
   int grid = 0;
-  const size_t smem = sizeof(V) * (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax);
+  const size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
   if (smem > 48 * 1024)
-    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_cg_persistent<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int rc = persistent_grid<V>(h, &grid, smem);
+    DPG_CUDA_TRY(h,
+                 cudaFuncSetAttribute(k_cg_persistent<V, Mv>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int rc = persistent_grid<V, Mv>(h, &grid, smem);
   if (rc) return rc;
   CgState host{};
   host.tol2 = tol2;
@@ -558,10 +570,28 @@ static int run_persistent(dpg_handle* h, const V* val, V* x, V* r, V* p, V* Ap, 
   SysView S = sys_view(h);
   double* red = h->d_red;
   void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st};
-  DPG_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_cg_persistent<V>, dim3(grid), dim3(CG_THREADS), args, smem, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->timing) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  DPG_CUDA_TRY(h,
+               cudaLaunchCooperativeKernel((void*)k_cg_persistent<V, Mv>, dim3(grid), dim3(CG_THREADS), args, smem, s));
   h->launches += 1;
+  if (h->timing) cudaEventRecord(e1, s);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(&host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (h->timing) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cgk_ms += ms;
+    h->cgk_launches += 1;
+    h->cgk_iters += host.iters;
+    if (sizeof(Mv) == sizeof(float2)) h->cgk_fp32 = true;
+  }
   if (host.status != 0) {
     h->err = "a grid barrier of the CG kernel timed out";
     return DPG_ERR_TIMEOUT;
@@ -610,6 +640,26 @@ static int prepare_preconditioner(dpg_handle* h, cudaStream_t s) {
   h->have_binv = true;
   h->have_dinv = true;
   return DPG_OK;
+}
+
+// Algorithmic bytes of one CG iteration: the matrix values (16 B per complex
+// non-zero in FP64, 8 B in FP32), the per-entity column lists, the
+// preconditioner data, and the vector traffic of the three phases
+// (SpMV reads p once and writes Ap; the update reads x, r, p, Ap and writes
+// x, r, z; the direction update reads z, p and writes p): 13 vector passes.
+int64_t cg_bytes_per_iteration(const dpg_handle* h, int mode) {
+  const bool ir = (mode & DPG_CG_IR_FP32) != 0;
+  const int64_t mb = ir ? 8 : 16, vb = ir ? 8 : 16;
+  int64_t ncol = (int64_t)h->cols.size();
+  int64_t bytes = mb * h->nnz + 4 * ncol + 13 * vb * h->n;
+  if (mode & DPG_CG_BLOCK_JACOBI) {
+    int64_t inv = 0;
+    for (const int4& B : h->blk) inv += (int64_t)B.y * B.y;
+    bytes += vb * inv;
+  } else if (mode & DPG_CG_JACOBI) {
+    bytes += (ir ? 4 : 8) * h->n;
+  }
+  return bytes;
 }
 
 int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, double inner_rtol, double2* x,
@@ -684,14 +734,14 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
       const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
       k_to_f32<<<1184, 256, 0, s>>>((int64_t)n, h->d_r, h->d_r32);
       h->launches += 1;
-      rc = run_persistent<float2>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32, precond,
-                                  h->d_dinv32, h->d_binv32, itol * itol, max_iter - total_iters, s, &it, &rr);
+      rc = run_persistent<float2, float2>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32, precond,
+                                          h->d_dinv32, h->d_binv32, itol * itol, max_iter - total_iters, s, &it, &rr);
       if (rc) return rc;
       k_add_correction<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_x32);
     } else {
       const double itol = 0.5 * tol;
-      rc = run_persistent<double2>(h, h->d_val, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond, h->d_dinv,
-                                   h->d_binv, itol * itol, max_iter - total_iters, s, &it, &rr);
+      rc = run_persistent<double2, double2>(h, h->d_val, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond,
+                                            h->d_dinv, h->d_binv, itol * itol, max_iter - total_iters, s, &it, &rr);
       if (rc) return rc;
       k_add_correction64<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_d64);
     }
@@ -738,20 +788,22 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
 // ------------------------------------------------------------ estimate --
 // Per element: uhat_K gathered from x (free) and the Dirichlet values,
 // eta^2 = c - 2 Re(uhat^H s) + uhat^H S uhat, u = z - Z uhat.
-__global__ void __launch_bounds__(256) k_estimate(int nh, int nu, const int32_t* __restrict__ l2g,
+__global__ void __launch_bounds__(256) k_estimate(int nh, int nu, const int* __restrict__ elems,
+                                                  const ElemOff* __restrict__ off, const int32_t* __restrict__ l2g,
                                                   const double2* __restrict__ xfix, const double2* __restrict__ xhat,
                                                   const double2* __restrict__ Sst, const double2* __restrict__ sst,
                                                   const double* __restrict__ cst, const double2* __restrict__ Zst,
                                                   const double2* __restrict__ zst, double2* u_out, double* eta2) {
   extern __shared__ double2 su[];
-  const int e = blockIdx.x;
+  const int e = elems[blockIdx.x];
+  const ElemOff of = off[e];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int t = threadIdx.x; t < nh; t += blockDim.x) {
-    const int g = l2g[(size_t)e * nh + t];
-    su[t] = g >= 0 ? xhat[g] : (g == -1 ? xfix[(size_t)e * nh + t] : make_double2(0.0, 0.0));
+    const int g = l2g[of.h + t];
+    su[t] = g >= 0 ? xhat[g] : (g == -1 ? xfix[of.h + t] : make_double2(0.0, 0.0));
   }
   __syncthreads();
-  const double2* Se = Sst + (size_t)e * nh * nh;
+  const double2* Se = Sst + of.S;
   double q = 0.0;  // sum over rows of Re(conj(uhat_i) (S uhat)_i)
   for (int i = wid; i < nh; i += nw) {
     double yr = 0.0, yi = 0.0;
@@ -762,11 +814,11 @@ __global__ void __launch_bounds__(256) k_estimate(int nh, int nu, const int32_t*
     }
     yr = warp_sum(yr);
     yi = warp_sum(yi);
-    const double2 ui = su[i], si = sst[(size_t)e * nh + i];
+    const double2 ui = su[i], si = sst[of.h + i];
     q += (lane == 0) ? (ui.x * yr + ui.y * yi) - 2.0 * (ui.x * si.x + ui.y * si.y) : 0.0;
   }
   if (u_out) {
-    const double2* Ze = Zst + (size_t)e * nu * nh;
+    const double2* Ze = Zst + of.Z;
     for (int i = wid; i < nu; i += nw) {
       double yr = 0.0, yi = 0.0;
       for (int j = lane; j < nh; j += 32) {
@@ -777,8 +829,8 @@ __global__ void __launch_bounds__(256) k_estimate(int nh, int nu, const int32_t*
       yr = warp_sum(yr);
       yi = warp_sum(yi);
       if (lane == 0) {
-        const double2 zi = zst[(size_t)e * nu + i];
-        u_out[(size_t)e * nu + i] = make_double2(zi.x - yr, zi.y - yi);
+        const double2 zi = zst[of.u + i];
+        u_out[of.u + i] = make_double2(zi.x - yr, zi.y - yi);
       }
     }
   }
@@ -811,6 +863,17 @@ __global__ void k_sqrt_sum(int n, const double* __restrict__ eta2, double* eta, 
   }
 }
 
+// eta_K^2 of every element into eta2[e] (and u), one launch per order group.
+static void launch_estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta2, cudaStream_t s) {
+  for (const Group& G : h->grp) {
+    const Sizes& S = G.sz;
+    k_estimate<<<(int)G.elems.size(), 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, G.d_elems, h->d_off, h->d_l2g,
+                                                                        h->d_xfix, xhat, h->d_S, h->d_s, h->d_c,
+                                                                        h->d_Z, h->d_z, u, eta2);
+    h->launches += 1;
+  }
+}
+
 int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global, cudaStream_t s) {
   if (!h->have_elements) {
     h->err = "dpg_estimate before dpg_element_batch";
@@ -820,13 +883,11 @@ int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double
     h->err = "null xhat";
     return DPG_ERR_ARG;
   }
-  const Sizes& S = h->sz;
   double* d_eta2 = nullptr;
   DPG_CUDA_TRY(h, cudaMallocAsync(&d_eta2, sizeof(double) * (h->ne + 1), s));
-  k_estimate<<<h->ne, 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, h->d_l2g, h->d_xfix, xhat, h->d_S, h->d_s,
-                                                         h->d_c, h->d_Z, h->d_z, u, d_eta2);
+  launch_estimate(h, xhat, u, d_eta2, s);
   k_sqrt_sum<<<1, 1024, 0, s>>>(h->ne, d_eta2, eta, d_eta2 + h->ne);
-  h->launches += 2;
+  h->launches += 1;
   DPG_CUDA_TRY(h, cudaGetLastError());
   if (eta_global) {
     double tot = 0;
@@ -899,11 +960,9 @@ int estimate_noalloc(dpg_handle* h, const double2* xhat, double2* u, double* eta
   double* scratch = nullptr;
   int rc = noalloc_scratch(h, &scratch);
   if (rc) return rc;
-  const Sizes& S = h->sz;
-  k_estimate<<<h->ne, 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, h->d_l2g, h->d_xfix, xhat, h->d_S, h->d_s,
-                                                         h->d_c, h->d_Z, h->d_z, u, scratch);
+  launch_estimate(h, xhat, u, scratch, s);
   k_sqrt_sum<<<1, 1024, 0, s>>>(h->ne, scratch, eta, scratch + h->ne);
-  h->launches += 2;
+  h->launches += 1;
   DPG_CUDA_TRY(h, cudaGetLastError());
   if (eta_global) {
     double tot = 0;

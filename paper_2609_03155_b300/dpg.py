@@ -40,10 +40,16 @@ def _dirichlet_groups(mesh):
     return arr
 
 
+def element_sizes(p, dp=1):
+    """(n_v, n_u, n_h) of one element of trial degree p."""
+    r, rt = p + 1, p + 1 + dp
+    return 6 * rt * (rt + 1) ** 2, 6 * (p + 1) ** 3, 24 * r * r
+
+
 class DPG:
     """A DPG discretisation living on the current CUDA device (dpg_handle)."""
 
-    def __init__(self, mesh, alpha=1.0, chunk=0, adjoint=False, stream=None):
+    def __init__(self, mesh, alpha=1.0, chunk=0, adjoint=False, precision=0, stream=None):
         L = _lib.lib()
         self.mesh = mesh
         keep = dict(
@@ -62,12 +68,14 @@ class DPG:
             elem_mu=keep['mu'].ctypes.data, face_bc=keep['bc'].ctypes.data, face_grp=keep['grp'].ctypes.data,
             n_robin=len(mesh.robin), robin=C.cast(rob, C.POINTER(_lib.dpg_robin_group)),
             n_dirichlet=len(mesh.dirichlet), dirichlet=C.cast(dirg, C.POINTER(_lib.dpg_dirichlet_group)))
-        prm = _lib.dpg_params(omega=float(mesh.omega), alpha=float(alpha), dp=1, precision=0, chunk=int(chunk),
+        prm = _lib.dpg_params(omega=float(mesh.omega), alpha=float(alpha), dp=1, precision=int(precision), chunk=int(chunk),
                               flags=_lib.DPG_FLAG_ADJOINT if adjoint else 0)
         h = C.c_void_p()
         check(L.dpg_setup_mesh(C.byref(h), C.byref(desc), C.byref(prm), stream_handle(stream)))
         self.h = h
         self.n, self.nnz, self.n_elem, self.n_v, self.n_u, self.n_h = self.sizes()
+        self.p_elem, self.u_off, self.h_off = self.element_layout()
+        self.uniform = bool(np.all(self.p_elem == self.p_elem[0]))
 
     # ---- ABI calls -----------------------------------------------------------
     def sizes(self):
@@ -77,6 +85,14 @@ class DPG:
                                    C.byref(nh)), self.h)
         return n.value, nnz.value, ne.value, nv.value, nu.value, nh.value
 
+    def element_layout(self):
+        """Per-element trial degree and the offsets of u and of the trace map (n_elem + 1 each)."""
+        pe = np.empty(self.n_elem, np.int8)
+        uo = np.empty(self.n_elem + 1, np.int64)
+        ho = np.empty(self.n_elem + 1, np.int64)
+        check(_lib.lib().dpg_element_layout(self.h, ptr(pe), ptr(uo), ptr(ho)), self.h)
+        return pe, uo, ho
+
     def element_batch(self, stream=None):
         check(_lib.lib().dpg_element_batch(self.h, _lib.DPG_PASS_ASSEMBLE, stream_handle(stream)), self.h)
 
@@ -84,7 +100,7 @@ class DPG:
         check(_lib.lib().dpg_assemble(self.h, stream_handle(stream)), self.h)
 
     def cg_solve(self, x=None, b=None, mode=_lib.DPG_CG_FP64, rtol=1e-10, atol=0.0, max_iter=100000,
-                 inner_rtol=1e-4, stream=None, raise_on_nonconvergence=True):
+                 inner_rtol=1e-3, stream=None, raise_on_nonconvergence=True):
         if x is None:
             x = torch.zeros(self.n, dtype=torch.complex128, device='cuda')
         rep = _lib.dpg_cg_report()
@@ -96,19 +112,46 @@ class DPG:
                        converged=bool(rep.converged))
 
     def estimate(self, xhat, want_u=True, stream=None):
-        u = torch.empty(self.n_elem * self.n_u, dtype=torch.complex128, device='cuda') if want_u else None
+        """u (n_elem x n_u for one degree, else flat at u_off), eta_K, sqrt(sum eta_K^2)."""
+        u = torch.empty(int(self.u_off[-1]), dtype=torch.complex128, device='cuda') if want_u else None
         eta = torch.empty(self.n_elem, dtype=torch.float64, device='cuda')
         tot = C.c_double()
         check(_lib.lib().dpg_estimate(self.h, ptr(xhat), ptr(u), ptr(eta), C.byref(tot), stream_handle(stream)),
               self.h)
-        return (u.view(self.n_elem, self.n_u) if u is not None else None), eta, tot.value
+        if u is not None and self.uniform:
+            u = u.view(self.n_elem, self.n_u)
+        return u, eta, tot.value
 
     def update_elements(self, corners=None, eps=None, mu=None, stream=None):
         """Host -> device copy of per-element corners (n_elem x 8 x 3), eps, mu (use pinned tensors)."""
         check(_lib.lib().dpg_update_elements(self.h, ptr(corners), ptr(eps), ptr(mu), stream_handle(stream)), self.h)
 
+    def cg_bytes_per_iteration(self, mode):
+        b = C.c_int64()
+        check(_lib.lib().dpg_cg_bytes_per_iteration(self.h, int(mode), C.byref(b)), self.h)
+        return b.value
+
     def set_real_path(self, enable=True):
         check(_lib.lib().dpg_set_real_path(self.h, int(enable)), self.h)
+
+    def set_graph(self, enable=True):
+        check(_lib.lib().dpg_set_graph(self.h, int(enable)), self.h)
+
+    def group_info(self):
+        """[(p, n_elem, chunk)] per order group."""
+        ng = C.c_int32()
+        p, n, cap = (np.zeros(4, np.int32) for _ in range(3))
+        check(_lib.lib().dpg_group_info(self.h, C.byref(ng), ptr(p), ptr(n), ptr(cap)), self.h)
+        return [(int(p[g]), int(n[g]), int(cap[g])) for g in range(ng.value)]
+
+    def autotune(self, max_workspace_gb=40.0, stream=None):
+        """Measured chunk size per order group: {p: (chunk, ms per element)}."""
+        groups = self.group_info()
+        caps = np.zeros(len(groups), np.int32)
+        ms = np.zeros(len(groups), np.float32)
+        check(_lib.lib().dpg_autotune(self.h, float(max_workspace_gb) * 2.0 ** 30, ptr(caps), ptr(ms),
+                                      stream_handle(stream)), self.h)
+        return {g[0]: (int(caps[k]), float(ms[k])) for k, g in enumerate(groups)}
 
     def timing_enable(self, enable=True):
         check(_lib.lib().dpg_timing_enable(self.h, int(enable)), self.h)
@@ -129,20 +172,25 @@ class DPG:
         return P.value, dre, dim
 
     def trace_map(self):
-        m = np.empty((self.n_elem, self.n_h), dtype=np.int32)
-        fv = np.empty((self.n_elem, self.n_h), dtype=np.complex128)
+        """Trace map and fixed values: n_elem x n_h for one degree, else flat at h_off."""
+        m = np.empty(int(self.h_off[-1]), dtype=np.int32)
+        fv = np.empty(int(self.h_off[-1]), dtype=np.complex128)
         check(_lib.lib().dpg_trace_map(self.h, ptr(m), ptr(fv)), self.h)
+        if self.uniform:
+            return m.reshape(self.n_elem, self.n_h), fv.reshape(self.n_elem, self.n_h)
         return m, fv
 
     def element_dump(self, ids, stream=None):
+        """G, B, B-hat, l, S, s of elements that share one trial degree (S, s in the trace slots)."""
         ids = np.ascontiguousarray(ids, dtype=np.int32)
         k = len(ids)
-        G = np.empty((k, self.n_v, self.n_v), np.complex128)
-        B = np.empty((k, self.n_v, self.n_u), np.complex128)
-        Bh = np.empty((k, self.n_v, self.n_h), np.complex128)
-        l = np.empty((k, self.n_v), np.complex128)
-        S = np.empty((k, self.n_h, self.n_h), np.complex128)
-        s = np.empty((k, self.n_h), np.complex128)
+        nv, nu, nh = element_sizes(int(self.p_elem[ids[0]]))
+        G = np.empty((k, nv, nv), np.complex128)
+        B = np.empty((k, nv, nu), np.complex128)
+        Bh = np.empty((k, nv, nh), np.complex128)
+        l = np.empty((k, nv), np.complex128)
+        S = np.empty((k, nh, nh), np.complex128)
+        s = np.empty((k, nh), np.complex128)
         check(_lib.lib().dpg_element_dump(self.h, ptr(ids), k, ptr(G), ptr(B), ptr(Bh), ptr(l), ptr(S), ptr(s),
                                           stream_handle(stream)), self.h)
         return dict(G=G, B=B, Bh=Bh, l=l, S=S, s=s)
@@ -165,6 +213,17 @@ class DPG:
             self.destroy()
         except Exception:
             pass
+
+
+def tc_gemm(A, B, split=1, upper_only=False, C=None):
+    """A^T B through the tensor-core contraction kernel (check hook; host float64 arrays)."""
+    A = np.ascontiguousarray(A, np.float64)
+    B = np.ascontiguousarray(B, np.float64)
+    Kd, Ma = A.shape
+    Nb = B.shape[1]
+    C = np.zeros((Ma, Nb)) if C is None else np.ascontiguousarray(C, np.float64).copy()
+    check(_lib.lib().dpg_tc_gemm(split, Ma, Nb, Kd, ptr(A), ptr(B), ptr(C), int(upper_only)))
+    return C
 
 
 def probe_peaks(stream=None):

@@ -189,3 +189,83 @@ def sphere_obstacle(mesh, center=(0.5, 0.5, 0.5), radius=0.2, eps=20.0 + 5.0j):
     mesh.eps = mesh.eps.copy()
     mesh.eps[mask] = eps
     return mask
+
+
+def _graded_unit(n, toward_hi, grade):
+    """n + 1 nodes on [0, 1], denser toward 1 (toward_hi) or 0, spacing ratio set by grade >= 1."""
+    t = np.arange(n + 1, dtype=np.float64) / n
+    return 1.0 - (1.0 - t) ** grade if toward_hi else t ** grade
+
+
+def order_mix(ne, fractions, seed, stream=5):
+    """Trial degrees 1..len(fractions) in exact proportions (rounded), seeded permutation."""
+    counts = [int(np.floor(f * ne)) for f in fractions]
+    counts[0] += ne - sum(counts)
+    p = np.concatenate([np.full(c, k + 1, dtype=np.int8) for k, c in enumerate(counts)])
+    perm = np.argsort(uniform01(seed, stream, ne), kind='stable')
+    out = np.empty(ne, dtype=np.int8)
+    out[perm] = p
+    return out
+
+
+def fichera_cavity(n_unit, grade=1.0, omega=5.0, p=None, mix=(0.4, 0.3, 0.2, 0.1), seed=20260904,
+                   name="fichera"):
+    """Fichera-corner cavity ((0,2)^3 minus [0,1]^3, plus [1,2]^2 x [2,3]) on a graded tensor grid.
+
+    Every unit interval of the axes is split into n_unit cells, graded toward
+    the re-entrant corner (1, 1, 1) and the re-entrant edges at x3 = 2 (grade
+    1 = uniform).  The grid is conforming: the local refinement of an adaptive
+    mesh is imitated by the grading, not by hanging faces.  PEC walls, and on
+    the top face x3 = 3 the excitation n x E = (sin(pi x2), 0, 0) (Sec. 4.2).
+    Trial degrees: p for all elements if given, else drawn in the proportions
+    ``mix`` for p = 1, 2, ... (seeded permutation, stream 5).
+    """
+    lo = _graded_unit(n_unit, True, grade)
+    hi = 1.0 + _graded_unit(n_unit, False, grade)
+    xs = np.concatenate([lo, hi[1:]])                       # [0, 2]
+    zs = np.concatenate([lo, hi[1:], 2.0 + _graded_unit(n_unit, False, grade)[1:]])  # [0, 3]
+    nx, nz = xs.size - 1, zs.size - 1
+    Z, Y, X = np.meshgrid(zs, xs, xs, indexing='ij')
+    allv = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    vid = lambda i, j, k: (k * (nx + 1) + j) * (nx + 1) + i
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(nx), np.arange(nx), indexing='ij')
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    c = np.stack([0.5 * (xs[i] + xs[i + 1]), 0.5 * (xs[j] + xs[j + 1]), 0.5 * (zs[k] + zs[k + 1])], axis=1)
+    lower = (c[:, 2] < 2.0) & ~((c[:, 0] < 1.0) & (c[:, 1] < 1.0) & (c[:, 2] < 1.0))
+    top = (c[:, 0] > 1.0) & (c[:, 1] > 1.0) & (c[:, 2] > 2.0)
+    keep = lower | top
+    i, j, k = i[keep], j[keep], k[keep]
+    elem = np.zeros((i.size, 8), dtype=np.int64)
+    for v in range(8):
+        elem[:, v] = vid(i + (v & 1), j + ((v >> 1) & 1), k + ((v >> 2) & 1))
+    used, inv = np.unique(elem.ravel(), return_inverse=True)
+    vert = allv[used]
+    elem = inv.reshape(elem.shape).astype(np.int32)
+    ne = elem.shape[0]
+    # boundary faces: faces that no other element shares
+    bc = np.zeros((ne, 6), dtype=np.int8)
+    grp = np.zeros((ne, 6), dtype=np.int16)
+    keys = {}
+    for d in range(3):
+        for s in (0, 1):
+            f = 2 * d + s
+            cs = [v for v in range(8) if ((v >> d) & 1) == s]
+            fk = np.sort(elem[:, cs], axis=1)
+            for e in range(ne):
+                t = tuple(fk[e])
+                keys[t] = keys.get(t, 0) + 1
+    for d in range(3):
+        for s in (0, 1):
+            f = 2 * d + s
+            cs = [v for v in range(8) if ((v >> d) & 1) == s]
+            fk = np.sort(elem[:, cs], axis=1)
+            for e in range(ne):
+                if keys[tuple(fk[e])] == 1:
+                    bc[e, f] = BC_DIRICHLET
+                    ztop = d == 2 and s == 1 and abs(vert[elem[e, cs[0]], 2] - 3.0) < 1e-12
+                    grp[e, f] = 1 if ztop else 0
+    pk = np.full(ne, p, dtype=np.int8) if p is not None else order_mix(ne, mix, seed)
+    return Mesh(vert=vert, elem=elem, p=pk, eps=np.ones(ne, dtype=complex), mu=np.ones(ne, dtype=complex),
+                face_bc=bc, face_grp=grp, omega=omega, robin=[],
+                dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None}, {'kind': DIRICHLET_SIN_PI_X2, 'port': None}],
+                name=name)

@@ -71,12 +71,12 @@ def test_setup_rejects_bad_arguments_before_touching_the_device():
     bad.elem[0] = bad.elem[0][[1, 0, 3, 2, 5, 4, 7, 6]]
     rc, _, msg = _setup(bad)
     assert rc == -2 and "Jacobian" in msg
-    # mixed degrees are rejected explicitly
+    # degrees outside 1..4 are rejected (mixed degrees within it are accepted)
     bad = inputs.waveguide_2d_config(p=1)
     bad.p = bad.p.copy()
-    bad.p[0] = 2
+    bad.p[0] = 5
     rc, _, msg = _setup(bad)
-    assert rc == -9
+    assert rc == -2 and "degree" in msg
     # null handles
     assert L.dpg_element_batch(None, 0, None) == -1
     assert L.dpg_assemble(None, None) == -1

@@ -269,3 +269,65 @@ def fichera_cavity(n_unit, grade=1.0, omega=5.0, p=None, mix=(0.4, 0.3, 0.2, 0.1
                 face_bc=bc, face_grp=grp, omega=omega, robin=[],
                 dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None}, {'kind': DIRICHLET_SIN_PI_X2, 'port': None}],
                 name=name)
+
+
+def refined_box(n, refine, p=1, lengths=(1.0, 1.0, 1.0), omega=5.0, bc="cavity", name="refined_box"):
+    """One level of 2:1 refinement of an n = (nx, ny, nz) box grid: hanging faces and edges.
+
+    refine: coarse cells (i, j, k) split into 8 children.  Vertices live on the
+    lattice of half cells, so children and their coarse neighbours share the
+    corner and mid-edge / mid-face points; a coarse face next to a refined cell
+    is matched by four child faces (a 2:1 hanging face).  Geometry is affine
+    (axis-aligned box).  bc "cavity": PEC walls with n x E = (sin(pi x2), 0, 0)
+    on the top face x3 = lz (the excitation of Sec. 4.2).  p: one degree for all
+    elements, or a callable (element index, is_child) -> degree.
+    """
+    nx, ny, nz = n
+    lx, ly, lz = lengths
+    refine = set(tuple(c) for c in refine)
+    L = (2 * nx + 1, 2 * ny + 1, 2 * nz + 1)
+    lid = lambda i, j, k: (k * L[1] + j) * L[0] + i
+    elems, child = [], []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                if (i, j, k) in refine:
+                    for c in range(8):
+                        a, b, cc = c & 1, (c >> 1) & 1, (c >> 2) & 1
+                        elems.append([lid(2 * i + a + (v & 1), 2 * j + b + ((v >> 1) & 1), 2 * k + cc + ((v >> 2) & 1))
+                                      for v in range(8)])
+                        child.append(True)
+                else:
+                    elems.append([lid(2 * i + 2 * (v & 1), 2 * j + 2 * ((v >> 1) & 1), 2 * k + 2 * ((v >> 2) & 1))
+                                  for v in range(8)])
+                    child.append(False)
+    elem = np.array(elems, dtype=np.int64)
+    used, inv = np.unique(elem.ravel(), return_inverse=True)
+    ii = used % L[0]
+    jj = (used // L[0]) % L[1]
+    kk = used // (L[0] * L[1])
+    vert = np.stack([ii * lx / (2 * nx), jj * ly / (2 * ny), kk * lz / (2 * nz)], axis=1)
+    elem = inv.reshape(elem.shape).astype(np.int32)
+    ne = elem.shape[0]
+    bc_arr = np.zeros((ne, 6), dtype=np.int8)
+    grp = np.zeros((ne, 6), dtype=np.int16)
+    ext = (lx, ly, lz)
+    for e in range(ne):
+        X = vert[elem[e]]
+        for d in range(3):
+            for s in (0, 1):
+                cs = [v for v in range(8) if ((v >> d) & 1) == s]
+                coord = X[cs, d]
+                target = ext[d] if s else 0.0
+                if np.all(np.abs(coord - target) < 1e-12):
+                    bc_arr[e, 2 * d + s] = BC_DIRICHLET
+                    grp[e, 2 * d + s] = 1 if (d == 2 and s == 1) else 0
+    child = np.array(child)
+    if callable(p):
+        pk = np.array([p(e, bool(child[e])) for e in range(ne)], dtype=np.int8)
+    else:
+        pk = np.full(ne, p, dtype=np.int8)
+    return Mesh(vert=vert, elem=elem, p=pk, eps=np.ones(ne, dtype=complex), mu=np.ones(ne, dtype=complex),
+                face_bc=bc_arr, face_grp=grp, omega=omega, robin=[],
+                dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None}, {'kind': DIRICHLET_SIN_PI_X2, 'port': None}],
+                name=name)

@@ -13,7 +13,8 @@ keeps its own nodal trace coefficients, u-hat_K = R_K u-hat:
 * a coefficient on a slave is the master's trace evaluated at the physical node
   (through the master owner's reference coordinates), times the ratio of the
   tangents J_K e_c and J_M e_c (1/2 for a 2:1 child).
-Entity order: min over the elements that touch the entity's geometry of p + 1.
+Entity order: min over the elements that touch the entity's geometry of p + 1,
+and an edge of a master face at most the face's order.
 Geometry is assumed affine (containment and the inverse map use it).
 Uniform meshes without refinement reproduce ``mixed.solve_mixed``.
 """
@@ -123,6 +124,23 @@ class Topology:
             r = min(int(mesh.p[e]) + 1 for e in self.touch[k])
             self.order[m] = min(self.order.get(m, r), r)
         self.normal = {k: self.ents[k][1] for k in keys if self.ents[k][0] == 'F'}
+        # an edge of a master face is capped by the face's order: the face's
+        # trace (edge functions included) must lie in the trace space of every
+        # element touching the face, including lower-degree children on it
+        # (automatic on conforming meshes, where the face's elements contain its edges)
+        for k in keys:
+            if self.ents[k][0] != 'F' or not self.is_master(k):
+                continue
+            e = self.owner[k]
+            d = self.normal[k]
+            sd = int(round(np.mean([_inverse(mesh, e, x)[d] for x in self.ents[k][2]])))
+            for c in range(3):
+                if c == d:
+                    continue
+                eax = [q for q in range(3) if q != c and q != d][0]
+                for send in (0, 1):
+                    em = self.master[_edge_key(mesh, e, c, {d: sd, eax: send})]
+                    self.order[em] = min(self.order[em], self.order[k])
 
     def is_master(self, k):
         return self.master[k] == k

@@ -48,14 +48,18 @@ def config_mesh(name):
     if name == "waveguide2d":
         return inputs.waveguide_2d_config(p=1)
     if name == "cavity3":
-        # jittered unit cavity, p = 3, random lossy permittivity; 24^3 elements
+        # jittered unit cavity, p = 3, random lossy permittivity; 16^3 elements
         # (2^18 elements at p = 3 need ~1.3 TB of condensation data and CSR)
-        return inputs.cavity(24, 3, jitter=0.1, eps_mode='random', name="cavity3_24x24x24_p3_jitter0.1")
+        return inputs.cavity(16, 3, jitter=0.1, eps_mode='random', name="cavity3_16x16x16_p3_jitter0.1")
     if name == "fichera":
         # Fichera-corner cavity, graded toward the re-entrant corner, degrees
         # 1..4 in a 40/30/20/10 % mix; 12 cells per unit length (13,824 elements)
         m = inputs.fichera_cavity(12, grade=1.5, name="fichera_12_graded_p1234")
         return m
+    if name == "fichera-amr":
+        # Fichera cavity, 12 coarse cells per unit, cells within 0.3 of the
+        # re-entrant corner refined once (2:1 hanging faces), degrees 1..4 mixed
+        return inputs.fichera_amr(12, radius=0.3)
     if name == "obstacle":
         # unit cavity 32^3, p = 2, dielectric sphere eps = 20 + 5i of radius 0.2
         m = inputs.cavity(32, 2, name="obstacle_cavity_32x32x32_p2")
@@ -137,6 +141,21 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
+def max_over_ranks(value, dist, device):
+    """Max of a per-rank number over all ranks (all_reduce MAX); the number itself without a process group."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_elem, ms_step):
+    """Whole-job elements/s: every rank solves its own replica of n_elem elements in ms_step (max over ranks)."""
+    return world * n_elem / (ms_step / 1e3)
+
+
 def cpu_oracle_rate(mesh, n_sample, threads_note=True):
     """Oracle (as it stands) element pass + estimator on a bounded sample of elements: elements/s."""
     from oracle import element as oel
@@ -199,6 +218,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--chunk", type=int, default=0, help="elements per launch (0: library default)")
     ap.add_argument("--autotune", action="store_true", help="measure chunk sizes per degree before the warm-up")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="after the timed steps, solve the same system with the plain FP64 CG and report it")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="after the timed steps, time the adjoint gradient of the absorbed power (obstacle elements)")
     ap.add_argument("--precision-report", action="store_true",
                     help="after the timed steps, solve again with FP64 quadrature and report the differences")
     args = ap.parse_args()
@@ -218,7 +241,7 @@ def main():
 
     from paper_2609_03155_b300 import dpg
     mesh = config_mesh(args.config)
-    d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk)
+    d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk, adjoint=args.adjoint)
     mode = CG_MODES[args.cg]
     tuned = d.autotune() if args.autotune else None
     stream = torch.cuda.current_stream()
@@ -237,8 +260,18 @@ def main():
         ev[4].record(stream)
         return ev, rep, x, eta, etag
 
-    for _ in range(args.warmup):
-        step()
+    try:
+        for _ in range(args.warmup):
+            step()
+    except dpg.DPGError as err:
+        if args.precision == "fp64":
+            raise
+        # reduced-precision quadrature can make G_K indefinite: report that and
+        # the element-matrix differences instead of a throughput
+        print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "config": {"workload": mesh.name,
+                          "quadrature": args.precision}, "error": str(err),
+                          "precision_report": element_error_report(d, mesh)}), flush=True)
+        return
     torch.cuda.synchronize()
     fp64, fp32 = dpg.probe_peaks()
 
@@ -261,11 +294,7 @@ def main():
         dist.barrier()
     clocks = clk.stop()
     tim = d.timing_get()
-    ms = t_start.elapsed_time(t_end)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), dist, "cuda")
     ms_step = ms / args.steps
     br = {"element_pass_s": [], "assemble_s": [], "cg_s": [], "estimate_s": []}
     for ev, rep in phases:
@@ -296,12 +325,8 @@ def main():
         eta_h.copy_(eta2, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if dist:
-            tt = torch.tensor([ems], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": world * mesh.n_elem / (ems / 1e3), "unit": UNIT,
+        ems = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        e2e = {"value": job_throughput(world, mesh.n_elem, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(corners.numel() * 8 + eps_h.numel() * 16 + mu_h.numel() * 16),
                "d2h_bytes_per_step": int(x_h.numel() * 16 + eta_h.numel() * 8)}
 
@@ -336,10 +361,19 @@ def main():
     except Exception:
         pass
     bpi = d.cg_bytes_per_iteration(mode)
+    # DRAM traffic per iteration / algorithmic bytes of the FP32 inner CG kernel,
+    # from the ncu capture of the 12x6x24 guide (dram__bytes_read.sum +
+    # dram__bytes_write.sum over 279 iterations); the traffic per iteration
+    # scales with the system, so a launch's traffic is this ratio times its
+    # algorithmic bytes
+    CG_TRAFFIC_RATIO_FP32 = 1.022
     cg_ach = bpi * tim["cg_kernel_iterations"] / max(1e-9, tim["cg_kernel_ms"] / 1e3) / 1e9
     roof_cg = {"bound": "hbm", "kernel": "k_cg_persistent<%s> (one cooperative CG solve per launch)"
                % ("float2" if mode & 1 else "double2"),
-               "achieved": cg_ach, "peak": hbm_peak, "unit": "GB/s", "frac": cg_ach / hbm_peak, "traffic": None,
+               "achieved": cg_ach, "peak": hbm_peak, "unit": "GB/s", "frac": cg_ach / hbm_peak,
+               "traffic": (CG_TRAFFIC_RATIO_FP32 * bpi * tim["cg_kernel_iterations"] / max(1, tim["cg_kernel_launches"])
+                           if mode & 1 else None),
+               "traffic_unit": "bytes per launch (ncu ratio 1.022 x algorithmic, from the 12x6x24 capture)",
                "peak_source": hbm_src, "bytes_per_iteration": bpi,
                "iterations": tim["cg_kernel_iterations"], "launches": tim["cg_kernel_launches"],
                "avg_launch_ms": tim["cg_kernel_ms"] / max(1, tim["cg_kernel_launches"]),
@@ -354,7 +388,7 @@ def main():
     cg_iters = last_rep["iterations"]
     rate, cores, dt, nsamp = cpu_oracle_rate(mesh, args.cpu_sample)
     line = {
-        "metric": METRIC, "value": world * mesh.n_elem / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(world, mesh.n_elem, ms_step), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": ("f64" if not (mode & 1) else "f64+f32(IR inner)")
@@ -384,11 +418,59 @@ def main():
         "gpu_launches": int(tim["kernel_launches"]),
         "peaks_measured": {"fp64_tflops": fp64 / 1e12, "fp32_tflops": fp32 / 1e12},
     }
+    if args.compare_fp64:
+        line["fp64_comparison"] = fp64_comparison(d, x, args)
+    if args.adjoint:
+        line["adjoint"] = adjoint_timing(d, mesh, x, args)
     if args.precision_report and args.precision != "fp64":
         line["precision_report"] = precision_report(d, mesh, x, eta, mode, args)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def fp64_comparison(d, x, args):
+    """The paper's solver (plain FP64 CG, x0 = 0) on the same assembled system, against the timed solution."""
+    import torch
+    x64, rep = d.cg_solve(mode=CG_MODES["fp64"], rtol=args.rtol, max_iter=args.max_iter,
+                          raise_on_nonconvergence=False)
+    diff = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
+    return {"cg": "fp64 (unpreconditioned, the paper's solver)", "time_s": rep["ms"] / 1e3,
+            "iterations": rep["iterations"], "rel_residual": rep["rel_residual"], "converged": rep["converged"],
+            "solution_rel_l2_difference": diff}
+
+
+def adjoint_timing(d, mesh, x, args):
+    """P and dP/deps of the elements with Im eps > 0 (the obstacle): one adjoint CG and one gradient pass."""
+    import torch
+    mask = torch.tensor((mesh.eps.imag > 0).astype(np.uint8), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P, dre, dim = d.grad_eps(x, mask, cg_mode=CG_MODES[args.cg], rtol=args.rtol, max_iter=args.max_iter)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"P": P, "time_s": dt, "obstacle_elements": int(mask.sum().item()),
+            "grad_abs_max": float(torch.maximum(dre.abs().max(), dim.abs().max()).item()),
+            "cg": args.cg, "cg_rtol": args.rtol}
+
+
+def element_error_report(d, mesh):
+    """G, B, S of sampled elements in the handle's precision against FP64 quadrature."""
+    from paper_2609_03155_b300 import dpg
+    ids = np.linspace(0, mesh.n_elem - 1, 8).astype(np.int32)
+    ids = ids[mesh.p[ids] == mesh.p[ids[0]]]
+    red = d.element_dump(ids)
+    d.destroy()
+    ref = dpg.DPG(mesh)
+    full = ref.element_dump(ids)
+    ref.destroy()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    # smallest eigenvalue of each sampled G_K relative to its largest (FP64 and reduced)
+    lam = lambda G: float(min(np.linalg.eigvalsh(g)[0] / np.linalg.eigvalsh(g)[-1] for g in G))
+    return {"elements_sampled": int(len(ids)), "G_rel_frobenius": rel(red["G"], full["G"]),
+            "B_rel_frobenius": rel(red["B"], full["B"]), "min_eig_ratio_G_fp64": lam(full["G"]),
+            "min_eig_ratio_G_reduced": lam(red["G"]),
+            "reference": "same elements, FP64 quadrature"}
 
 
 def precision_report(d, mesh, x, eta, mode, args):

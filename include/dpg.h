@@ -95,7 +95,7 @@ enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2
  * error against FP64 is a reported quantity, not a parity bound. */
 enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
-enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4 };
+enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8 };
 enum { DPG_FLAG_ADJOINT = 1 };
 
 /* Robin group (Sec. 2.2, Eq. robin_boundary; Sec. 4.1 port / outlet):
@@ -197,6 +197,8 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * preconditioning to future work; the stopping test stays on the
  * unpreconditioned residual.  Each (inner) solve is one cooperative kernel
  * whose grid barriers give up after a bounded wait (DPG_ERR_TIMEOUT).
+ * DPG_CG_X0 may be or-ed too: start from the x passed in (resume a stopped
+ * solve, or warm-start from a nearby problem's solution) instead of x0 = 0.
  * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or
  * NULL for the assembled right-hand side.  rep: host, may be NULL.
  * Synchronises the stream (the report is a host value).
@@ -312,6 +314,19 @@ int dpg_autotune(dpg_handle* h, double max_workspace_bytes, int32_t* caps, float
  * trial degree, number of elements and current chunk size of each group,
  * ascending degree. */
 int dpg_group_info(dpg_handle* h, int32_t* n_groups, int32_t* p, int32_t* n_elem, int32_t* cap);
+
+/* Electromagnetic power of a trace solution (Sec. 3.2): with the interior
+ * fields u_K of dpg_estimate and the element pass's Gauss-Legendre rule,
+ *   q (device, n_elem doubles, may be NULL): int_K Q_em dV,
+ *     Q_em = 1/2 omega (Im eps |E|^2 + Im mu |H|^2) (dimensionless; the
+ *     conductivity is part of Im eps);
+ *   flux (host, n_robin doubles, may be NULL): per Robin group, the sum over
+ *     its faces of int Re(E x conj(H)) . n dA with the outward normal (inflow
+ *     through a port is negative).  The reference field of Eq. (power_scaling)
+ *     follows on the host: E0^2 = 2 Z0 P_input / (-flux_port).
+ * xhat: device, n complex.  Synchronises when flux is given.
+ * Errors: DPG_ERR_STATE (no element pass), DPG_ERR_ARG, DPG_ERR_NOMEM. */
+int dpg_power(dpg_handle* h, const dpg_complex* xhat, double* q, double* flux, dpg_stream s);
 
 /* Sizes: n = free trace unknowns, nnz of the CSR matrix, per-element sizes
  * (the largest over the elements when the degrees differ). */

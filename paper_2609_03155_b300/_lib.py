@@ -19,6 +19,7 @@ DPG_BC_NONE, DPG_BC_DIRICHLET, DPG_BC_ROBIN = 0, 1, 2
 DPG_PASS_ASSEMBLE = 0
 DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI, DPG_CG_BLOCK_JACOBI = 0, 1, 2, 4
 DPG_PREC_FP64, DPG_PREC_TF32, DPG_PREC_3XTF32 = 0, 1, 2
+DPG_CG_X0 = 8
 DPG_FLAG_ADJOINT = 1
 
 
@@ -93,6 +94,7 @@ def lib():
     L.dpg_element_layout.argtypes = [vp, vp, vp, vp]
     L.dpg_tc_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, i32]
     L.dpg_set_graph.argtypes = [vp, i32]
+    L.dpg_power.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_autotune.argtypes = [vp, dbl, vp, vp, vp]
     L.dpg_group_info.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_element_dump.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
@@ -112,7 +114,7 @@ def lib():
                  "dpg_estimate_noalloc",
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
                  "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps",
-                 "dpg_set_real_path", "dpg_cg_bytes_per_iteration", "dpg_element_layout", "dpg_tc_gemm", "dpg_set_graph", "dpg_autotune",
+                 "dpg_set_real_path", "dpg_cg_bytes_per_iteration", "dpg_element_layout", "dpg_tc_gemm", "dpg_set_graph", "dpg_autotune", "dpg_power",
                  "dpg_group_info"):
         getattr(L, name).restype = C.c_int
     _lib = L

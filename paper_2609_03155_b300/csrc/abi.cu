@@ -3,9 +3,20 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dpg_internal.h"
 
 using namespace dpg;
+
+// NVTX range around each entry point (visible to nsys / ncu range filters;
+// free when no tool is attached).
+namespace {
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 static cudaStream_t S_(dpg_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 static thread_local std::string g_setup_err;
@@ -33,6 +44,7 @@ static void free_all(dpg_handle* h) {
 }
 
 extern "C" int dpg_setup_mesh(dpg_handle** out, const dpg_mesh_desc* m, const dpg_params* prm, dpg_stream st) {
+  Range range_("dpg_setup_mesh");
   if (!out) return DPG_ERR_ARG;
   *out = nullptr;
   dpg_handle* h = new (std::nothrow) dpg_handle();
@@ -57,6 +69,7 @@ extern "C" int dpg_setup_mesh(dpg_handle** out, const dpg_mesh_desc* m, const dp
 }
 
 extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
+  Range range_("dpg_element_batch");
   if (!h) return DPG_ERR_ARG;
   if (pass != DPG_PASS_ASSEMBLE) {
     h->err = "unknown element pass";
@@ -76,7 +89,7 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
   if (h->timing) {
     for (const ChunkPlan& cp : h->plan) {
       float ms = 0;
-      cudaEventElapsedTime(&ms, cp.ev0, cp.ev1);
+      DPG_CUDA_TRY(h, cudaEventElapsedTime(&ms, cp.ev0, cp.ev1));
       h->factor_ms += ms;
       h->factor_launches += 1;
       h->factor_elements += cp.count;
@@ -103,6 +116,7 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
 }
 
 extern "C" int dpg_assemble(dpg_handle* h, dpg_stream st) {
+  Range range_("dpg_assemble");
   if (!h) return DPG_ERR_ARG;
   if (!h->have_elements) {
     h->err = "dpg_assemble before dpg_element_batch";
@@ -114,6 +128,7 @@ extern "C" int dpg_assemble(dpg_handle* h, dpg_stream st) {
 extern "C" int dpg_cg_solve(dpg_handle* h, int32_t mode, double rtol, double atol, int32_t max_iter,
                             double inner_rtol, dpg_complex* x, const dpg_complex* b, dpg_cg_report* rep,
                             dpg_stream st) {
+  Range range_("dpg_cg_solve");
   if (!h) return DPG_ERR_ARG;
   return cg_solve(h, mode, rtol, atol, max_iter, inner_rtol, reinterpret_cast<double2*>(x),
                   reinterpret_cast<const double2*>(b), rep, S_(st));
@@ -121,12 +136,14 @@ extern "C" int dpg_cg_solve(dpg_handle* h, int32_t mode, double rtol, double ato
 
 extern "C" int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta, double* eta_global,
                             dpg_stream st) {
+  Range range_("dpg_estimate");
   if (!h) return DPG_ERR_ARG;
   return estimate(h, reinterpret_cast<const double2*>(xhat), reinterpret_cast<double2*>(u), eta, eta_global, S_(st));
 }
 
 extern "C" int dpg_estimate_noalloc(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
                                     double* eta_global, dpg_stream st) {
+  Range range_("dpg_estimate_noalloc");
   if (!h) return DPG_ERR_ARG;
   return estimate_noalloc(h, reinterpret_cast<const double2*>(xhat), reinterpret_cast<double2*>(u), eta, eta_global,
                           S_(st));
@@ -135,9 +152,16 @@ extern "C" int dpg_estimate_noalloc(dpg_handle* h, const dpg_complex* xhat, dpg_
 extern "C" int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle_mask, double* P,
                             double* dP_deps_re, double* dP_deps_im, int32_t cg_mode, double cg_rtol, int32_t max_iter,
                             dpg_stream st) {
+  Range range_("dpg_grad_eps");
   if (!h) return DPG_ERR_ARG;
   return grad_eps(h, reinterpret_cast<const double2*>(xhat), obstacle_mask, P, dP_deps_re, dP_deps_im, cg_mode, cg_rtol,
                   max_iter, S_(st));
+}
+
+extern "C" int dpg_power(dpg_handle* h, const dpg_complex* xhat, double* q, double* flux, dpg_stream st) {
+  Range range_("dpg_power");
+  if (!h) return DPG_ERR_ARG;
+  return power(h, reinterpret_cast<const double2*>(xhat), q, flux, S_(st));
 }
 
 extern "C" int dpg_sizes(dpg_handle* h, int64_t* n, int64_t* nnz, int32_t* n_elem, int32_t* n_v, int32_t* n_u,
@@ -173,6 +197,7 @@ extern "C" int dpg_trace_map(dpg_handle* h, int32_t* map, dpg_complex* fixed_val
 
 extern "C" int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids, dpg_complex* G, dpg_complex* B,
                                 dpg_complex* Bh, dpg_complex* l, dpg_complex* Sout, dpg_complex* sout, dpg_stream st) {
+  Range range_("dpg_element_dump");
   if (!h || !ids || n_ids <= 0) return DPG_ERR_ARG;
   cudaStream_t s = S_(st);
   for (int k = 0; k < n_ids; ++k)
@@ -252,6 +277,7 @@ extern "C" int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids
 
 extern "C" int dpg_csr_copy(dpg_handle* h, int64_t* row_ptr, int32_t* col, dpg_complex* val, dpg_complex* b,
                             dpg_stream st) {
+  Range range_("dpg_csr_copy");
   if (!h) return DPG_ERR_ARG;
   if (!h->have_system && (val || b)) {
     h->err = "dpg_csr_copy of values before dpg_assemble";
@@ -331,6 +357,7 @@ extern "C" int dpg_probe_peaks(double* fp64, double* fp32, dpg_stream st) {
 
 extern "C" int dpg_tc_gemm(int32_t split, int32_t Ma, int32_t Nb, int32_t Kd, const double* A, const double* B,
                            double* C, int32_t upper_only) {
+  Range range_("dpg_tc_gemm");
   if ((split != 1 && split != 3) || Ma <= 0 || Nb <= 0 || Kd <= 0 || !A || !B || !C) return DPG_ERR_ARG;
   double *dA = nullptr, *dB = nullptr, *dC = nullptr;
   int* derr = nullptr;
@@ -364,6 +391,7 @@ extern "C" int dpg_tc_gemm(int32_t split, int32_t Ma, int32_t Nb, int32_t Kd, co
 
 extern "C" int dpg_update_elements(dpg_handle* h, const double* corners, const dpg_complex* eps, const dpg_complex* mu,
                                    dpg_stream st) {
+  Range range_("dpg_update_elements");
   if (!h) return DPG_ERR_ARG;
   cudaStream_t s = S_(st);
   if (corners)
@@ -419,6 +447,7 @@ extern "C" int dpg_set_graph(dpg_handle* h, int32_t enable) {
 
 extern "C" int dpg_autotune(dpg_handle* h, double max_workspace_bytes, int32_t* caps, float* ms_per_element,
                             dpg_stream st) {
+  Range range_("dpg_autotune");
   if (!h || !(max_workspace_bytes > 0)) return DPG_ERR_ARG;
   int rc = autotune(h, max_workspace_bytes, caps, ms_per_element, S_(st));
   h->have_elements = false;

@@ -56,6 +56,8 @@ struct Workspace {
   double* Cu = nullptr;      // cap x 3nq x n_f   sqrt(w detJ) curl psi
   double* PhiL = nullptr;    // cap x 3nq x 3nL   sqrt(w detJ) L e_d
   double* MC = nullptr;      // cap x (2 n_f^2 + 2 n_f 3nL): M, C, P, Q
+  double* F = nullptr;       // cap x nq x n_f    sqrt(w detJ) f_i (scalar factor of each test function)
+  double* KW = nullptr;      // cap x 6 x nq      (J^{-1} J^{-T})_{cd}, pairs 00 11 22 01 02 12
   int* ids = nullptr;        // cap element ids of the chunk
   // Robin face scratch (per Robin entry of the chunk)
   int rcap = 0;
@@ -133,6 +135,7 @@ struct dpg_handle {
   std::vector<dpg::RobinEntry> robin_entries;  // sorted by element
   std::vector<int> robin_first;                // per element: first entry index or -1
   int ncolor = 0;
+  int64_t n_slaves = 0;                        // hanging (2:1) edges and faces without unknowns
   int64_t n = 0, nnz = 0;
   std::vector<int32_t> l2g;                    // element-major, n_h(K) per element (offsets ElemOff::h)
   std::vector<dpg::ElemOff> off;               // ne + 1 (the last holds the totals)
@@ -236,6 +239,8 @@ int element_pass(dpg_handle* h, cudaStream_t s);
 int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem, cudaStream_t s);
 int compute_reference_matrices(dpg_handle* h, int g, cudaStream_t s);
 int factor_gram_only(dpg_handle* h, int g, int count, cudaStream_t s);
+// power.cu
+int power(dpg_handle* h, const double2* xhat, double* q, double* flux_host, cudaStream_t s);
 // quad_tc.cu
 int tc_init();
 int gemm_tn_tc(int split, int Ma, int Nb, int Kd, const double* A, int lda, long long sA, const double* B, int ldb,

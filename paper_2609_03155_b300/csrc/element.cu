@@ -163,7 +163,8 @@ __device__ void te_fields(const dpg_robin_group& g, double omega, const double x
 constexpr int QB = 8;
 
 __global__ void __launch_bounds__(256) k_vol_arrays(const __grid_constant__ Tables T, Sizes S, const double* __restrict__ Xall,
-                                                    const int* __restrict__ ids, double* V, double* Cu, double* PhiL) {
+                                                    const int* __restrict__ ids, double* V, double* Cu, double* PhiL,
+                                                    double* Fs, double* KW) {
   const int slot = blockIdx.y;
   const int e = ids[slot];
   __shared__ double sX[24];
@@ -187,6 +188,12 @@ __global__ void __launch_bounds__(256) k_vol_arrays(const __grid_constant__ Tabl
           sJs[threadIdx.x][3 * a + b] = J[a][b] * (s / det);
         }
       sw[threadIdx.x] = s;
+      if (KW) {  // metric of the covariant map, for the component-pair mass products
+        const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k)
+          KW[((size_t)slot * 6 + k) * nq + q] =
+              Ji[pa[k]][0] * Ji[pb[k]][0] + Ji[pa[k]][1] * Ji[pb[k]][1] + Ji[pa[k]][2] * Ji[pb[k]][2];
+      }
     }
   }
   __syncthreads();
@@ -212,6 +219,7 @@ __global__ void __launch_bounds__(256) k_vol_arrays(const __grid_constant__ Tabl
       Ve[((size_t)q * 3 + a) * nf + i] = s * Ji[3 * c + a] * f;  // (J^{-T})_{a c} = (J^{-1})_{c a}
       Ce[((size_t)q * 3 + a) * nf + i] = Js[3 * a + 0] * cr[0] + Js[3 * a + 1] * cr[1] + Js[3 * a + 2] * cr[2];
     }
+    if (Fs) Fs[(size_t)slot * nq * nf + (size_t)q * nf + i] = s * f;
   }
   const int nL = S.nL, w3 = 3 * nL;
   double* Pe = PhiL + slot * (size_t)3 * nq * w3;
@@ -336,7 +344,8 @@ constexpr int GT = 64, GK = 16;
 
 __global__ void __launch_bounds__(256) k_gemm_tn(int Ma, int Nb, int Kd, const double* __restrict__ A, int lda, long long sA,
                                                  const double* __restrict__ B, int ldb, long long sB, double* C, int ldc,
-                                                 long long sC, int upper_only) {
+                                                 long long sC, int upper_only, const double* __restrict__ wk,
+                                                 long long sw) {
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   const int b = blockIdx.z;
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int Ma, int Nb, int Kd, const d
       int kk = t / GT, mm = t - kk * GT;
       int k = k0 + kk;
       As[kk][mm] = (k < Kd && m0 + mm < Ma) ? Ab[(size_t)k * lda + m0 + mm] : 0.0;
-      Bs[kk][mm] = (k < Kd && n0 + mm < Nb) ? Bb[(size_t)k * ldb + n0 + mm] : 0.0;
+      Bs[kk][mm] = (k < Kd && n0 + mm < Nb) ? Bb[(size_t)k * ldb + n0 + mm] * (wk ? wk[b * sw + k] : 1.0) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -386,10 +395,12 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int Ma, int Nb, int Kd, const d
   }
 }
 
+// C = A^T diag(wk) B when wk is given (one weight per k, stride sw per batch entry).
 static void gemm_tn(int Ma, int Nb, int Kd, const double* A, int lda, long long sA, const double* B, int ldb,
-                    long long sB, double* C, int ldc, long long sC, int batch, cudaStream_t s, int upper_only = 0) {
+                    long long sB, double* C, int ldc, long long sC, int batch, cudaStream_t s, int upper_only = 0,
+                    const double* wk = nullptr, long long sw = 0) {
   dim3 grid((Nb + GT - 1) / GT, (Ma + GT - 1) / GT, batch);
-  k_gemm_tn<<<grid, 256, 0, s>>>(Ma, Nb, Kd, A, lda, sA, B, ldb, sB, C, ldc, sC, upper_only);
+  k_gemm_tn<<<grid, 256, 0, s>>>(Ma, Nb, Kd, A, lda, sA, B, ldb, sB, C, ldc, sC, upper_only, wk, sw);
 }
 
 // ------------------------------------------------------ build K matrix --
@@ -627,6 +638,62 @@ template <> struct Sc<double2> {
 };
 
 
+// Column tiles per pass of the trailing update.
+template <typename T> struct FactorJW { static constexpr int value = 1; };
+
+template <typename T>
+constexpr size_t factor_smem() {
+  return sizeof(T) * (NB * NB + (1 + FactorJW<T>::value) * NB * TT);
+}
+
+// A[row][col] -= sum_kk PI[kk][row] conj(PJ_j[kk][col]) for NJ adjacent
+// column tiles (lower triangle only); thread (tx, ty) owns rows tx + 16 a and
+// columns ty + 16 b of each tile.  The panel tiles are zero beyond column w,
+// so the k loop runs the compile-time width and unrolls.
+template <typename T, int NJ>
+__device__ __forceinline__ void tile_update(T* A, int N, int nact, int r0, int c0, const T* sPI, const T* sPJ,
+                                            int tid) {
+  using O = Sc<T>;
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[NJ][4][4];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[j][a][b] = O::zero();
+#pragma unroll
+  for (int kk = 0; kk < NB; ++kk) {
+    T pa[4], pb[NJ][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) pa[a] = sPI[kk * TT + tx + 16 * a];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) pb[j][b] = sPJ[j * NB * TT + kk * TT + ty + 16 * b];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) O::fma_conj(acc[j][a][b], pa[a], pb[j][b]);  // acc += pa conj(pb)
+  }
+#pragma unroll
+  for (int j = 0; j < NJ; ++j)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int row = r0 + tx + 16 * a;
+      if (row >= nact) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int col = c0 + j * TT + ty + 16 * b;
+        if (col >= nact || col > row) continue;
+        T* p = &A[(size_t)row + (size_t)col * N];
+        *p = O::sub(*p, acc[j][a][b]);
+      }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npiv, const int* __restrict__ ids,
                                                 T* K, int* status) {
@@ -634,7 +701,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
   extern __shared__ __align__(16) unsigned char fsm[];
   T* sD = reinterpret_cast<T*>(fsm);  // NB x NB diagonal block (column-major)
   T* sPI = sD + NB * NB;              // NB x TT panel rows of tile I ([k][row])
-  T* sPJ = sPI + NB * TT;             // NB x TT panel rows of tile J
+  T* sPJ = sPI + NB * TT;             // JW x NB x TT panel rows of the column tiles
   const int slot = blockIdx.x;
   T* A = K + (size_t)slot * N * N;
   const int tid = threadIdx.x;
@@ -712,7 +779,6 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
     // --- trailing update of the lower triangle of rows/cols [k1, N)
     const int R = nact - k1;
     const int ntile = (R + TT - 1) / TT;
-    const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16 a, cols ty + 16 b
     for (int I = 0; I < ntile; ++I) {
       const int r0 = k1 + I * TT;
       __syncthreads();
@@ -729,34 +795,7 @@ __global__ void __launch_bounds__(256) k_factor(int N, int nact, int nv, int npi
               (kk < w && c0 + rr < nact) ? A[(size_t)(c0 + rr) + (size_t)(k0 + kk) * N] : O::zero();
         }
         __syncthreads();
-        T acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = O::zero();
-        for (int kk = 0; kk < w; ++kk) {
-          T pa[4], pb[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) pa[a] = sPI[kk * TT + tx + 16 * a];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) pb[b] = sPJ[kk * TT + ty + 16 * b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) O::fma_conj(acc[a][b], pa[a], pb[b]);  // acc += pa conj(pb)
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int row = r0 + tx + 16 * a;
-          if (row >= nact) continue;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int col = c0 + ty + 16 * b;
-            if (col >= nact || col > row) continue;
-            T* p = &A[(size_t)row + (size_t)col * N];
-            *p = O::sub(*p, acc[a][b]);
-          }
-        }
+        tile_update<T, 1>(A, N, nact, r0, c0, sPI, sPJ, tid);
       }
     }
     __syncthreads();
@@ -949,7 +988,8 @@ __global__ void __launch_bounds__(256) k_restrict(int nt, int nu, const int* __r
 // Per-element bytes of the chunk workspace of one group.
 static size_t chunk_bytes(const Sizes& S) {
   return sizeof(double2) * (size_t)S.N * S.N + sizeof(double) * 3 * (size_t)S.nq * (2 * S.n_f + 3 * S.nL) +
-         sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) + sizeof(int);
+         sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) +
+         sizeof(double) * (size_t)S.nq * (S.n_f + 6) + sizeof(int);
 }
 
 // Default chunk capacity per group: a byte budget of 12 GB, raised to one
@@ -973,11 +1013,11 @@ void set_default_caps(dpg_handle* h, int chunk) {
 // One workspace sized for the largest group chunk (frees the previous one).
 int alloc_workspace(dpg_handle* h) {
   Workspace& w = h->ws;
-  void* old[] = {w.K, w.V, w.Cu, w.PhiL, w.MC, w.ids, w.FV, w.FR, w.rent};
+  void* old[] = {w.K, w.V, w.Cu, w.PhiL, w.MC, w.ids, w.FV, w.FR, w.rent, w.F, w.KW};
   for (void* b : old)
     if (b) cudaFree(b);
   w = Workspace{};
-  size_t bK = 0, bV = 0, bP = 0, bMC = 0, bFV = 0, bFR = 0;
+  size_t bK = 0, bV = 0, bP = 0, bMC = 0, bFV = 0, bFR = 0, bF = 0, bKW = 0;
   int capmax = 1;
   for (Group& G : h->grp) {
     const Sizes& S = G.sz;
@@ -988,6 +1028,8 @@ int alloc_workspace(dpg_handle* h) {
     bV = std::max(bV, sizeof(double) * nq3 * S.n_f * cap);
     bP = std::max(bP, sizeof(double) * nq3 * 3 * S.nL * cap);
     bMC = std::max(bMC, sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) * cap);
+    bF = std::max(bF, sizeof(double) * (size_t)S.nq * S.n_f * cap);
+    bKW = std::max(bKW, sizeof(double) * 6 * (size_t)S.nq * cap);
   }
   w.rcap = std::max(6, std::min(capmax * 2, std::max(6, (int)h->robin_entries.size())));
   for (Group& G : h->grp) {
@@ -996,10 +1038,11 @@ int alloc_workspace(dpg_handle* h) {
     bFV = std::max(bFV, sizeof(double) * 3 * (size_t)S.nqf * Wf * w.rcap);
     bFR = std::max(bFR, sizeof(double) * (size_t)S.n_f * Wf * w.rcap);
   }
-  size_t bytes[] = {bK, bV, bV, bP, bMC, sizeof(int) * (size_t)capmax, bFV, bFR, sizeof(int) * 4 * (size_t)w.rcap};
+  size_t bytes[] = {bK, bV, bV, bP, bMC, sizeof(int) * (size_t)capmax, bFV, bFR, sizeof(int) * 4 * (size_t)w.rcap,
+                    bF, bKW};
   void** ptrs[] = {(void**)&w.K, (void**)&w.V, (void**)&w.Cu, (void**)&w.PhiL, (void**)&w.MC, (void**)&w.ids,
-                   (void**)&w.FV, (void**)&w.FR, (void**)&w.rent};
-  for (int k = 0; k < 9; ++k) {
+                   (void**)&w.FV, (void**)&w.FR, (void**)&w.rent, (void**)&w.F, (void**)&w.KW};
+  for (int k = 0; k < 11; ++k) {
     if (cudaMalloc(ptrs[k], bytes[k]) != cudaSuccess) {
       cudaGetLastError();
       h->err = "workspace allocation of " + std::to_string(bytes[k]) + " bytes failed";
@@ -1014,8 +1057,8 @@ int alloc_workspace(dpg_handle* h) {
 
 // Kernel attributes set once (never inside a stream capture).
 int init_kernel_attributes(dpg_handle* h) {
-  const int s64 = (int)(sizeof(double) * (NB * NB + 2 * NB * TT));
-  const int s128 = (int)(sizeof(double2) * (NB * NB + 2 * NB * TT));
+  const int s64 = (int)factor_smem<double>();
+  const int s128 = (int)factor_smem<double2>();
   DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64));
   DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128));
   if (tc_init() != DPG_OK) {
@@ -1105,19 +1148,42 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
   const int* ids = cp ? h->d_plan_ids + cp->ids_off : w.ids;
   if (!cp) DPG_CUDA_TRY(h, cudaMemcpyAsync(w.ids, ids_host, sizeof(int) * count, cudaMemcpyHostToDevice, s));
   const size_t nq3 = 3 * (size_t)S.nq;
-  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(G.tab, S, h->d_X, ids, w.V, w.Cu, w.PhiL);
+  const bool fp64q = h->prec == DPG_PREC_FP64;
+  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(G.tab, S, h->d_X, ids, w.V, w.Cu, w.PhiL,
+                                                                   fp64q ? w.F : nullptr, fp64q ? w.KW : nullptr);
   const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
   const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
   const int nL3 = 3 * S.nL;
   // M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL (FP64, or the tensor cores)
   if (h->prec == DPG_PREC_FP64) {
-    gemm_tn(S.n_f, S.n_f, (int)nq3, w.V, S.n_f, sV, w.V, S.n_f, sV, w.MC, S.n_f, (long long)mcs, count, s, 1);
+    // M_ij = sum_q w det f_i f_j (J^{-1} J^{-T})_{c_i c_j}: test functions are
+    // component-major (n_f / 3 per reference component), so the upper triangle
+    // of M is six weighted products over the n_q points (one per component
+    // pair) instead of one product over 3 n_q rows
+    {
+      const int nc = S.n_f / 3;
+      const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+      const long long sF = (long long)S.nq * S.n_f;
+      for (int k = 0; k < 6; ++k)
+        gemm_tn(nc, nc, S.nq, w.F + (size_t)pa[k] * nc, S.n_f, sF, w.F + (size_t)pb[k] * nc, S.n_f, sF,
+                w.MC + (size_t)pa[k] * nc * S.n_f + (size_t)pb[k] * nc, S.n_f, (long long)mcs, count, s,
+                pa[k] == pb[k] ? 1 : 0, w.KW + (size_t)k * S.nq, 6LL * S.nq);
+      h->launches += 5;
+    }
     gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f, S.n_f,
             (long long)mcs, count, s, 1);
-    gemm_tn(S.n_f, nL3, (int)nq3, w.V, S.n_f, sV, w.PhiL, nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f, nL3,
-            (long long)mcs, count, s);
-    gemm_tn(S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
-            w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, s);
+    // PhiL is block diagonal over the component d (row q*3+d holds s_q L_l(q) in
+    // columns d nL + l only): P[:, d nL + l] = sum_q V[q*3+d][:] PhiL[q*3+d][d nL + l],
+    // one K = n_q product per d (rows of stride 3) instead of K = 3 n_q over the zero blocks
+    const int nL = S.nL;
+    for (int d = 0; d < 3; ++d) {
+      gemm_tn(S.n_f, nL, S.nq, w.V + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
+              3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)d * nL, nL3, (long long)mcs, count, s);
+      gemm_tn(S.n_f, nL, S.nq, w.Cu + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
+              3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3 + (size_t)d * nL, nL3,
+              (long long)mcs, count, s);
+    }
+    h->launches += 4;
   } else {
     const int split = h->prec == DPG_PREC_3XTF32 ? 3 : 1;
     int* terr = h->d_status + h->ne;
@@ -1157,16 +1223,21 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
     }
   }
   if (factor) {
-    const size_t smem = (real ? sizeof(double) : sizeof(double2)) * (NB * NB + 2 * NB * TT);
+    const size_t smem = real ? factor_smem<double>() : factor_smem<double2>();
     const bool timed = cp && h->timing;
-    if (timed) DPG_CUDA_TRY(h, cudaEventRecord(cp->ev0, s));
+    // inside a stream capture an event record is only a dependency unless it
+    // is marked external; then it is recorded at every graph replay
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (timed) DPG_CUDA_TRY(h, cudaStreamIsCapturing(s, &cap));
+    const unsigned int rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (timed) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(cp->ev0, s, rec_flags));
     if (real)
       k_factor<double><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, Kr, h->d_status);
     else
       k_factor<double2><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, w.K, h->d_status);
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
-    if (timed) DPG_CUDA_TRY(h, cudaEventRecord(cp->ev1, s));
+    if (timed) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(cp->ev1, s, rec_flags));
   }
   if (extract) {
     if (real)
@@ -1373,7 +1444,7 @@ int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem,
 // Cholesky of the G block alone for the current chunk (rows below untouched).
 int factor_gram_only(dpg_handle* h, int g, int count, cudaStream_t s) {
   const Sizes& S = h->grp[g].sz;
-  const size_t smem = sizeof(double2) * (NB * NB + 2 * NB * TT);
+  const size_t smem = factor_smem<double2>();
   k_factor<double2><<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status);
   h->launches += 1;
   DPG_CUDA_TRY(h, cudaGetLastError());
@@ -1415,7 +1486,8 @@ int compute_reference_matrices(dpg_handle* h, int g, cudaStream_t s) {
   int zeros[32] = {0};
   DPG_CUDA_TRY(h, cudaMemcpyAsync(dXu, Xu, sizeof(Xu), cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(dids, zeros, sizeof(zeros), cudaMemcpyHostToDevice, s));
-  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, 1), 256, 0, s>>>(G.tab, S, dXu, dids, w.V, w.Cu, w.PhiL);
+  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, 1), 256, 0, s>>>(G.tab, S, dXu, dids, w.V, w.Cu, w.PhiL, nullptr,
+                                                               nullptr);
   const size_t nq3 = 3 * (size_t)S.nq;
   gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, 0, w.V, S.n_f, 0, G.d_Xref, S.n_f, 0, 1, s);
   // faces of the unit cube

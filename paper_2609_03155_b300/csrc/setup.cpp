@@ -23,6 +23,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <unordered_map>
 
@@ -141,6 +142,21 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     return DPG_ERR_UNSUPPORTED;
   }
   const int ne = m->n_elem;
+  if (!std::isfinite(prm->omega) || !std::isfinite(prm->alpha)) {
+    h->err = "omega and alpha must be finite";
+    return DPG_ERR_ARG;
+  }
+  for (int64_t k = 0; k < (int64_t)m->n_vert * 3; ++k)
+    if (!std::isfinite(m->vert[k])) {
+      h->err = "non-finite vertex coordinate";
+      return DPG_ERR_MESH;
+    }
+  for (int e = 0; e < ne; ++e)
+    if (!std::isfinite(m->elem_eps[e].re) || !std::isfinite(m->elem_eps[e].im) || !std::isfinite(m->elem_mu[e].re) ||
+        !std::isfinite(m->elem_mu[e].im)) {
+      h->err = "non-finite permittivity or permeability (element " + std::to_string(e) + ")";
+      return DPG_ERR_ARG;
+    }
   for (int e = 0; e < ne; ++e)
     if (m->elem_p[e] < 1 || m->elem_p[e] > MAXP) {
       h->err = "trial degree must be in 1..4 (element " + std::to_string(e) + ")";
@@ -277,13 +293,140 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
       }
   }
   const int n_ent = n_edges + n_faces;  // entity id: edges [0, n_edges), faces after
-  // entity trace order: min over the containing elements of p + 1
+  // ---- 2:1 hanging entities ---------------------------------------------------
+  // A face met by one element only and not on a tagged boundary whose four
+  // quarters (corner, two mid-edge points, centre) are faces of other elements
+  // is a master; the quarters and the four interior half-lines (mid-edge point
+  // to centre) are its slaves.  An edge whose two halves are edges of other
+  // elements is the master of the halves.  Points are matched by coordinates.
+  std::vector<int> master(n_ent);
+  for (int en = 0; en < n_ent; ++en) master[en] = en;
+  std::vector<int> owner_elem(n_ent, -1), owner_slot(n_ent, -1);
+  for (int e = 0; e < ne; ++e) {
+    for (int k = 0; k < 12; ++k) {
+      const int en = elem_edge[(size_t)e * 12 + k];
+      if (owner_elem[en] < 0) owner_elem[en] = e, owner_slot[en] = k;
+    }
+    for (int k = 0; k < 6; ++k) {
+      const int en = n_edges + elem_face[(size_t)e * 6 + k];
+      if (owner_elem[en] < 0) owner_elem[en] = e, owner_slot[en] = 12 + k;
+    }
+  }
+  {
+    double span = 0.0;
+    for (int64_t k = 0; k < (int64_t)m->n_vert * 3; ++k) span = std::max(span, std::fabs(m->vert[k]));
+    const double qscale = 1.0 / (1e-9 * std::max(span, 1e-300));
+    auto qkey = [&](const double* x) {
+      uint64_t hsh = 1469598103934665603ull;
+      for (int a2 = 0; a2 < 3; ++a2) {
+        hsh ^= (uint64_t)(int64_t)std::llround(x[a2] * qscale);
+        hsh *= 1099511628211ull;
+      }
+      return hsh;
+    };
+    std::unordered_map<uint64_t, int> vat;
+    for (int v = 0; v < m->n_vert; ++v) vat.emplace(qkey(&m->vert[3 * (size_t)v]), v);
+    auto vert_at = [&](const double* x) {
+      auto it = vat.find(qkey(x));
+      if (it == vat.end()) return -1;
+      const double* y = &m->vert[3 * (size_t)it->second];
+      for (int a2 = 0; a2 < 3; ++a2)
+        if (std::fabs(y[a2] - x[a2]) > 1e-8 * std::max(span, 1e-300)) return -1;
+      return it->second;
+    };
+    auto mid = [&](int v0, int v1, double* out) {
+      for (int a2 = 0; a2 < 3; ++a2) out[a2] = 0.5 * (m->vert[3 * (size_t)v0 + a2] + m->vert[3 * (size_t)v1 + a2]);
+    };
+    auto find_edge = [&](int v0, int v1) {
+      auto it = edge_id.find(((uint64_t)(uint32_t)v0 << 32) | (uint32_t)v1);
+      if (it != edge_id.end()) return it->second;
+      it = edge_id.find(((uint64_t)(uint32_t)v1 << 32) | (uint32_t)v0);
+      return it == edge_id.end() ? -1 : it->second;
+    };
+    std::vector<int> face_elems(n_faces, 0);
+    std::vector<char> face_tagged(n_faces, 0);
+    for (int e = 0; e < ne; ++e)
+      for (int k = 0; k < 6; ++k) {
+        face_elems[elem_face[(size_t)e * 6 + k]]++;
+        if (m->face_bc[6 * (size_t)e + k] != DPG_BC_NONE) face_tagged[elem_face[(size_t)e * 6 + k]] = 1;
+      }
+    for (int f = 0; f < n_faces; ++f) {
+      if (face_elems[f] != 1 || face_tagged[f]) continue;
+      const std::array<int, 4>& o = face_order[f];  // corners (0,0), (1,0), (0,1), (1,1)
+      double x01[3], x02[3], x13[3], x23[3], xc[3];
+      mid(o[0], o[1], x01);
+      mid(o[0], o[2], x02);
+      mid(o[1], o[3], x13);
+      mid(o[2], o[3], x23);
+      mid(o[0], o[3], xc);
+      const int m01 = vert_at(x01), m02 = vert_at(x02), m13 = vert_at(x13), m23 = vert_at(x23), mc = vert_at(xc);
+      if (m01 < 0 || m02 < 0 || m13 < 0 || m23 < 0 || mc < 0) continue;
+      const std::array<int, 4> quarters[4] = {{o[0], m01, m02, mc}, {m01, o[1], mc, m13}, {m02, mc, o[2], m23},
+                                               {mc, m13, m23, o[3]}};
+      int qid[4];
+      bool ok = true;
+      for (int q = 0; q < 4 && ok; ++q) {
+        std::array<int, 4> key = quarters[q];
+        std::sort(key.begin(), key.end());
+        auto it = face_id.find(key);
+        ok = it != face_id.end() && face_elems[it->second] == 1 && !face_tagged[it->second];
+        if (ok) qid[q] = it->second;
+      }
+      const int cross[4] = {find_edge(m01, mc), find_edge(m02, mc), find_edge(mc, m13), find_edge(mc, m23)};
+      for (int q = 0; q < 4 && ok; ++q) ok = cross[q] >= 0;
+      if (!ok) continue;
+      for (int q = 0; q < 4; ++q) {
+        master[n_edges + qid[q]] = n_edges + f;
+        master[cross[q]] = n_edges + f;
+      }
+    }
+    for (const auto& kv : edge_id) {
+      const int v0 = (int)(kv.first >> 32), v1 = (int)(kv.first & 0xffffffffu);
+      double xm[3];
+      mid(v0, v1, xm);
+      const int vm = vert_at(xm);
+      if (vm < 0) continue;
+      const int h0 = find_edge(v0, vm), h1 = find_edge(vm, v1);
+      if (h0 < 0 || h1 < 0) continue;
+      master[h0] = kv.second;
+      master[h1] = kv.second;
+    }
+    for (int en = 0; en < n_ent; ++en) {  // follow chains to the top master
+      int mm = master[en];
+      for (int guard = 0; master[mm] != mm && guard < 8; ++guard) mm = master[mm];
+      master[en] = mm;
+    }
+  }
+  h->n_slaves = 0;
+  for (int en = 0; en < n_ent; ++en) h->n_slaves += master[en] != en;
+  // entity trace order: min over the elements that touch the entity or one of
+  // its slaves of p + 1; an edge of a face is capped by the face's order
   std::vector<int> ent_r(n_ent, MAXP + 1);
   for (int e = 0; e < ne; ++e) {
     const int re = m->elem_p[e] + 1;
-    for (int k = 0; k < 12; ++k) ent_r[elem_edge[(size_t)e * 12 + k]] = std::min(ent_r[elem_edge[(size_t)e * 12 + k]], re);
-    for (int k = 0; k < 6; ++k)
-      ent_r[n_edges + elem_face[(size_t)e * 6 + k]] = std::min(ent_r[n_edges + elem_face[(size_t)e * 6 + k]], re);
+    for (int k = 0; k < 12; ++k) {
+      const int mm = master[elem_edge[(size_t)e * 12 + k]];
+      ent_r[mm] = std::min(ent_r[mm], re);
+    }
+    for (int k = 0; k < 6; ++k) {
+      const int mm = master[n_edges + elem_face[(size_t)e * 6 + k]];
+      ent_r[mm] = std::min(ent_r[mm], re);
+    }
+  }
+  for (int f = 0; f < n_faces; ++f) {
+    const int en = n_edges + f;
+    if (master[en] != en) continue;
+    const int e = owner_elem[en], kf = owner_slot[en] - 12, d = kf / 2, sd = kf % 2;
+    for (int c = 0; c < 3; ++c) {
+      if (c == d) continue;
+      const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+      for (int s2 = 0; s2 < 2; ++s2)
+        for (int s1 = 0; s1 < 2; ++s1) {
+          if ((d1 == d && s1 != sd) || (d2 == d && s2 != sd)) continue;
+          const int mm = master[elem_edge[(size_t)e * 12 + c * 4 + s1 + 2 * s2]];
+          ent_r[mm] = std::min(ent_r[mm], ent_r[en]);
+        }
+    }
   }
   auto ent_dofs = [&](int ent) { return ent < n_edges ? ent_r[ent] : 2 * ent_r[ent] * (ent_r[ent] - 1); };
 
@@ -342,6 +485,7 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   std::vector<int64_t> startE(n_ent, -1), startH(n_ent, -1);
   int64_t nfree = 0;
   for (int en = 0; en < n_ent; ++en) {
+    if (master[en] != en) continue;  // slaves carry no unknowns
     if (dir_grp[en] < 0) {
       startE[en] = nfree;
       nfree += ent_dofs(en);
@@ -416,206 +560,373 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     h->off[e + 1] = o;
   }
   const ElemOff tot = h->off[ne];
+
+  // 1D node sets of every order (open: Gauss-Legendre, closed: Gauss-Lobatto)
+  double onodes[MAXF1D][MAXF1D], cnodes[MAXF1D][MAXF1D + 1];
+  for (int r = 1; r <= MAXP + 1; ++r) {
+    double wd[MAXF1D];
+    gauss_legendre01(r, onodes[r], wd);
+    gauss_lobatto01(r + 1, cnodes[r]);
+  }
+  auto lag_open = [&](int r, double x, double* v) {
+    double der[MAXF1D + 1];
+    lagrange1d(onodes[r], r, x, v, der);
+  };
+  auto lag_closed = [&](int r, double x, double* v) {
+    double der[MAXF1D + 1];
+    lagrange1d(cnodes[r], r + 1, x, v, der);
+  };
+  // reference point of physical x in element e (Newton on the trilinear map)
+  auto invert = [&](int e, const double* x, double* xi) {
+    xi[0] = xi[1] = xi[2] = 0.5;
+    for (int it = 0; it < 30; ++it) {
+      double J[3][3], y[3], Ji[3][3];
+      trilinear(&X[(size_t)e * 24], xi, J, y);
+      inv3(J, Ji);
+      double dx[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]}, step = 0.0;
+      for (int a2 = 0; a2 < 3; ++a2) {
+        const double dxi = Ji[a2][0] * dx[0] + Ji[a2][1] * dx[1] + Ji[a2][2] * dx[2];
+        xi[a2] -= dxi;
+        step = std::max(step, std::fabs(dxi));
+      }
+      if (step < 1e-15) break;
+    }
+  };
+  // Trace coefficient along element e's axis c at its reference point xi, on
+  // its edge slot ks / face slot kf: terms (global entity, index, weight).  A
+  // master entity contributes its own nodal basis (a face also its edges'
+  // functions through the closed factor of the face order); a slave is its
+  // master's trace at the same physical point times the tangent ratio.
+  struct Term {
+    int ent, idx;
+    double w;
+  };
+  std::function<void(int, int, const double*, double, std::vector<Term>&)> eval_edge;
+  std::function<void(int, int, int, const double*, double, std::vector<Term>&)> eval_face;
+  auto eval_master = [&](int M, int e, const double* xi, int c, double scale, std::vector<Term>& out) {
+    double J[3][3], x[3], Jm[3][3], xm[3], xim[3];
+    trilinear(&X[(size_t)e * 24], xi, J, x);
+    const int em = owner_elem[M];
+    invert(em, x, xim);
+    trilinear(&X[(size_t)em * 24], xim, Jm, xm);
+    double tt = 0.0, mm = 0.0;
+    for (int a2 = 0; a2 < 3; ++a2) {
+      tt += J[a2][c] * Jm[a2][c];
+      mm += Jm[a2][c] * Jm[a2][c];
+    }
+    const double ratio = tt / mm;
+    if (M < n_edges)
+      eval_edge(em, owner_slot[M], xim, scale * ratio, out);
+    else
+      eval_face(em, owner_slot[M], c, xim, scale * ratio, out);
+  };
+  eval_edge = [&](int e, int ks, const double* xi, double scale, std::vector<Term>& out) {
+    const int en = elem_edge[(size_t)e * 12 + ks], c = ks / 4;
+    if (master[en] != en) {
+      eval_master(master[en], e, xi, c, scale, out);
+      return;
+    }
+    const int r = ent_r[en];
+    double v[MAXF1D + 1];
+    lag_open(r, xi[c], v);
+    for (int q = 0; q < r; ++q) out.push_back({en, q, scale * v[q]});
+  };
+  eval_face = [&](int e, int kf, int c, const double* xi, double scale, std::vector<Term>& out) {
+    const int en = n_edges + elem_face[(size_t)e * 6 + kf - 12];
+    if (master[en] != en) {
+      eval_master(master[en], e, xi, c, scale, out);
+      return;
+    }
+    const int d = (kf - 12) / 2, sd = (kf - 12) % 2;
+    const int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+    const int eax = (c == a) ? b : a, comp = (c == a) ? 0 : 1;
+    const int rF = ent_r[en];
+    double vo[MAXF1D + 1], vc[MAXF1D + 1];
+    lag_open(rF, xi[c], vo);
+    lag_closed(rF, xi[eax], vc);
+    for (int ia = 0; ia < rF; ++ia)
+      for (int ib = 1; ib < rF; ++ib)
+        out.push_back({en, comp * rF * (rF - 1) + ia * (rF - 1) + (ib - 1), scale * vo[ia] * vc[ib]});
+    for (int send = 0; send < 2; ++send) {
+      const double wv = vc[send ? rF : 0];
+      if (wv == 0.0) continue;
+      int pos[3];
+      pos[d] = sd;
+      pos[eax] = send;
+      const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+      double xe[3] = {xi[0], xi[1], xi[2]};
+      xe[eax] = (double)send;
+      eval_edge(e, c * 4 + pos[d1] + 2 * pos[d2], xe, scale * wv, out);
+    }
+  };
+
+  // Fixed E-hat values per master entity on Dirichlet faces: nodal
+  // interpolation of the tangential datum at the entity's own nodes, evaluated
+  // in its owner element: coefficient = E_t(x_node) . (J e_c).
+  std::vector<std::vector<double2>> fixval(n_ent);
+  for (int en = 0; en < n_ent; ++en) {
+    if (master[en] != en || dir_grp[en] < 0) continue;
+    const dpg_dirichlet_group& g = h->dirichlet[dir_grp[en]];
+    const int rE = ent_r[en], nd = ent_dofs(en);
+    fixval[en].assign(nd, make_double2(0.0, 0.0));
+    if (g.kind == DPG_DIRICHLET_ZERO) continue;
+    const int e = owner_elem[en], slot = owner_slot[en];
+    for (int q = 0; q < nd; ++q) {
+      double xi[3];
+      int c;
+      if (slot < 12) {
+        c = slot / 4;
+        const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
+        xi[c] = onodes[rE][q];
+        xi[d1] = (double)((slot % 4) & 1);
+        xi[d2] = (double)((slot % 4) >> 1);
+      } else {
+        const int d = (slot - 12) / 2, sd = (slot - 12) % 2;
+        const int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+        const int comp = q / (rE * (rE - 1)), rem = q % (rE * (rE - 1));
+        c = comp ? b : a;
+        const int eax = comp ? a : b;
+        xi[d] = (double)sd;
+        xi[c] = onodes[rE][rem / (rE - 1)];
+        xi[eax] = cnodes[rE][rem % (rE - 1) + 1];
+      }
+      double J[3][3], x[3];
+      trilinear(&X[(size_t)e * 24], xi, J, x);
+      // outward unit normal of the deciding Dirichlet face, at its centre
+      // (boundary faces are planar; the datum n x E_D refers to it)
+      int f = dir_src_face[en], es = dir_src_elem[en];
+      int d = f / 2;
+      double xc[3] = {0.5, 0.5, 0.5}, Js[3][3], xs[3], Jsi[3][3];
+      xc[d] = (f % 2) ? 1.0 : 0.0;
+      trilinear(&X[(size_t)es * 24], xc, Js, xs);
+      inv3(Js, Jsi);
+      double sgn = (f % 2) ? 1.0 : -1.0;
+      double nrm[3] = {sgn * Jsi[d][0], sgn * Jsi[d][1], sgn * Jsi[d][2]};
+      double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+      for (int a2 = 0; a2 < 3; ++a2) nrm[a2] /= nn;
+      cplx Et[3];
+      if (g.kind == DPG_DIRICHLET_SIN_PI_X2) {
+        // n x E = v with v = (sin(pi x2), 0, 0)  =>  E_t = v x n
+        double v[3] = {std::sin(3.14159265358979323846 * x[1]), 0.0, 0.0};
+        Et[0] = {v[1] * nrm[2] - v[2] * nrm[1], 0.0};
+        Et[1] = {v[2] * nrm[0] - v[0] * nrm[2], 0.0};
+        Et[2] = {v[0] * nrm[1] - v[1] * nrm[0], 0.0};
+      } else {
+        cplx E[3];
+        te_E(g, h->omega, x, E);
+        // E_t = E - (E . n) n
+        cplx en_{0, 0};
+        for (int a2 = 0; a2 < 3; ++a2) {
+          en_.re += E[a2].re * nrm[a2];
+          en_.im += E[a2].im * nrm[a2];
+        }
+        for (int a2 = 0; a2 < 3; ++a2) Et[a2] = {E[a2].re - en_.re * nrm[a2], E[a2].im - en_.im * nrm[a2]};
+      }
+      double2 val = make_double2(0.0, 0.0);
+      for (int a2 = 0; a2 < 3; ++a2) {
+        val.x += Et[a2].re * J[a2][c];
+        val.y += Et[a2].im * J[a2][c];
+      }
+      fixval[en][q] = val;
+    }
+  }
+
+  // Per element: R rows through the masters, the global entities they touch
+  // (elem_ents, which also drive the CSR pattern and the colouring), and a
+  // layout of those entities' unknowns in the element's own trace slots.
   h->l2g.assign((size_t)tot.h, -2);
   std::vector<double2> xfix((size_t)tot.h, make_double2(0.0, 0.0));
   h->elem_sig.assign(ne, -1);
   h->rsig.clear();
   std::vector<int32_t> rint;
   std::vector<double> rdbl;
-  std::map<std::vector<int>, int> sig_id;
+  std::unordered_map<uint64_t, std::vector<int>> sig_by_hash;
+  std::vector<std::vector<int>> elem_ents(ne);
+  std::vector<Term> terms;
   for (int e = 0; e < ne; ++e) {
     const Group& G = h->grp[h->elem_grp[e]];
     const LocalMap& L = lmap[h->elem_grp[e]];
     const int r = G.sz.r, nt = G.sz.nt;
     const int64_t o = h->off[e].h;
-    double onode[MAXF1D], cnode[MAXF1D], wdum[MAXF1D];
-    bool restricted = false;
+    std::vector<std::vector<Term>> rows(nt);
     for (int t = 0; t < nt; ++t) {
-      const int en = elem_entity(e, L.ent[t]);
-      const int rE = ent_r[en];
-      if (rE < r) restricted = true;
-      int q;  // index within the entity at its own order, or -1 (slot unused)
-      if (L.ent[t] < 12) {
-        q = L.ia[t] < rE ? L.ia[t] : -1;
-      } else {
-        const int comp = L.idx[t] / (r * (r - 1));
-        q = (L.ia[t] < rE && L.ib[t] <= rE - 1) ? comp * rE * (rE - 1) + L.ia[t] * (rE - 1) + (L.ib[t] - 1) : -1;
-      }
-      if (q < 0) continue;
-      int32_t gE = dir_grp[en] >= 0 ? -1 : (int32_t)(startE[en] + q);
-      int32_t gH = h_drop[en] ? -2 : (int32_t)(startH[en] + q);
-      h->l2g[o + t] = gE;
-      h->l2g[o + nt + t] = gH;
-      if (gE == -1) {
-        const dpg_dirichlet_group& g = h->dirichlet[dir_grp[en]];
-        double2 val = make_double2(0.0, 0.0);
-        if (g.kind != DPG_DIRICHLET_ZERO) {
-          // nodal interpolation at the entity's own nodes: open node q of
-          // order rE along c, closed nodes of order rE across (the element's
-          // corner coordinates 0 / 1 on the entity); evaluated in this element
-          // (the node and J e_c agree between neighbours)
-          gauss_legendre01(rE, onode, wdum);
-          gauss_lobatto01(rE + 1, cnode);
-          const int pk = L.pk[t];
-          const int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
-          double xi[3];
-          for (int d = 0; d < 3; ++d) {
-            if (d == c)
-              xi[d] = onode[L.ia[t]];
-            else
-              xi[d] = ii[d] == 0 ? 0.0 : (ii[d] == r ? 1.0 : cnode[ii[d]]);
+      const int pk = L.pk[t];
+      const int c = pk & 3, ii[3] = {(pk >> 2) & 15, (pk >> 6) & 15, (pk >> 10) & 15};
+      double xi[3];
+      for (int d = 0; d < 3; ++d) xi[d] = d == c ? onodes[r][ii[d]] : cnodes[r][ii[d]];
+      terms.clear();
+      if (L.ent[t] < 12)
+        eval_edge(e, L.ent[t], xi, 1.0, terms);
+      else
+        eval_face(e, L.ent[t], c, xi, 1.0, terms);
+      std::vector<Term>& row = rows[t];
+      for (const Term& tm : terms) {  // merge repeated (entity, index)
+        if (tm.w == 0.0) continue;
+        bool merged = false;
+        for (Term& q : row)
+          if (q.ent == tm.ent && q.idx == tm.idx) {
+            q.w += tm.w;
+            merged = true;
+            break;
           }
-          double J[3][3], x[3];
-          trilinear(&X[(size_t)e * 24], xi, J, x);
-          // outward unit normal of the deciding Dirichlet face, at its centre
-          // (boundary faces are planar; the datum n x E_D refers to it)
-          int f = dir_src_face[en], es = dir_src_elem[en];
-          int d = f / 2;
-          double xc[3] = {0.5, 0.5, 0.5}, Js[3][3], xs[3], Jsi[3][3];
-          xc[d] = (f % 2) ? 1.0 : 0.0;
-          trilinear(&X[(size_t)es * 24], xc, Js, xs);
-          inv3(Js, Jsi);
-          double sgn = (f % 2) ? 1.0 : -1.0;
-          double nrm[3] = {sgn * Jsi[d][0], sgn * Jsi[d][1], sgn * Jsi[d][2]};
-          double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-          for (int a = 0; a < 3; ++a) nrm[a] /= nn;
-          cplx Et[3];
-          if (g.kind == DPG_DIRICHLET_SIN_PI_X2) {
-            // n x E = v with v = (sin(pi x2), 0, 0)  =>  E_t = v x n
-            double v[3] = {std::sin(3.14159265358979323846 * x[1]), 0.0, 0.0};
-            Et[0] = {v[1] * nrm[2] - v[2] * nrm[1], 0.0};
-            Et[1] = {v[2] * nrm[0] - v[0] * nrm[2], 0.0};
-            Et[2] = {v[0] * nrm[1] - v[1] * nrm[0], 0.0};
-          } else {
-            cplx E[3];
-            te_E(g, h->omega, x, E);
-            // E_t = E - (E . n) n
-            cplx en_{0, 0};
-            for (int a = 0; a < 3; ++a) {
-              en_.re += E[a].re * nrm[a];
-              en_.im += E[a].im * nrm[a];
-            }
-            for (int a = 0; a < 3; ++a) Et[a] = {E[a].re - en_.re * nrm[a], E[a].im - en_.im * nrm[a]};
-          }
-          for (int a = 0; a < 3; ++a) {
-            val.x += Et[a].re * J[a][c];
-            val.y += Et[a].im * J[a][c];
-          }
-        }
-        xfix[o + t] = val;
+        if (!merged) row.push_back(tm);
       }
     }
-    if (!restricted) continue;
-    // signature: degree and the orders of the 18 entities
-    std::vector<int> key(19);
-    key[0] = r;
-    for (int k = 0; k < 18; ++k) key[1 + k] = ent_r[elem_entity(e, k)];
-    auto it = sig_id.find(key);
-    if (it != sig_id.end()) {
-      h->elem_sig[e] = it->second;
+    // global entities touched
+    std::vector<int>& ge = elem_ents[e];
+    for (const auto& row : rows)
+      for (const Term& q : row) ge.push_back(q.ent);
+    std::sort(ge.begin(), ge.end());
+    ge.erase(std::unique(ge.begin(), ge.end()), ge.end());
+    // slots: an entity goes to the local slot whose own master it is, the rest
+    // to free local slots of the same kind and enough capacity
+    int slot_ent[18];
+    for (int k = 0; k < 18; ++k) slot_ent[k] = -1;
+    std::vector<char> placed(ge.size(), 0);
+    for (int k = 0; k < 18; ++k) {
+      const int mk = master[elem_entity(e, k)];
+      for (size_t gi = 0; gi < ge.size(); ++gi)
+        if (!placed[gi] && ge[gi] == mk && ((k < 12) == (mk < n_edges))) {
+          slot_ent[k] = mk;
+          placed[gi] = 1;
+          break;
+        }
+    }
+    for (size_t gi = 0; gi < ge.size(); ++gi) {
+      if (placed[gi]) continue;
+      const bool is_edge = ge[gi] < n_edges;
+      for (int k = is_edge ? 0 : 12; k < (is_edge ? 12 : 18); ++k)
+        if (slot_ent[k] < 0 && ent_r[ge[gi]] <= r) {
+          slot_ent[k] = ge[gi];
+          placed[gi] = 1;
+          break;
+        }
+      if (!placed[gi]) {
+        h->err = "element " + std::to_string(e) + ": its constrained trace needs more slots than it has";
+        return DPG_ERR_UNSUPPORTED;
+      }
+    }
+    // (entity, global index) -> local trace function t
+    auto slot_of = [&](int en, int idx) -> int {
+      for (int k = 0; k < 18; ++k)
+        if (slot_ent[k] == en) {
+          const int rE = ent_r[en];
+          if (k < 12) return L.lookup[k][idx];
+          const int comp = idx / (rE * (rE - 1)), rem = idx % (rE * (rE - 1));
+          return L.lookup[k][comp * r * (r - 1) + (rem / (rE - 1)) * (r - 1) + rem % (rE - 1)];
+        }
+      return -1;
+    };
+    // trace map and fixed values of the slots
+    for (int k = 0; k < 18; ++k) {
+      const int en = slot_ent[k];
+      if (en < 0) continue;
+      for (int q = 0; q < ent_dofs(en); ++q) {
+        const int t = slot_of(en, q);
+        const int32_t gE = dir_grp[en] >= 0 ? -1 : (int32_t)(startE[en] + q);
+        const int32_t gH = h_drop[en] ? -2 : (int32_t)(startH[en] + q);
+        h->l2g[o + t] = gE;
+        h->l2g[o + nt + t] = gH;
+        if (gE == -1) xfix[o + t] = fixval[en][q];
+      }
+    }
+    // R over the slots: identity for an element whose entities are its own
+    // masters at its own order
+    std::vector<int> rc(nt + 1, 0), rcol;
+    std::vector<double> rw;
+    bool identity = true;
+    for (int t = 0; t < nt; ++t) {
+      for (const Term& q : rows[t]) {
+        const int col = slot_of(q.ent, q.idx);
+        if (col < 0) {
+          h->err = "element " + std::to_string(e) + ": a constrained trace unknown has no slot";
+          return DPG_ERR_UNSUPPORTED;
+        }
+        rcol.push_back(col);
+        rw.push_back(q.w);
+        identity = identity && col == t && q.w == 1.0;
+      }
+      rc[t + 1] = (int)rcol.size();
+      identity = identity && rows[t].size() == 1;
+    }
+    if (identity) continue;
+    // signature: content hash of the row-compressed R
+    uint64_t hsh = 1469598103934665603ull ^ (uint64_t)nt;
+    auto mix = [&](uint64_t v) {
+      hsh ^= v;
+      hsh *= 1099511628211ull;
+    };
+    for (int t = 0; t <= nt; ++t) mix((uint64_t)rc[t]);
+    for (size_t k = 0; k < rcol.size(); ++k) {
+      uint64_t bits;
+      std::memcpy(&bits, &rw[k], 8);
+      mix((uint64_t)rcol[k]);
+      mix(bits);
+    }
+    int found = -1;
+    for (int id : sig_by_hash[hsh]) {
+      const RSig& q = h->rsig[id];
+      if (q.nt != nt) continue;
+      bool same = true;
+      for (int t = 0; t <= nt && same; ++t) same = rint[q.rptr + t] == rc[t];
+      for (size_t k = 0; k < rcol.size() && same; ++k)
+        same = rint[q.ridx + k] == rcol[k] && rdbl[q.rw + k] == rw[k];
+      if (same) {
+        found = id;
+        break;
+      }
+    }
+    if (found >= 0) {
+      h->elem_sig[e] = found;
       continue;
-    }
-    // R (nt x nt, one field): row t = element trace function, column = slot
-    std::vector<double> R((size_t)nt * nt, 0.0);
-    double oK[MAXF1D], cK[MAXF1D];
-    gauss_legendre01(r, oK, wdum);
-    gauss_lobatto01(r + 1, cK);
-    double val[MAXF1D], der[MAXF1D], vo[MAXF1D], vc[MAXF1D];
-    for (int t = 0; t < nt; ++t) {
-      const int slot = L.ent[t];
-      const int c = L.c[t];
-      const double xc = oK[L.ia[t]];
-      auto add_edge = [&](int eslot, double scale) {
-        const int re = key[1 + eslot];
-        double on[MAXF1D];
-        gauss_legendre01(re, on, wdum);
-        lagrange1d(on, re, xc, val, der);
-        for (int q = 0; q < re; ++q) {
-          const int col = L.lookup[eslot][q];
-          R[(size_t)t * nt + col] += scale * val[q];
-        }
-      };
-      if (slot < 12) {
-        add_edge(slot, 1.0);
-        continue;
-      }
-      const int rF = key[1 + slot];
-      const int dn = (slot - 12) / 2, sd = (slot - 12) % 2;
-      const int a = (dn == 0) ? 1 : 0, b = (dn == 2) ? 1 : 2;
-      const int eo = (c == a) ? b : a;
-      const int comp = (c == a) ? 0 : 1;
-      const double xe = cK[L.ib[t]];
-      double on[MAXF1D], cn[MAXF1D];
-      gauss_legendre01(rF, on, wdum);
-      gauss_lobatto01(rF + 1, cn);
-      lagrange1d(on, rF, xc, vo, der);
-      lagrange1d(cn, rF + 1, xe, vc, der);
-      for (int ia = 0; ia < rF; ++ia)
-        for (int ib = 1; ib < rF; ++ib) {
-          const int col = L.lookup[slot][comp * r * (r - 1) + ia * (r - 1) + (ib - 1)];
-          R[(size_t)t * nt + col] += vo[ia] * vc[ib];
-        }
-      // the face's two edges along c, at eo = 0 (closed end 0) and eo = 1 (end rF)
-      for (int send = 0; send < 2; ++send) {
-        int pos[3];
-        pos[dn] = sd;
-        pos[eo] = send;
-        const int d1 = (c == 0) ? 1 : 0, d2 = (c == 2) ? 1 : 2;
-        const int eslot = c * 4 + pos[d1] + 2 * pos[d2];
-        add_edge(eslot, vc[send ? rF : 0]);
-      }
     }
     RSig rs{};
     rs.nt = nt;
+    // column-compressed form
+    std::vector<int> cc(nt + 1, 0);
+    for (int col : rcol) cc[col + 1]++;
+    for (int t = 0; t < nt; ++t) cc[t + 1] += cc[t];
+    std::vector<int> crow(rcol.size());
+    std::vector<double> cw(rcol.size());
+    std::vector<int> fill(cc.begin(), cc.end() - 1);
+    for (int t = 0; t < nt; ++t)
+      for (int k = rc[t]; k < rc[t + 1]; ++k) {
+        const int dst = fill[rcol[k]]++;
+        crow[dst] = t;
+        cw[dst] = rw[k];
+      }
     rs.cptr = (int64_t)rint.size();
-    std::vector<int> cnt(nt + 1, 0);
-    for (int t = 0; t < nt; ++t)
-      for (int col = 0; col < nt; ++col)
-        if (R[(size_t)t * nt + col] != 0.0) cnt[col + 1]++;
-    for (int col = 0; col < nt; ++col) cnt[col + 1] += cnt[col];
-    rint.insert(rint.end(), cnt.begin(), cnt.end());
+    rint.insert(rint.end(), cc.begin(), cc.end());
     rs.cidx = (int64_t)rint.size();
+    rint.insert(rint.end(), crow.begin(), crow.end());
     rs.cw = (int64_t)rdbl.size();
-    for (int col = 0; col < nt; ++col)
-      for (int t = 0; t < nt; ++t)
-        if (R[(size_t)t * nt + col] != 0.0) {
-          rint.push_back(t);
-          rdbl.push_back(R[(size_t)t * nt + col]);
-        }
+    rdbl.insert(rdbl.end(), cw.begin(), cw.end());
     rs.rptr = (int64_t)rint.size();
-    std::vector<int> rc(nt + 1, 0);
-    for (int t = 0; t < nt; ++t)
-      for (int col = 0; col < nt; ++col)
-        if (R[(size_t)t * nt + col] != 0.0) rc[t + 1]++;
-    for (int t = 0; t < nt; ++t) rc[t + 1] += rc[t];
     rint.insert(rint.end(), rc.begin(), rc.end());
     rs.ridx = (int64_t)rint.size();
+    rint.insert(rint.end(), rcol.begin(), rcol.end());
     rs.rw = (int64_t)rdbl.size();
-    for (int t = 0; t < nt; ++t)
-      for (int col = 0; col < nt; ++col)
-        if (R[(size_t)t * nt + col] != 0.0) {
-          rint.push_back(col);
-          rdbl.push_back(R[(size_t)t * nt + col]);
-        }
+    rdbl.insert(rdbl.end(), rw.begin(), rw.end());
     const int id = (int)h->rsig.size();
     h->rsig.push_back(rs);
-    sig_id.emplace(key, id);
+    sig_by_hash[hsh].push_back(id);
     h->elem_sig[e] = id;
   }
 
-  // ---- colouring (elements sharing a vertex get different colours) ----------
+  // ---- colouring: elements that touch a common global entity (directly or
+  // through a hanging constraint) get different colours ----------------------
   {
-    std::vector<std::vector<int>> v2e(m->n_vert);
+    std::vector<std::vector<int>> ent_el(n_ent);
     for (int e = 0; e < ne; ++e)
-      for (int v = 0; v < 8; ++v) v2e[m->elem[8 * (size_t)e + v]].push_back(e);
+      for (int en : elem_ents[e]) ent_el[en].push_back(e);
     std::vector<int> color(ne, -1);
     int ncol = 0;
     std::vector<int> mark;
     for (int e = 0; e < ne; ++e) {
       mark.assign(ncol + 1, 0);
-      for (int v = 0; v < 8; ++v)
-        for (int o : v2e[m->elem[8 * (size_t)e + v]])
-          if (color[o] >= 0) mark[color[o]] = 1;
+      for (int en : elem_ents[e])
+        for (int o2 : ent_el[en])
+          if (color[o2] >= 0) mark[color[o2]] = 1;
       int c = 0;
       while (c < ncol && mark[c]) ++c;
       color[e] = c;
@@ -638,10 +949,8 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   // in cols[colptr_b .. colptr_b + W_b) (sorted).  Only these per-entity lists
   // are stored, not one column index per non-zero.
   std::vector<std::vector<int>> ent_elems(n_ent);
-  for (int e = 0; e < ne; ++e) {
-    for (int k = 0; k < 12; ++k) ent_elems[elem_edge[(size_t)e * 12 + k]].push_back(e);
-    for (int k = 0; k < 6; ++k) ent_elems[n_edges + elem_face[(size_t)e * 6 + k]].push_back(e);
-  }
+  for (int e = 0; e < ne; ++e)
+    for (int en : elem_ents[e]) ent_elems[en].push_back(e);
   h->blk.clear();
   h->blk_colptr.clear();
   h->cols.clear();
@@ -651,10 +960,7 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     const int dE = startE[en] >= 0 ? ent_dofs(en) : 0, dH = startH[en] >= 0 ? ent_dofs(en) : 0;
     if (dE + dH == 0) continue;
     std::vector<int> nb;
-    for (int e : ent_elems[en]) {
-      for (int k = 0; k < 12; ++k) nb.push_back(elem_edge[(size_t)e * 12 + k]);
-      for (int k = 0; k < 6; ++k) nb.push_back(n_edges + elem_face[(size_t)e * 6 + k]);
-    }
+    for (int e : ent_elems[en]) nb.insert(nb.end(), elem_ents[e].begin(), elem_ents[e].end());
     std::sort(nb.begin(), nb.end());
     nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
     const int64_t cp = (int64_t)h->cols.size();

@@ -160,10 +160,21 @@ __device__ __forceinline__ bool grid_barrier(CgState* st, unsigned int& gen) {
 
 // Block-level sum of (a, b) into red[slot*G + block] pairs, then every block
 // sums all partials in index order.  All threads get the totals.
-__device__ __forceinline__ void block_partial(double a, double b, double* red_a, double* red_b) {
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-lane partials are in the solve precision R (FP32 for the inner solves of
+// iterative refinement, whose tolerance is ~1e-3); each warp's total is widened
+// to FP64 once, and block / grid sums are FP64 in a fixed order.
+template <typename R>
+__device__ __forceinline__ void block_partial(R a_r, R b_r, double* red_a, double* red_b) {
   __shared__ double sw[2][CG_THREADS / 32];
-  a = warp_sum(a);
-  b = warp_sum(b);
+  const double a = (double)warp_sum_r(a_r);
+  const double b = (double)warp_sum_r(b_r);
   if ((threadIdx.x & 31) == 0) {
     sw[0][threadIdx.x >> 5] = a;
     sw[1][threadIdx.x >> 5] = b;
@@ -180,26 +191,28 @@ __device__ __forceinline__ void block_partial(double a, double b, double* red_a,
   }
 }
 
+// One warp of each block sums the per-block partials (FP64, fixed order: lane
+// strides then the shuffle tree), so every block obtains identical totals
+// while the FP64 pipe (2 DFMA/clk/SM on B300) sees one warp's work, not eight.
 __device__ __forceinline__ void grid_total(const double* red_a, const double* red_b, double& ta, double& tb) {
-  __shared__ double sw[2][CG_THREADS / 32];
-  double a = 0, b = 0;
-  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
-    a += ((volatile const double*)red_a)[k];
-    if (red_b) b += ((volatile const double*)red_b)[k];
+  __shared__ double sw[2];
+  if (threadIdx.x < 32) {
+    double a = 0, b = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) {
+      a += ((volatile const double*)red_a)[k];
+      if (red_b) b += ((volatile const double*)red_b)[k];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) {
+      sw[0] = a;
+      sw[1] = b;
+    }
   }
-  a = warp_sum(a);
-  b = warp_sum(b);
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    sw[0][threadIdx.x >> 5] = a;
-    sw[1][threadIdx.x >> 5] = b;
-  }
+  ta = sw[0];
+  tb = sw[1];
   __syncthreads();
-  ta = tb = 0;
-  for (int k = 0; k < CG_THREADS / 32; ++k) {
-    ta += sw[0][k];
-    tb += sw[1][k];
-  }
 }
 
 template <typename V> struct RealOf;
@@ -207,6 +220,7 @@ template <> struct RealOf<double2> { using T = double; };
 template <> struct RealOf<float2> { using T = float; };
 __device__ __forceinline__ double2 mkv(double a, double b, double2*) { return make_double2(a, b); }
 __device__ __forceinline__ float2 mkv(double a, double b, float2*) { return make_float2((float)a, (float)b); }
+__device__ __forceinline__ float2 mkv(float a, float b, float2*) { return make_float2(a, b); }
 
 // y_row = (A x)_row by one warp; the row's columns are its entity's list.
 // Products and the row sum in the matrix precision Mv.
@@ -258,7 +272,8 @@ __device__ __forceinline__ V row_spmv(const SysView& S, int64_t row, const Mv* _
 template <typename V>
 __device__ __forceinline__ void block_precond(const SysView& S, int b, int precond, const V* __restrict__ r, V* z,
                                               const typename RealOf<V>::T* __restrict__ dinv,
-                                              const V* __restrict__ binv, V* rs, double& rr, double& rz) {
+                                              const V* __restrict__ binv, V* rs, typename RealOf<V>::T& rr,
+                                              typename RealOf<V>::T& rz) {
   using R = typename RealOf<V>::T;
   const int lane = threadIdx.x & 31;
   const int4 B = S.blk[b];
@@ -279,8 +294,8 @@ __device__ __forceinline__ void block_precond(const SysView& S, int b, int preco
         const V ri = rs[i];
         const V zv = mkv(zr, zi, (V*)nullptr);
         z[B.x + i] = zv;
-        rr += (double)ri.x * ri.x + (double)ri.y * ri.y;
-        rz += (double)ri.x * zr + (double)ri.y * zi;
+        rr += ri.x * ri.x + ri.y * ri.y;
+        rz += ri.x * zr + ri.y * zi;
       }
     }
     __syncwarp();
@@ -296,8 +311,8 @@ __device__ __forceinline__ void block_precond(const SysView& S, int b, int preco
       zi.y = d * ri.y;
     }
     z[row] = zi;
-    rr += (double)ri.x * ri.x + (double)ri.y * ri.y;
-    rz += (double)ri.x * zi.x + (double)ri.y * zi.y;
+    rr += ri.x * ri.x + ri.y * ri.y;
+    rz += ri.x * zi.x + ri.y * zi.y;
   }
 }
 
@@ -306,7 +321,7 @@ __device__ __forceinline__ void block_precond(const SysView& S, int b, int preco
 // matrix and of the SpMV products (FP32 values with FP64 recurrences keeps the
 // convergence rate of FP64 CG at the bandwidth of an FP32 matrix).
 template <typename V, typename Mv>
-__global__ void __launch_bounds__(CG_THREADS) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
+__global__ void __launch_bounds__(CG_THREADS, 5) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
                                                              V* Ap, V* z, int precond,
                                                              const typename RealOf<V>::T* __restrict__ dinv,
                                                              const V* __restrict__ binv, double* red, CgState* st) {
@@ -323,9 +338,9 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_persistent(SysView S, const M
   const double tol2 = st->tol2;
   const int max_iter = st->max_iter;
   // phase 0: z = M^{-1} r, p = z, x = 0
-  double rr = 0, rz = 0;
+  R rr0 = 0, rz0 = 0;
   for (int b = gw; b < S.nblk; b += warps) {
-    block_precond<V>(S, b, precond, r, z, dinv, binv, rs, rr, rz);
+    block_precond<V>(S, b, precond, r, z, dinv, binv, rs, rr0, rz0);
     __syncwarp();
     const int4 B = S.blk[b];
     for (int i = threadIdx.x & 31; i < B.y; i += 32) {
@@ -333,29 +348,30 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_persistent(SysView S, const M
       x[B.x + i] = mkv(0.0, 0.0, (V*)nullptr);
     }
   }
-  block_partial(rr, rz, redB0, redB1);
+  block_partial(rr0, rz0, redB0, redB1);
   if (!grid_barrier(st, gen)) return;
+  double rr, rz;
   grid_total(redB0, redB1, rr, rz);
   int it = 0;
   bool done = rr <= tol2;
   while (!done && it < max_iter) {
     // A: Ap = A p and Re(p^H A p)
-    double pap = 0;
+    R pap = 0;
     for (int64_t row = gw; row < S.n; row += warps) {
       const V y = row_spmv<V, Mv>(S, row, val, p);
       if ((threadIdx.x & 31) == 0) {
         Ap[row] = y;
         const V pr = p[row];
-        pap += (double)pr.x * y.x + (double)pr.y * y.y;
+        pap += pr.x * y.x + pr.y * y.y;
       }
     }
-    block_partial(pap, 0.0, redA, nullptr);
+    block_partial(pap, (R)0, redA, nullptr);
     if (!grid_barrier(st, gen)) return;
     double tpap, dummy;
     grid_total(redA, nullptr, tpap, dummy);
     const R alpha = (R)(rz / tpap);
     // B: x += alpha p, r -= alpha Ap, z = M^{-1} r
-    double rr2 = 0, rz2 = 0;
+    R rr2 = 0, rz2 = 0;
     for (int b = gw; b < S.nblk; b += warps) {
       const int4 B = S.blk[b];
       for (int i = threadIdx.x & 31; i < B.y; i += 32) {
@@ -672,7 +688,7 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     h->err = "bad CG arguments";
     return DPG_ERR_ARG;
   }
-  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI) ||
+  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0) ||
       ((mode & DPG_CG_JACOBI) && (mode & DPG_CG_BLOCK_JACOBI))) {
     h->err = "unknown CG mode";
     return DPG_ERR_ARG;
@@ -711,7 +727,7 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     h->launches += 1;
     h->have_val32 = true;
   }
-  // r = b (x = 0)
+  // ||b|| (and r = b for x0 = 0)
   double bb = 0;
   rc = residual(h, nullptr, rhs, h->d_r, s, &bb);
   if (rc) return rc;
@@ -723,8 +739,15 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
   // (inner tolerance inner_rtol); with FP64 inner solves the first pass already
   // targets the final tolerance and further passes only replace a recursive
   // residual that drifted from the true one.
-  DPG_CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double2) * n, s));
   double rnorm = bnorm;
+  if (mode & DPG_CG_X0) {  // warm start: r = b - A x for the caller's x
+    double r2 = 0;
+    rc = residual(h, x, rhs, h->d_r, s, &r2);
+    if (rc) return rc;
+    rnorm = std::sqrt(r2);
+  } else {
+    DPG_CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double2) * n, s));
+  }
   bool conv = rnorm <= tol;
   const int max_outer = ir ? 100 : 8;
   while (!conv && total_iters < max_iter && outer < max_outer) {

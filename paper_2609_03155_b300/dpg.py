@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import check, ptr, stream_handle
+from ._lib import DPGError, check, ptr, stream_handle  # noqa: F401 (DPGError re-exported)
 
 
 def _robin_groups(mesh):
@@ -170,6 +170,14 @@ class DPG:
         check(_lib.lib().dpg_grad_eps(self.h, ptr(xhat), ptr(mask), C.byref(P), ptr(dre), ptr(dim), cg_mode, rtol,
                                       max_iter, stream_handle(stream)), self.h)
         return P.value, dre, dim
+
+    def power(self, xhat, want_flux=True, stream=None):
+        """Per-element int_K Q_em dV (cuda float64, n_elem) and the outward Poynting flux per Robin group."""
+        q = torch.empty(self.n_elem, dtype=torch.float64, device='cuda')
+        flux = np.zeros(max(1, len(self.mesh.robin)), np.float64) if want_flux else None
+        check(_lib.lib().dpg_power(self.h, ptr(xhat), ptr(q), ptr(flux) if want_flux else None,
+                                   stream_handle(stream)), self.h)
+        return q, (flux[:len(self.mesh.robin)] if want_flux else None)
 
     def trace_map(self):
         """Trace map and fixed values: n_elem x n_h for one degree, else flat at h_off."""

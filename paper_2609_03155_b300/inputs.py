@@ -331,3 +331,76 @@ def refined_box(n, refine, p=1, lengths=(1.0, 1.0, 1.0), omega=5.0, bc="cavity",
                 face_bc=bc_arr, face_grp=grp, omega=omega, robin=[],
                 dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None}, {'kind': DIRICHLET_SIN_PI_X2, 'port': None}],
                 name=name)
+
+
+def amr_box(n, lengths, keep, refine, p=1, omega=5.0, mix=None, seed=20260904, name="amr"):
+    """A masked box grid with one level of 2:1 refinement (hanging faces and edges).
+
+    n = (nx, ny, nz) coarse cells over [0, lx] x [0, ly] x [0, lz]; keep(c) and
+    refine(c) take a coarse cell centre c.  Kept cells not refined are single
+    elements; refined ones are split into 8 children.  Faces without a kept
+    neighbour cell are walls: PEC, and n x E = (sin(pi x2), 0, 0) on the top
+    plane x3 = lz (Sec. 4.2).  Degrees: p for all, or the proportions `mix` for
+    p = 1, 2, ... (seeded permutation, stream 5).
+    """
+    nx, ny, nz = n
+    lx, ly, lz = lengths
+    h = (lx / nx, ly / ny, lz / nz)
+    cen = lambda i, j, k: np.array([(i + 0.5) * h[0], (j + 0.5) * h[1], (k + 0.5) * h[2]])
+    kept = {(i, j, k) for k in range(nz) for j in range(ny) for i in range(nx) if keep(cen(i, j, k))}
+    ref = {c for c in kept if refine(cen(*c))}
+    L = (2 * nx + 1, 2 * ny + 1, 2 * nz + 1)
+    lid = lambda i, j, k: (k * L[1] + j) * L[0] + i
+    elems, walls = [], []
+    for (i, j, k) in sorted(kept, key=lambda c: (c[2], c[1], c[0])):
+        cells = [(c & 1, (c >> 1) & 1, (c >> 2) & 1) for c in range(8)] if (i, j, k) in ref else [None]
+        for ch in cells:
+            if ch is None:
+                base, span = (2 * i, 2 * j, 2 * k), 2
+            else:
+                base, span = (2 * i + ch[0], 2 * j + ch[1], 2 * k + ch[2]), 1
+            elems.append([lid(base[0] + span * (v & 1), base[1] + span * ((v >> 1) & 1),
+                              base[2] + span * ((v >> 2) & 1)) for v in range(8)])
+            w = []
+            for d in range(3):
+                for s in (0, 1):
+                    # a wall when the face lies on the cell's face and no kept cell is across
+                    on_cell_face = ch is None or ch[d] == s
+                    nb = [i, j, k]
+                    nb[d] += 1 if s else -1
+                    w.append(on_cell_face and tuple(nb) not in kept)
+            walls.append(w)
+    elem = np.array(elems, dtype=np.int64)
+    used, inv = np.unique(elem.ravel(), return_inverse=True)
+    ii = used % L[0]
+    jj = (used // L[0]) % L[1]
+    kk = used // (L[0] * L[1])
+    vert = np.stack([ii * lx / (2 * nx), jj * ly / (2 * ny), kk * lz / (2 * nz)], axis=1)
+    elem = inv.reshape(elem.shape).astype(np.int32)
+    ne = elem.shape[0]
+    bc = np.zeros((ne, 6), dtype=np.int8)
+    grp = np.zeros((ne, 6), dtype=np.int16)
+    for e in range(ne):
+        for f in range(6):
+            if walls[e][f]:
+                bc[e, f] = BC_DIRICHLET
+                top = f == 5 and abs(vert[elem[e, 4], 2] - lz) < 1e-12
+                grp[e, f] = 1 if top else 0
+    pk = np.full(ne, p, dtype=np.int8) if mix is None else order_mix(ne, mix, seed)
+    return Mesh(vert=vert, elem=elem, p=pk, eps=np.ones(ne, dtype=complex), mu=np.ones(ne, dtype=complex),
+                face_bc=bc, face_grp=grp, omega=omega, robin=[],
+                dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None}, {'kind': DIRICHLET_SIN_PI_X2, 'port': None}],
+                name=name)
+
+
+def fichera_amr(n_unit, radius=0.75, mix=(0.4, 0.3, 0.2, 0.1), p=None, seed=20260904):
+    """Fichera-corner cavity, n_unit coarse cells per unit length, cells within `radius` of the
+    re-entrant corner (1, 1, 1) refined once (2:1 hanging faces); degrees drawn in `mix`."""
+    def keep(c):
+        lower = c[2] < 2.0 and not (c[0] < 1.0 and c[1] < 1.0 and c[2] < 1.0)
+        top = c[0] > 1.0 and c[1] > 1.0 and c[2] > 2.0
+        return lower or top
+    refine = lambda c: np.linalg.norm(c - np.array([1.0, 1.0, 1.0])) < radius
+    n = (2 * n_unit, 2 * n_unit, 3 * n_unit)
+    return amr_box(n, (2.0, 2.0, 3.0), keep, refine, p=p if p is not None else 1,
+                   mix=None if p is not None else mix, seed=seed, name=f"fichera_amr_{n_unit}_r{radius}")

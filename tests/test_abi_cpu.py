@@ -44,7 +44,8 @@ def _desc(mesh):
 
 def _setup(mesh, **prm):
     d, keep = _desc(mesh)
-    p = _lib.dpg_params(omega=prm.get('omega', 1.0), alpha=prm.get('alpha', 1.0), dp=prm.get('dp', 1), precision=0)
+    p = _lib.dpg_params(omega=prm.get('omega', 1.0), alpha=prm.get('alpha', 1.0), dp=prm.get('dp', 1),
+                        precision=prm.get('precision', 0))
     h = C.c_void_p()
     rc = _lib.lib().dpg_setup_mesh(C.byref(h), C.byref(d), C.byref(p), None)
     return rc, h, _lib.lib().dpg_last_error(None).decode()
@@ -71,12 +72,32 @@ def test_setup_rejects_bad_arguments_before_touching_the_device():
     bad.elem[0] = bad.elem[0][[1, 0, 3, 2, 5, 4, 7, 6]]
     rc, _, msg = _setup(bad)
     assert rc == -2 and "Jacobian" in msg
+    # host-side fault injection: non-finite inputs are errors, not device faults
+    bad = inputs.waveguide_2d_config(p=1)
+    bad.eps = bad.eps.copy()
+    bad.eps[5] = complex(np.nan, 0.0)
+    rc, _, msg = _setup(bad)
+    assert rc == -1 and "non-finite" in msg
+    bad = inputs.waveguide_2d_config(p=1)
+    bad.vert = bad.vert.copy()
+    bad.vert[2, 1] = np.inf
+    rc, _, msg = _setup(bad)
+    assert rc == -2 and "non-finite" in msg
     # degrees outside 1..4 are rejected (mixed degrees within it are accepted)
     bad = inputs.waveguide_2d_config(p=1)
     bad.p = bad.p.copy()
     bad.p[0] = 5
     rc, _, msg = _setup(bad)
     assert rc == -2 and "degree" in msg
+    # empty mesh
+    d, keep = _desc(inputs.waveguide_2d_config(p=1))
+    d.n_elem = 0
+    prm = _lib.dpg_params(omega=1.0, alpha=1.0, dp=1, precision=0)
+    assert L.dpg_setup_mesh(C.byref(h), C.byref(d), C.byref(prm), None) == -1
+    assert "empty" in L.dpg_last_error(None).decode()
+    # unknown precision mode
+    rc, _, msg = _setup(inputs.waveguide_2d_config(p=1), precision=7)
+    assert rc == -9 and "precision" in msg
     # null handles
     assert L.dpg_element_batch(None, 0, None) == -1
     assert L.dpg_assemble(None, None) == -1

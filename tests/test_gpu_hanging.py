@@ -1,0 +1,71 @@
+"""2:1 hanging faces on the CUDA path against the oracle's constrained solve.
+
+Reading (not in the paper, which refines in h without stating the constraint):
+an edge or face lying inside a larger neighbour entity carries no unknowns and
+takes the larger entity's trace.  Numberings differ between the two codes, so
+the comparison is on the number of unknowns, the interior field u_K of every
+element (relative 1e-10, CG to 1e-13 against a direct solve) and eta_K (1e-7 of
+the largest).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import hanging
+from paper_2609_03155_b300 import inputs
+from test_gpu_parity import rel
+
+
+@pytest.fixture(scope="module")
+def dpg_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_03155_b300 import dpg
+    return dpg
+
+
+def _case(name):
+    if name == "one_refined_cell":
+        return inputs.refined_box((2, 1, 1), [(0, 0, 0)], p=1)
+    if name == "two_refined_lossy_mixed":
+        m = inputs.refined_box((2, 2, 1), [(0, 0, 0), (1, 1, 0)], p=lambda e, ch: 1 + (e % 3) if ch else 2)
+        rng = np.random.default_rng(3)
+        m.eps = 1.0 + rng.uniform(0, 4, m.n_elem) + 1j * rng.uniform(0, 2, m.n_elem)
+        m.mu = 1.0 + 0.1j * rng.uniform(0, 1, m.n_elem)
+        return m
+    return inputs.fichera_amr(1, radius=0.9, mix=(0.4, 0.3, 0.3))
+
+
+@pytest.mark.parametrize("name", ["one_refined_cell", "two_refined_lossy_mixed", "fichera_amr_mixed"])
+def test_hanging_faces_match_oracle(dpg_mod, name):
+    mesh = _case(name)
+    sol = hanging.solve(mesh)
+    d = dpg_mod.DPG(mesh)
+    assert d.n == sol['n']
+    d.element_batch()
+    d.assemble()
+    x, rep = d.cg_solve(rtol=1e-13, max_iter=200000)
+    assert rep['converged']
+    u, eta, etag = d.estimate(x)
+    u = u.cpu().numpy().reshape(-1)
+    for e in range(mesh.n_elem):
+        assert rel(u[d.u_off[e]:d.u_off[e + 1]], sol['rec'][e]['u']) < 1e-10, e
+    eta_or = sol['eta']
+    assert np.max(np.abs(eta.cpu().numpy() - eta_or)) < 1e-7 * eta_or.max()
+    d.destroy()
+
+
+def test_hanging_faces_graph_and_chunks_bitwise(dpg_mod):
+    mesh = _case("two_refined_lossy_mixed")
+    out = []
+    for chunk, graph in ((0, False), (3, True)):
+        d = dpg_mod.DPG(mesh, chunk=chunk)
+        d.set_graph(graph)
+        d.element_batch()
+        d.assemble()
+        x, _ = d.cg_solve(rtol=1e-12)
+        out.append(x.cpu().numpy())
+        d.destroy()
+    assert np.array_equal(out[0], out[1])

@@ -279,3 +279,59 @@ def test_real_path_matches_complex_path(dpg_mod):
     assert rel(u_r.cpu().numpy(), u_c.cpu().numpy()) < 1e-10
     assert np.max(np.abs(eta_r.cpu().numpy() - eta_c.cpu().numpy())) < 1e-7 * eta_c.cpu().numpy().max()
     d.destroy()
+
+
+def test_cg_warm_start_resumes_a_stopped_solve(dpg_mod):
+    """DPG_CG_X0: a solve stopped at 1e-5 and resumed reaches the cold solve's answer with fewer new iterations."""
+    from paper_2609_03155_b300 import _lib
+    mesh = inputs.waveguide_3d_config(4, 2, 6, p=2)
+    d = dpg_mod.DPG(mesh)
+    d.element_batch()
+    d.assemble()
+    x_cold, rep_cold = d.cg_solve(rtol=1e-12, max_iter=100000)
+    x, rep1 = d.cg_solve(rtol=1e-5, max_iter=100000)
+    x, rep2 = d.cg_solve(x=x, mode=_lib.DPG_CG_FP64 | _lib.DPG_CG_X0, rtol=1e-12, max_iter=100000)
+    assert rep2['converged'] and rep2['iterations'] < rep_cold['iterations']
+    assert rel(x.cpu().numpy(), x_cold.cpu().numpy()) < 1e-9
+    d.destroy()
+
+
+def _condensation_floor(el, S):
+    """Relative difference of S between two backward-stable FP64 routes (Cholesky, as the oracle does,
+    and the explicit inverse of G): how closely any FP64 condensation of this element can agree."""
+    BB = np.hstack([el.B, el.Bh])
+    A = BB.conj().T @ np.linalg.inv(el.G) @ BB
+    nu = el.B.shape[1]
+    S_alt = A[nu:, nu:] - A[:nu, nu:].conj().T @ np.linalg.solve(A[:nu, :nu], A[:nu, nu:])
+    return rel(S_alt, S)
+
+
+def test_full_size_waveguide_sampled_elements(dpg_mod):
+    """The 32x16x64 p=2 guide at full size (32,768 elements, the bench workload): element matrices of
+    sampled elements (port corner, interior, wall, outlet) against the oracle, one by one.  These
+    elements are small against the wavelength and G_K has kappa ~ 1e9, so the S_K bound is ten times
+    the disagreement of two FP64 routes on the same element (at least 2e-9)."""
+    mesh = inputs.waveguide_3d_config(32, 16, 64, 2)
+    d = dpg_mod.DPG(mesh)
+    ids = [0, 32 * 16 * 30 + 16 * 8 + 16, 32 * 16 * 40 + 31, mesh.n_elem - 1]
+    out = d.element_dump(ids)
+    d.destroy()
+    for k, e in enumerate(ids):
+        el, cond = _oracle_element(mesh, e)
+        assert rel(out['G'][k], el.G) < 1e-12
+        assert rel(out['B'][k], el.B) < 1e-12
+        assert rel(out['Bh'][k], el.Bh) < 1e-12
+        assert rel(out['S'][k], cond['S']) < max(2e-9, 10 * _condensation_floor(el, cond['S']))
+
+
+def test_cg_reports_non_convergence(dpg_mod):
+    from paper_2609_03155_b300 import _lib
+    mesh = inputs.waveguide_3d_config(4, 2, 6, p=2)
+    d = dpg_mod.DPG(mesh)
+    d.element_batch()
+    d.assemble()
+    with pytest.raises(_lib.DPGError, match="NOT_CONVERGED"):
+        d.cg_solve(rtol=1e-12, max_iter=5)
+    x, rep = d.cg_solve(rtol=1e-12, max_iter=5, raise_on_nonconvergence=False)
+    assert not rep['converged'] and rep['iterations'] <= 5
+    d.destroy()

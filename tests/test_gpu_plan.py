@@ -65,3 +65,18 @@ def test_autotune_keeps_results_bitwise(dpg_mod):
     for u, v in zip(again, ref):
         assert np.array_equal(u, v)
     d.destroy()
+
+
+def test_graph_replay_with_timing(dpg_mod):
+    """Factorisation timing events inside the captured graph are recorded at every replay."""
+    mesh = inputs.waveguide_3d_config(4, 2, 6, p=2)
+    d = dpg_mod.DPG(mesh, chunk=10)
+    d.element_batch()             # capture without timing
+    d.timing_enable(True)
+    d.element_batch()             # re-capture with external event nodes
+    d.element_batch()             # replay
+    t = d.timing_get()
+    assert t["factor_elements"] == 2 * mesh.n_elem
+    assert t["factor_launches"] > 0 and t["factor_ms"] > 0
+    d.assemble()                  # no stale error left behind
+    d.destroy()

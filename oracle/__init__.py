@@ -30,6 +30,14 @@ Readings of the paper taken here (the paper is silent or ambiguous):
   end) are removed from the global system.
 * Dirichlet trace data is imposed by nodal interpolation of the tangential
   field at the Nedelec nodes.
+* Mixed trial degrees (``mixed``): an edge or face carries trace unknowns of
+  order min over its elements of p + 1; each element computes at its own
+  degree and sees the global trace through nodal evaluation, u-hat_K = R_K u-hat.
+* 2:1 hanging faces (``hanging``): an edge or face inside a larger neighbour
+  entity takes that entity's trace (no unknowns of its own).
+* Absorbed power and its adjoint gradient (``power``, ``adjoint``): Q_em of
+  Sec. 3.2; the gradient with respect to Re eps and Im eps separately (G_K is
+  not holomorphic in eps).
 
 Functions whose result has no independent pin are marked "parity unpinned" in
 their docstring; every other function is pinned by ``tests/test_oracle_*``.

@@ -156,47 +156,77 @@ def job_throughput(world, n_elem, ms_step):
     return world * n_elem / (ms_step / 1e3)
 
 
-def cpu_oracle_rate(mesh, n_sample, threads_note=True):
-    """Oracle (as it stands) element pass + estimator on a bounded sample of elements: elements/s."""
+def _oracle_elements(task):
+    """Worker of the CPU baseline: the oracle's element pass + recovery on a few elements (one BLAS thread)."""
     from oracle import element as oel
     from oracle import system as osys
-    # the sample mixes boundary (port / impedance) and interior elements
-    robin = np.where((mesh.face_bc == 2).any(axis=1))[0]
-    inner = np.where(~(mesh.face_bc > 0).any(axis=1))[0]
-    pick = list(robin[: max(1, n_sample // 4)]) + list(inner[: n_sample - max(1, n_sample // 4)])
+    mesh, ids = task
     t0 = time.perf_counter()
-    for e in pick:
+    for e in ids:
         el = oel.element_matrices(mesh.vert[mesh.elem[e]], int(mesh.p[e]), mesh.omega, complex(mesh.eps[e]),
                                   complex(mesh.mu[e]), osys.element_faces(mesh, e))
         c = oel.condense(el)
         oel.recover(el, c, np.zeros(el.Bh.shape[1], complex))
-    dt = time.perf_counter() - t0
-    try:
-        import threadpoolctl
-        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info())
-    except Exception:
-        cores = os.cpu_count()
-    return len(pick) / dt, cores, dt, len(pick)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """Element-parallel CPU oracle: one process per host core (spawned, one BLAS thread each).
+
+    The pool is started with the spawn method before any GPU work is done in
+    the children, and every worker runs the oracle as it stands on its own
+    share of the sampled elements.
+    """
+
+    def __init__(self, workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = workers or max(1, min(os.cpu_count() or 1, 64))
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        self.pool = cf.ProcessPoolExecutor(max_workers=self.workers, mp_context=mp.get_context("spawn"))
+        # start every worker and import the oracle there before anything is timed
+        list(self.pool.map(_oracle_elements, [(None, []) for _ in range(self.workers)]))
+
+    def rate(self, mesh, per_worker):
+        """elements/s of the oracle over a sample of per_worker elements per process (wall clock)."""
+        n_sample = per_worker * self.workers
+        # the sample mixes boundary (port / impedance) and interior elements
+        robin = np.where((mesh.face_bc == 2).any(axis=1))[0]
+        inner = np.where(~(mesh.face_bc > 0).any(axis=1))[0]
+        pick = list(robin[: max(1, n_sample // 4)]) + list(inner[: n_sample - max(1, n_sample // 4)])
+        pick = (pick * (n_sample // max(1, len(pick)) + 1))[:n_sample]
+        tasks = [(mesh, [int(e) for e in pick[k::self.workers]]) for k in range(self.workers)]
+        t0 = time.perf_counter()
+        list(self.pool.map(_oracle_elements, tasks))
+        dt = time.perf_counter() - t0
+        return len(pick) / dt, self.workers, dt, len(pick)
+
+    def close(self):
+        self.pool.shutdown()
 
 
 def run_reference(args, rank):
     mesh = config_mesh(args.config)
     if rank != 0:
         return
+    pool = OraclePool()
     vals = []
     for _ in range(args.warmup):
-        cpu_oracle_rate(mesh, args.ref_sample)
+        pool.rate(mesh, args.ref_sample)
     for _ in range(args.steps):
-        rate, cores, dt, n = cpu_oracle_rate(mesh, args.ref_sample)
+        rate, cores, dt, n = pool.rate(mesh, args.ref_sample)
         vals.append((rate, dt))
+    pool.close()
     rate = statistics.median(v[0] for v in vals)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(v[1] for v in vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": mesh.name, "elements": int(mesh.n_elem), "p": int(mesh.p[0]), "dp": 1},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} elements of {mesh.name} per step (element formation, condensation, "
-                                       f"local recovery and eta_K); the global CG is not in the sample"},
+                             "sample": f"{n} elements of {mesh.name} per step, {args.ref_sample} per process on "
+                                       f"{cores} spawned processes with one BLAS thread each (element formation, "
+                                       f"condensation, local recovery and eta_K); the global CG is not in the sample"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -212,8 +242,10 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--max-iter", type=int, default=200000)
-    ap.add_argument("--cpu-sample", type=int, default=16)
-    ap.add_argument("--ref-sample", type=int, default=8)
+    ap.add_argument("--cpu-sample", type=int, default=2, help="oracle elements per host process (CPU baseline)")
+    ap.add_argument("--ref-sample", type=int, default=1, help="oracle elements per host process per reference step")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="skip the one-step FP64-throughout comparison arm after the timed steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--chunk", type=int, default=0, help="elements per launch (0: library default)")
@@ -231,6 +263,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    # the CPU baseline's process pool starts (spawn) before this process touches the GPU
+    pool = OraclePool() if rank == 0 else None
 
     import torch
     torch.cuda.set_device(local)
@@ -353,7 +387,12 @@ def main():
                 "elements_real": n_real,
                 "elements_complex": n_cplx, "launches": tim["factor_launches"], "avg_launch_ms": fac_avg_ms,
                 "time_s": tim["factor_ms"] / 1e3}
-    # persistent CG kernel (HBM bound)
+    # persistent CG kernel (HBM bound).  Algorithmic bytes per iteration
+    # (the method's own traffic): the matrix values, 16 B per complex FP64
+    # non-zero or 8 B per complex FP32 non-zero of the inner solves, plus six
+    # vector passes; the column lists, the preconditioner's block inverses and
+    # the further vector passes of this implementation are overhead, reported
+    # apart.
     hbm_peak, hbm_src = 6400.0, "fallback 6.4 TB/s (no MEASURED_PEAKS.json)"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -361,20 +400,26 @@ def main():
     except Exception:
         pass
     bpi = d.cg_bytes_per_iteration(mode)
-    # DRAM traffic per iteration / algorithmic bytes of the FP32 inner CG kernel,
-    # from the ncu capture of the 12x6x24 guide (dram__bytes_read.sum +
+    vb = 8 if mode & 1 else 16
+    algo_bpi = vb * int(d.nnz) + 6 * vb * int(d.n)
+    # DRAM traffic per iteration / implementation bytes of the FP32 inner CG
+    # kernel, from the ncu capture of the 12x6x24 guide (dram__bytes_read.sum +
     # dram__bytes_write.sum over 279 iterations); the traffic per iteration
-    # scales with the system, so a launch's traffic is this ratio times its
-    # algorithmic bytes
+    # scales with the system, so a launch's traffic is this ratio times its bytes
     CG_TRAFFIC_RATIO_FP32 = 1.022
-    cg_ach = bpi * tim["cg_kernel_iterations"] / max(1e-9, tim["cg_kernel_ms"] / 1e3) / 1e9
+    cg_s = max(1e-9, tim["cg_kernel_ms"] / 1e3)
+    cg_ach = algo_bpi * tim["cg_kernel_iterations"] / cg_s / 1e9
     roof_cg = {"bound": "hbm", "kernel": "k_cg_persistent<%s> (one cooperative CG solve per launch)"
                % ("float2" if mode & 1 else "double2"),
                "achieved": cg_ach, "peak": hbm_peak, "unit": "GB/s", "frac": cg_ach / hbm_peak,
                "traffic": (CG_TRAFFIC_RATIO_FP32 * bpi * tim["cg_kernel_iterations"] / max(1, tim["cg_kernel_launches"])
                            if mode & 1 else None),
-               "traffic_unit": "bytes per launch (ncu ratio 1.022 x algorithmic, from the 12x6x24 capture)",
-               "peak_source": hbm_src, "bytes_per_iteration": bpi,
+               "traffic_unit": "bytes per launch (ncu ratio 1.022 x implementation bytes, from the 12x6x24 capture)",
+               "peak_source": hbm_src, "bytes_per_iteration": algo_bpi,
+               "bytes_rule": f"{vb} B x nnz + 6 x {vb} B x n (matrix values and six vector passes)",
+               "overhead_bytes_per_iteration": bpi - algo_bpi,
+               "overhead_rule": "per-entity column lists, block-Jacobi inverses and the other vector passes",
+               "achieved_with_overhead": bpi * tim["cg_kernel_iterations"] / cg_s / 1e9,
                "iterations": tim["cg_kernel_iterations"], "launches": tim["cg_kernel_launches"],
                "avg_launch_ms": tim["cg_kernel_ms"] / max(1, tim["cg_kernel_launches"]),
                "time_s": tim["cg_kernel_ms"] / 1e3}
@@ -382,11 +427,13 @@ def main():
         roof, roof2 = roof_cg, roof_fac
     else:
         roof, roof2 = roof_fac, roof_cg
-    # per-iteration cost of the paper's plain FP64 CG on the same system (short capped run)
-    _, rep64 = d.cg_solve(mode=0, rtol=1e-30, max_iter=200, raise_on_nonconvergence=False)
-    fp64_ms_it = rep64["ms"] / max(1, rep64["iterations"])
     cg_iters = last_rep["iterations"]
-    rate, cores, dt, nsamp = cpu_oracle_rate(mesh, args.cpu_sample)
+    # the FP64-throughout arm (the paper's solver: plain FP64 CG from x0 = 0),
+    # one whole step end to end, and the complex-path element rate
+    fp64_arm = None if args.no_fp64_arm else fp64_step(d, mesh, x, args)
+    complex_rate = complex_path_rate(mesh, args) if args.config == "waveguide3d" else None
+    rate, cores, dt, nsamp = pool.rate(mesh, args.cpu_sample)
+    pool.close()
     line = {
         "metric": METRIC, "value": job_throughput(world, mesh.n_elem, ms_step), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -405,14 +452,15 @@ def main():
         "breakdown": {**br, "element_pass_elements_per_s": mesh.n_elem / br["element_pass_s"],
                       "cg_time_to_rtol_s": br["cg_s"], "cg_iterations": cg_iters, "cg_outer": last_rep["outer"],
                       "cg_rel_residual": last_rep["rel_residual"], "cg_converged": last_rep["converged"],
-                      "cg_ms_per_iteration": 1e3 * br["cg_s"] / max(1, cg_iters),
-                      "fp64_plain_cg_ms_per_iteration": fp64_ms_it,
-                      "mixed_vs_fp64_ms_per_iteration": fp64_ms_it / (1e3 * br["cg_s"] / max(1, cg_iters))},
+                      "cg_ms_per_iteration": 1e3 * br["cg_s"] / max(1, cg_iters)},
+        "fp64_arm": fp64_arm,
+        "complex_path_element_pass": complex_rate,
         "roofline": roof,
         "roofline_secondary": roof2,
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{nsamp} elements of {mesh.name} ({dt:.1f} s): element formation, condensation, "
-                                   f"recovery and eta_K; CG not in the sample"},
+                         "sample": f"{nsamp} elements of {mesh.name} ({dt:.1f} s wall), {args.cpu_sample} per process "
+                                   f"on {cores} spawned processes with one BLAS thread each: element formation, "
+                                   f"condensation, recovery and eta_K; CG not in the sample"},
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(tim["kernel_launches"]),
@@ -427,6 +475,87 @@ def main():
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def fp64_step(d, mesh, x_mixed, args):
+    """One whole step in FP64 throughout, the paper's solver (plain FP64 CG, x0 = 0, no preconditioner).
+
+    Timed end to end like e2e (pinned host inputs in, solution and eta out),
+    with CUDA events around each phase; value = elements / device time of the
+    step without the copies.  Also the relative L2 difference of its trace
+    solution from the timed (mixed-precision) step's.
+    """
+    import torch
+    corners = torch.from_numpy(np.ascontiguousarray(mesh.vert[mesh.elem].reshape(-1))).pin_memory()
+    eps_h = torch.from_numpy(np.ascontiguousarray(mesh.eps)).pin_memory()
+    mu_h = torch.from_numpy(np.ascontiguousarray(mesh.mu)).pin_memory()
+    x_h = torch.empty(d.n, dtype=torch.complex128).pin_memory()
+    eta_h = torch.empty(d.n_elem, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    ev[0].record(stream)
+    d.update_elements(corners, eps_h, mu_h)
+    ev[1].record(stream)
+    d.element_batch()
+    ev[2].record(stream)
+    d.assemble()
+    ev[3].record(stream)
+    x64, rep = d.cg_solve(mode=CG_MODES["fp64"], rtol=args.rtol, max_iter=args.max_iter,
+                          raise_on_nonconvergence=False)
+    ev[4].record(stream)
+    _, eta64, _ = d.estimate(x64)
+    ev[5].record(stream)
+    x_h.copy_(x64, non_blocking=True)
+    eta_h.copy_(eta64, non_blocking=True)
+    ev[6].record(stream)
+    torch.cuda.synchronize()
+    dev_ms = ev[1].elapsed_time(ev[5])
+    e2e_ms = ev[0].elapsed_time(ev[6])
+    diff = float(torch.linalg.vector_norm(x_mixed - x64) / torch.linalg.vector_norm(x64))
+    return {"cg": "fp64 (unpreconditioned, x0 = 0: the paper's solver)", "quadrature": "fp64",
+            "value": mesh.n_elem / (dev_ms / 1e3), "unit": UNIT, "ms_per_step": dev_ms,
+            "element_pass_s": ev[1].elapsed_time(ev[2]) / 1e3, "assemble_s": ev[2].elapsed_time(ev[3]) / 1e3,
+            "cg_time_to_rtol_s": ev[3].elapsed_time(ev[4]) / 1e3, "estimate_s": ev[4].elapsed_time(ev[5]) / 1e3,
+            "cg_iterations": rep["iterations"], "cg_rel_residual": rep["rel_residual"],
+            "cg_converged": rep["converged"],
+            "cg_ms_per_iteration": ev[3].elapsed_time(ev[4]) / max(1, rep["iterations"]),
+            "e2e": {"value": mesh.n_elem / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(corners.numel() * 8 + eps_h.numel() * 16 + mu_h.numel() * 16),
+                    "d2h_bytes_per_step": int(x_h.numel() * 16 + eta_h.numel() * 8)},
+            "solution_rel_l2_difference_vs_timed_step": diff,
+            "note": "one step after the timed region; both arms stop at the same FP64 relative residual"}
+
+
+def complex_path_rate(mesh, args):
+    """Element pass with every element on the complex path (real path off), on a 4-cell slab of the same guide.
+
+    The slab's elements have the shape, size, materials and frequency of the
+    full guide's, so its per-element rate is the full guide's complex-path rate.
+    """
+    import torch
+    from paper_2609_03155_b300 import dpg, inputs
+    p = int(mesh.p[0])
+    nx, ny, nz = mesh.grid if getattr(mesh, "grid", None) else (32, 16, 64)
+    slab = inputs.waveguide(0.08636, 0.04318, 0.300 * 4 / nz, nx, ny, 4, 2.45e9, p, name="waveguide3d_slab")
+    d = dpg.DPG(slab)
+    d.set_real_path(False)
+    d.element_batch()
+    torch.cuda.synchronize()
+    d.timing_enable(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.element_batch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tim = d.timing_get()
+    d.destroy()
+    fpe = flops_factor_per_element(p)
+    return {"elements": int(slab.n_elem), "workload": f"{nx}x{ny}x4 slab of the same guide, real path off",
+            "elements_per_s": slab.n_elem / (ms / 1e3), "element_pass_s": ms / 1e3,
+            "factor_tflops": fpe * tim["factor_elements"] / max(1e-9, tim["factor_ms"] / 1e3) / 1e12}
 
 
 def fp64_comparison(d, x, args):

@@ -291,6 +291,16 @@ int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle
                  double* dP_deps_re, double* dP_deps_im, int32_t cg_mode, double cg_rtol, int32_t max_iter,
                  dpg_stream s);
 
+/* Bound of the device-side waits of the CG kernel (its grid barriers): a
+ * wait that has not seen every block arrive after wait_ns nanoseconds of the
+ * GPU's global timer gives up, every block leaves the kernel, and dpg_cg_solve
+ * returns DPG_ERR_TIMEOUT with the context still usable.  Default 5 s.
+ * hold != 0 is a test hook of that failure path: no barrier releases, so the
+ * next solve's first wait runs out on purpose (no fault, no trap).  The paper
+ * has no counterpart; this is failure detection of this library.
+ * Errors: DPG_ERR_ARG (wait_ns <= 0). */
+int dpg_set_wait_limit(dpg_handle* h, int64_t wait_ns, int32_t hold);
+
 /* The element pass runs as a fixed launch plan: per trial degree and
  * arithmetic class (real path / complex), chunks of at most that degree's
  * chunk size.  The plan (device element lists, Robin face sub-batches) is

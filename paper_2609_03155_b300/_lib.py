@@ -94,6 +94,7 @@ def lib():
     L.dpg_element_layout.argtypes = [vp, vp, vp, vp]
     L.dpg_tc_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, i32]
     L.dpg_set_graph.argtypes = [vp, i32]
+    L.dpg_set_wait_limit.argtypes = [vp, i64, i32]
     L.dpg_power.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_autotune.argtypes = [vp, dbl, vp, vp, vp]
     L.dpg_group_info.argtypes = [vp, vp, vp, vp, vp]
@@ -115,6 +116,7 @@ def lib():
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
                  "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps",
                  "dpg_set_real_path", "dpg_cg_bytes_per_iteration", "dpg_element_layout", "dpg_tc_gemm", "dpg_set_graph", "dpg_autotune", "dpg_power",
+                 "dpg_set_wait_limit",
                  "dpg_group_info"):
         getattr(L, name).restype = C.c_int
     _lib = L

@@ -76,12 +76,15 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
     return DPG_ERR_ARG;
   }
   cudaStream_t s = S_(st);
+  h->have_elements = false;
+  h->have_system = false;
+  // per-element pivot flags and the tensor-core timeout flag start clear on
+  // every pass, so one failed pass does not poison the next
+  DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * (h->ne + 1), s));
   // the launch plan of every order group (lossless elements in real
   // arithmetic, the others in complex arithmetic), replayed as a CUDA graph
   int rc = element_pass(h, s);
   if (rc) return rc;
-  h->have_elements = true;
-  h->have_system = false;
   // pivot check
   std::vector<int> status(h->ne);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(status.data(), h->d_status, sizeof(int) * h->ne, cudaMemcpyDeviceToHost, s));
@@ -112,6 +115,8 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
       return DPG_ERR_TIMEOUT;
     }
   }
+  // only a pass whose every pivot was positive feeds assembly and estimation
+  h->have_elements = true;
   return DPG_OK;
 }
 
@@ -436,6 +441,13 @@ extern "C" int dpg_set_real_path(dpg_handle* h, int32_t enable) {
   if (!h) return DPG_ERR_ARG;
   if (h->allow_real != (enable != 0)) h->plan_valid = false;
   h->allow_real = enable != 0;
+  return DPG_OK;
+}
+
+extern "C" int dpg_set_wait_limit(dpg_handle* h, int64_t wait_ns, int32_t hold) {
+  if (!h || wait_ns <= 0) return DPG_ERR_ARG;
+  h->wait_ns = wait_ns;
+  h->wait_hold = hold != 0;
   return DPG_OK;
 }
 

@@ -485,7 +485,9 @@ int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_
   dpg_cg_report rep{};
   rc = cg_solve(h, cg_mode, cg_rtol, 0.0, max_iter, 1e-4, h->d_lam, h->d_rhs_adj, &rep, s);
   if (rc) return rc;
-  // gradient pass: re-form K, factor G only, evaluate the derivative terms
+  // gradient pass: re-form K, factor G only, evaluate the derivative terms;
+  // the pivot flags start clear so a failed factorisation here is reported
+  DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * ne, s));
   Workspace& wsp = h->ws;
   for (int gi = 0; gi < (int)h->grp.size(); ++gi) {
     const Group& G = h->grp[gi];
@@ -506,6 +508,14 @@ int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_
       DPG_CUDA_TRY(h, cudaGetLastError());
     }
   }
+  std::vector<int> status(ne);
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(status.data(), h->d_status, sizeof(int) * ne, cudaMemcpyDeviceToHost, s));
+  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  for (size_t e = 0; e < ne; ++e)
+    if (status[e]) {
+      h->err = "non-positive pivot of G_K in the gradient pass, element " + std::to_string(e);
+      return DPG_ERR_NOT_HPD;
+    }
   return DPG_OK;
 }
 

@@ -219,6 +219,8 @@ struct dpg_handle {
   double2 *d_r = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_zv = nullptr, *d_d64 = nullptr;
   float2 *d_r32 = nullptr, *d_p32 = nullptr, *d_Ap32 = nullptr, *d_x32 = nullptr, *d_z32 = nullptr;
   void* d_cgstate = nullptr;      // CG state of the persistent solver (solve.cu)
+  int64_t wait_ns = 5000000000ll; // bound of every grid-barrier wait of the CG kernel
+  bool wait_hold = false;         // test hook: CG barriers never release
   double* d_red = nullptr;      // reduction scratch
   dpg::Workspace ws;
 };

@@ -18,8 +18,9 @@
 // K = 8 each) and commits them to an mbarrier, and the CTA waits on it before
 // the next step overwrites the tiles.  The accumulator lives in tensor memory
 // (128 lanes x 128 FP32 columns); the epilogue reads it with tcgen05.ld and
-// writes FP64.  Every wait is bounded: on a timeout the CTA records an error,
-// waits once more (bounded) for its MMAs, frees its tensor memory and returns.
+// writes FP64.  Every wait is bounded in time: on a timeout the CTA records an
+// error, waits once more (bounded) for its MMAs, frees its tensor memory if
+// they completed (else leaves it allocated) and returns.
 #include <cstdint>
 
 #include "dpg_internal.h"
@@ -33,7 +34,7 @@ constexpr int TILE_BYTES = TC_M * TC_K * 4;       // one FP32 operand tile (16 K
 constexpr int LBO = (TC_M / 8) * 128;             // K-adjacent core matrices (2048 B)
 constexpr int SBO = 128;                          // M/N-adjacent core matrices
 constexpr uint32_t TMEM_COLS = 256;               // allocation (N = 128 used)
-constexpr long long WAIT_LIMIT = 1ll << 26;       // mbarrier polls before giving up
+constexpr unsigned long long WAIT_NS = 100000000ull;  // an mbarrier wait gives up after 100 ms
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -72,9 +73,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-// Bounded wait for the mbarrier phase; false on timeout.
+__device__ __forceinline__ unsigned long long tc_global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the mbarrier phase, bounded in time (WAIT_NS on the global
+// nanosecond timer, whatever each try_wait's own suspension); false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+  const unsigned long long t0 = tc_global_ns();
+  while (true) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -83,8 +92,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "=r"(done)
         : "r"(mbar), "r"(parity));
     if (done) return true;
+    if (tc_global_ns() - t0 > WAIT_NS) return false;
   }
-  return false;
 }
 
 // Stage rows [r0, r0 + 128) x K [k0, k0 + 32) of X^T (X: Kd x ncol row-major
@@ -179,9 +188,13 @@ __global__ void __launch_bounds__(128) k_gemm_tn_tc(int Ma, int Nb, int Kd, cons
     ok = __syncthreads_and(mbar_wait(mbar_a, phase) ? 1 : 0) != 0;
     phase ^= 1u;
   }
+  bool drained = true;
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(err, 1);
-    mbar_wait(mbar_a, phase ^ 1u);  // once more (bounded) for the MMAs in flight
+    // once more (bounded) for the MMAs in flight; if they still have not
+    // completed, the tensor memory they write is left allocated rather than
+    // freed under them (the host reports DPG_ERR_TIMEOUT either way)
+    drained = __syncthreads_and(mbar_wait(mbar_a, phase ^ 1u) ? 1 : 0) != 0;
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
@@ -207,7 +220,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn_tc(int Ma, int Nb, int Kd, cons
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 0 && drained) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }

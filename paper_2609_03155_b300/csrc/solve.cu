@@ -119,6 +119,9 @@ struct CgState {          // device-resident
   int iters;              // out
   double rr, rz;          // out
   unsigned int bar[2];    // grid barrier counter / generation
+  unsigned long long wait_ns;  // in: a barrier wait gives up after this long
+  int hold;               // in: test hook, no barrier ever releases (every wait runs out)
+  int pad_;
 };
 
 constexpr int CG_THREADS = 256;
@@ -129,26 +132,35 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Bounded grid-wide barrier for a cooperative launch.  Returns false when a
-// wait gave up (state->status set); callers then leave the kernel.
+// wait gave up (state->status set); callers then leave the kernel.  The wait
+// is bounded in time (st->wait_ns on the global nanosecond timer), not in
+// polls.  Every block arrives at every barrier once, so after a timeout the
+// last arriving block still resets the counter and all blocks leave.
 __device__ __forceinline__ bool grid_barrier(CgState* st, unsigned int& gen) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int target = gen + 1;
     __threadfence();
     const unsigned int arrived = atomicAdd(&st->bar[0], 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == gridDim.x && !st->hold) {
       st->bar[0] = 0u;
       __threadfence();
       atomicExch(&st->bar[1], target);
     } else {
-      unsigned long long spins = 0;
+      const unsigned long long t0 = global_ns(), limit = st->wait_ns;
       while (*((volatile unsigned int*)&st->bar[1]) != target) {
-        if (++spins > (1ull << 25)) {  // ~ seconds: something is broken, give up
+        if (global_ns() - t0 > limit) {  // something is broken: give up
           atomicExch(&st->status, 1);
           break;
         }
-        __nanosleep(40);
+        __nanosleep(64);
       }
     }
     __threadfence();
@@ -581,6 +593,8 @@ static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap,
   CgState host{};
   host.tol2 = tol2;
   host.max_iter = max_iter;
+  host.wait_ns = (unsigned long long)h->wait_ns;
+  host.hold = h->wait_hold ? 1 : 0;
   CgState* st = static_cast<CgState*>(h->d_cgstate);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(st, &host, sizeof(CgState), cudaMemcpyHostToDevice, s));
   SysView S = sys_view(h);

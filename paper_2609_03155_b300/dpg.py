@@ -137,6 +137,9 @@ class DPG:
     def set_graph(self, enable=True):
         check(_lib.lib().dpg_set_graph(self.h, int(enable)), self.h)
 
+    def set_wait_limit(self, wait_ns=5_000_000_000, hold=False):
+        check(_lib.lib().dpg_set_wait_limit(self.h, int(wait_ns), int(hold)), self.h)
+
     def group_info(self):
         """[(p, n_elem, chunk)] per order group."""
         ng = C.c_int32()

@@ -97,6 +97,8 @@ enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
 enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8 };
 enum { DPG_FLAG_ADJOINT = 1 };
+/* Arithmetic of the element factorisation's trailing updates (dpg_set_factor_arith). */
+enum { DPG_FACTOR_FP64 = 0, DPG_FACTOR_TC_SPLIT = 1 };
 
 /* Robin group (Sec. 2.2, Eq. robin_boundary; Sec. 4.1 port / outlet):
  * n x H + Z^{-1} n x (E x n) = g.  port = 0: g = 0; port = 1: g is the TE_mn
@@ -211,13 +213,26 @@ int dpg_cg_solve(dpg_handle* h, int32_t mode, double rtol, double atol, int32_t 
  * xhat (device, n complex) compute per element u_K = M1^{-1}(M4 l - M2 uhat_K)
  * (u: device, element e's n_u(e) complex values at the offset u_off[e] of
  * dpg_element_layout, n_elem x n_u for one degree; element-local order above;
- * may be NULL)
+ * may be NULL; from the stored condensation data)
  * and eta_K = ||Psi_K||_V with Psi_K = G^{-1}(l - B u - B-hat uhat)
- * (eta: device, n_elem doubles, may be NULL), evaluated as the minimum of the
- * element's residual quadratic, eta_K^2 = c_K - 2 Re(uhat^H s_K) + uhat^H S_K uhat.
- * eta_global: host, sqrt(sum eta_K^2) (may be NULL; synchronises if given). */
+ * (eta: device, n_elem doubles, may be NULL), by its definition: a second
+ * element pass forms G_K, B_K, B-hat_K, l_K again, forms r_K = l - B u - B-hat uhat
+ * and factors G_K = L L^H with r_K as one more column, so that
+ * eta_K^2 = ||L^{-1} r_K||^2 is accumulated as a sum of squares (rounding can
+ * only make it negative when eta_K ~ 0; such values are set to 0 and counted,
+ * see dpg_estimate_clamped).  With eta and eta_global both NULL only u is
+ * computed (no element pass).  Uses the handle's chunk workspace.
+ * eta_global: host, sqrt(sum eta_K^2) (may be NULL; synchronises if given).
+ * Errors: DPG_ERR_STATE (no element pass), DPG_ERR_ARG, DPG_ERR_NOMEM,
+ * DPG_ERR_TIMEOUT (a tensor-core wait of the pass gave up; reported with
+ * eta_global). */
 int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
                  double* eta_global, dpg_stream s);
+
+/* Number of elements whose eta_K^2 came out negative (through rounding, when
+ * eta_K ~ 0) in the last dpg_estimate or dpg_estimate_noalloc and was set to
+ * 0.  count: host.  Synchronises the device. */
+int dpg_estimate_clamped(dpg_handle* h, int32_t* count);
 
 /* Allocation-free variant of dpg_estimate, for callers that cannot allocate
  * device memory during the call (their memory is committed to a pool of
@@ -290,6 +305,33 @@ int dpg_timing_get(dpg_handle* h, dpg_timing* out);
 int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle_mask, double* P,
                  double* dP_deps_re, double* dP_deps_im, int32_t cg_mode, double cg_rtol, int32_t max_iter,
                  dpg_stream s);
+
+/* Arithmetic of the element factorisation (the blocked partial Cholesky of
+ * the augmented element matrix that condenses to S_K, Sec. 2.3, Eq.
+ * linear_system).  The diagonal blocks and the panel triangular solves are
+ * FP64 in both modes.  DPG_FACTOR_FP64: the trailing updates too, on the FP64
+ * pipe.  DPG_FACTOR_TC_SPLIT (default): the trailing updates on the tensor
+ * cores at FP64 accuracy, through an error-free splitting of each panel row
+ * (scaled by a power of two 2^e > its largest entry) into seven 8-bit integer
+ * digits, FP16 MMAs whose FP32 accumulators hold exact integers, and one
+ * rounding to FP64 per update (the error of an update is about
+ * 2^-57 2^e_i 2^e_j times the panel width, below FP64's own bound).  Changing the mode reallocates
+ * the chunk workspace and invalidates the element stores.
+ * Errors: DPG_ERR_ARG (unknown mode), DPG_ERR_NOMEM. */
+int dpg_set_factor_arith(dpg_handle* h, int32_t arith);
+
+/* Check hook of the two factorisation kernels: run the element factorisation
+ * of dpg_element_batch on one augmented matrix given on the host.  A (host,
+ * read): N x N column-major, lower triangle used, real (cplx = 0: N^2
+ * doubles) or complex (cplx = 1: N^2 interleaved re, im pairs).  Pivots
+ * [0, nv) positive, then the trailing block is negated, pivots [nv, npiv)
+ * positive; only rows and columns [0, nact) take part.  out (host, written,
+ * same layout): the factored matrix.  not_hpd (host, may be NULL): 1 if a
+ * pivot was not positive.  arith: DPG_FACTOR_*.  Synchronous, uses the
+ * current device.  Errors: DPG_ERR_ARG, DPG_ERR_NOMEM, DPG_ERR_TIMEOUT,
+ * DPG_ERR_CUDA, DPG_ERR_UNSUPPORTED (N > 3315). */
+int dpg_factor_check(int32_t arith, int32_t cplx, int32_t N, int32_t nact, int32_t nv, int32_t npiv, const double* A,
+                     double* out, int32_t* not_hpd);
 
 /* Bound of the device-side waits of the CG kernel (its grid barriers): a
  * wait that has not seen every block arrive after wait_ns nanoseconds of the

@@ -21,6 +21,7 @@ DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI, DPG_CG_BLOCK_JACOBI = 0, 1, 2, 4
 DPG_PREC_FP64, DPG_PREC_TF32, DPG_PREC_3XTF32 = 0, 1, 2
 DPG_CG_X0 = 8
 DPG_FLAG_ADJOINT = 1
+DPG_FACTOR_FP64, DPG_FACTOR_TC_SPLIT = 0, 1
 
 
 class dpg_complex(C.Structure):
@@ -95,6 +96,9 @@ def lib():
     L.dpg_tc_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, i32]
     L.dpg_set_graph.argtypes = [vp, i32]
     L.dpg_set_wait_limit.argtypes = [vp, i64, i32]
+    L.dpg_set_factor_arith.argtypes = [vp, i32]
+    L.dpg_estimate_clamped.argtypes = [vp, C.POINTER(i32)]
+    L.dpg_factor_check.argtypes = [i32, i32, i32, i32, i32, i32, vp, vp, C.POINTER(i32)]
     L.dpg_power.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_autotune.argtypes = [vp, dbl, vp, vp, vp]
     L.dpg_group_info.argtypes = [vp, vp, vp, vp, vp]
@@ -116,7 +120,7 @@ def lib():
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
                  "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps",
                  "dpg_set_real_path", "dpg_cg_bytes_per_iteration", "dpg_element_layout", "dpg_tc_gemm", "dpg_set_graph", "dpg_autotune", "dpg_power",
-                 "dpg_set_wait_limit",
+                 "dpg_set_wait_limit", "dpg_set_factor_arith", "dpg_factor_check", "dpg_estimate_clamped",
                  "dpg_group_info"):
         getattr(L, name).restype = C.c_int
     _lib = L

@@ -38,7 +38,7 @@ static void free_all(dpg_handle* h) {
                   h->ws.PhiL, h->ws.MC,   h->ws.ids, h->ws.FV,   h->ws.FR,   h->ws.rent,
                   h->d_dinv,  h->d_dinv32, h->d_L1, h->d_u, h->d_zg, h->d_gc, h->d_lam, h->d_rhs_adj,
                   h->d_Pk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_binv_ptr, h->d_binv, h->d_binv32,
-                  h->d_zv, h->d_z32, h->d_d64};
+                  h->d_zv, h->d_z32, h->d_d64, h->ws.Q, h->d_est_neg};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -107,11 +107,11 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
       h->err = "non-positive pivot in element " + std::to_string(e);
       return DPG_ERR_NOT_HPD;
     }
-  if (h->prec != DPG_PREC_FP64) {
+  {
     int terr = 0;
     DPG_CUDA_TRY(h, cudaMemcpy(&terr, h->d_status + h->ne, sizeof(int), cudaMemcpyDeviceToHost));
     if (terr) {
-      h->err = "a tensor-core contraction gave up waiting for its MMAs";
+      h->err = "a tensor-core kernel of the element pass gave up waiting for its MMAs";
       return DPG_ERR_TIMEOUT;
     }
   }
@@ -144,6 +144,14 @@ extern "C" int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex*
   Range range_("dpg_estimate");
   if (!h) return DPG_ERR_ARG;
   return estimate(h, reinterpret_cast<const double2*>(xhat), reinterpret_cast<double2*>(u), eta, eta_global, S_(st));
+}
+
+extern "C" int dpg_estimate_clamped(dpg_handle* h, int32_t* count) {
+  if (!h || !count) return DPG_ERR_ARG;
+  int c = 0;
+  int rc = estimate_negatives(h, &c);
+  *count = c;
+  return rc;
 }
 
 extern "C" int dpg_estimate_noalloc(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double* eta,
@@ -442,6 +450,15 @@ extern "C" int dpg_set_real_path(dpg_handle* h, int32_t enable) {
   if (h->allow_real != (enable != 0)) h->plan_valid = false;
   h->allow_real = enable != 0;
   return DPG_OK;
+}
+
+extern "C" int dpg_set_factor_arith(dpg_handle* h, int32_t arith) {
+  if (!h || (arith != DPG_FACTOR_FP64 && arith != DPG_FACTOR_TC_SPLIT)) return DPG_ERR_ARG;
+  if (arith == h->factor_arith) return DPG_OK;
+  h->factor_arith = arith;
+  h->have_elements = false;
+  h->have_system = false;
+  return alloc_workspace(h);  // the digit scratch; invalidates the launch plan and its graph
 }
 
 extern "C" int dpg_set_wait_limit(dpg_handle* h, int64_t wait_ns, int32_t hold) {

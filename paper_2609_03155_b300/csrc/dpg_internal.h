@@ -64,6 +64,7 @@ struct Workspace {
   double* FV = nullptr;      // rcap x 3nqf x (2 n_f + nt + 2)
   double* FR = nullptr;      // rcap x (2 n_f^2 + n_f nt + 2 n_f)
   int* rent = nullptr;       // rcap x 4 (elem slot, face, grp, elem id)
+  uint8_t* Q = nullptr;      // cap x digit scratch of the tensor-core factorisation (factor_tc.cu)
 };
 
 // Per-element offsets into the pooled element stores (in entries of each
@@ -97,7 +98,9 @@ struct ChunkPlan {
   bool restricted = false;     // some element needs the trace restriction
   int64_t ids_off = 0;         // into d_plan_ids
   int count = 0;
-  std::vector<int4> robin;     // sub-batches: (entries offset, entries, element list offset, elements) in d_plan_rent
+  std::vector<int4> robin;     // sub-batches: (entries offset, entries, element list offset, elements) in the rent list
+  const int* d_ids = nullptr;  // the plan's device element-id list (ids of this chunk at d_ids + ids_off)
+  const int* d_rent = nullptr; // the plan's device Robin entry list
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the factorisation (timing)
 };
 
@@ -128,6 +131,7 @@ struct dpg_handle {
   dpg::Sizes szmax{};             // largest sizes over the groups
   int ne = 0;
   int prec = DPG_PREC_FP64;       // quadrature contraction precision
+  int factor_arith = DPG_FACTOR_TC_SPLIT;  // arithmetic of the element factorisation's trailing updates
   double omega = 0, alpha = 1;
   // host copies used by setup / dumps
   std::vector<dpg_robin_group> robin;
@@ -198,6 +202,11 @@ struct dpg_handle {
   bool plan_valid = false;
   int* d_plan_ids = nullptr;
   int* d_plan_rent = nullptr;
+  // launch plan of the estimator's recompute pass (every element on the complex path)
+  std::vector<dpg::ChunkPlan> est_plan;
+  int* d_est_ids = nullptr;
+  int* d_est_rent = nullptr;
+  int* d_est_neg = nullptr;       // count of clamped negative eta_K^2 (one int)
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false, graph_timing = false;
@@ -241,8 +250,15 @@ int element_pass(dpg_handle* h, cudaStream_t s);
 int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem, cudaStream_t s);
 int compute_reference_matrices(dpg_handle* h, int g, cudaStream_t s);
 int factor_gram_only(dpg_handle* h, int g, int count, cudaStream_t s);
+int estimate_pass(dpg_handle* h, const double2* xhat, double2* u, double* eta2, cudaStream_t s);
+void recover_u(dpg_handle* h, const double2* xhat, double2* u, cudaStream_t s);
 // power.cu
 int power(dpg_handle* h, const double2* xhat, double* q, double* flux_host, cudaStream_t s);
+// factor_tc.cu
+int factor_tc_init();
+size_t factor_tc_scratch_bytes(int N, bool cplx);
+int factor_tc_launch(bool cplx, int count, int N, int nact, int nv, int npiv, const int* ids, void* K, int* status,
+                     int* tc_err, uint8_t* qscr, cudaStream_t s);
 // quad_tc.cu
 int tc_init();
 int gemm_tn_tc(int split, int Ma, int Nb, int Kd, const double* A, int lda, long long sA, const double* B, int ldb,
@@ -257,6 +273,7 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
 int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
              cudaStream_t s);
 int64_t cg_bytes_per_iteration(const dpg_handle* h, int mode);
+int estimate_negatives(dpg_handle* h, int* count);
 int estimate_noalloc(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
                      cudaStream_t s);
 }  // namespace dpg

@@ -1013,11 +1013,11 @@ void set_default_caps(dpg_handle* h, int chunk) {
 // One workspace sized for the largest group chunk (frees the previous one).
 int alloc_workspace(dpg_handle* h) {
   Workspace& w = h->ws;
-  void* old[] = {w.K, w.V, w.Cu, w.PhiL, w.MC, w.ids, w.FV, w.FR, w.rent, w.F, w.KW};
+  void* old[] = {w.K, w.V, w.Cu, w.PhiL, w.MC, w.ids, w.FV, w.FR, w.rent, w.F, w.KW, w.Q};
   for (void* b : old)
     if (b) cudaFree(b);
   w = Workspace{};
-  size_t bK = 0, bV = 0, bP = 0, bMC = 0, bFV = 0, bFR = 0, bF = 0, bKW = 0;
+  size_t bK = 0, bV = 0, bP = 0, bMC = 0, bFV = 0, bFR = 0, bF = 0, bKW = 0, bQ = 16;
   int capmax = 1;
   for (Group& G : h->grp) {
     const Sizes& S = G.sz;
@@ -1030,6 +1030,7 @@ int alloc_workspace(dpg_handle* h) {
     bMC = std::max(bMC, sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) * cap);
     bF = std::max(bF, sizeof(double) * (size_t)S.nq * S.n_f * cap);
     bKW = std::max(bKW, sizeof(double) * 6 * (size_t)S.nq * cap);
+    if (h->factor_arith == DPG_FACTOR_TC_SPLIT) bQ = std::max(bQ, factor_tc_scratch_bytes(S.N, true) * cap);
   }
   w.rcap = std::max(6, std::min(capmax * 2, std::max(6, (int)h->robin_entries.size())));
   for (Group& G : h->grp) {
@@ -1039,10 +1040,10 @@ int alloc_workspace(dpg_handle* h) {
     bFR = std::max(bFR, sizeof(double) * (size_t)S.n_f * Wf * w.rcap);
   }
   size_t bytes[] = {bK, bV, bV, bP, bMC, sizeof(int) * (size_t)capmax, bFV, bFR, sizeof(int) * 4 * (size_t)w.rcap,
-                    bF, bKW};
+                    bF, bKW, bQ};
   void** ptrs[] = {(void**)&w.K, (void**)&w.V, (void**)&w.Cu, (void**)&w.PhiL, (void**)&w.MC, (void**)&w.ids,
-                   (void**)&w.FV, (void**)&w.FR, (void**)&w.rent, (void**)&w.F, (void**)&w.KW};
-  for (int k = 0; k < 11; ++k) {
+                   (void**)&w.FV, (void**)&w.FR, (void**)&w.rent, (void**)&w.F, (void**)&w.KW, (void**)&w.Q};
+  for (int k = 0; k < 12; ++k) {
     if (cudaMalloc(ptrs[k], bytes[k]) != cudaSuccess) {
       cudaGetLastError();
       h->err = "workspace allocation of " + std::to_string(bytes[k]) + " bytes failed";
@@ -1061,7 +1062,7 @@ int init_kernel_attributes(dpg_handle* h) {
   const int s128 = (int)factor_smem<double2>();
   DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64));
   DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128));
-  if (tc_init() != DPG_OK) {
+  if (tc_init() != DPG_OK || factor_tc_init() != DPG_OK) {
     h->err = "tensor-core kernel attribute setup failed";
     return DPG_ERR_CUDA;
   }
@@ -1145,7 +1146,7 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
   const Sizes& S = G.sz;
   if (count > G.cap) return DPG_ERR_ARG;
   // element ids of the chunk: the plan's device list, or a copy of the host list
-  const int* ids = cp ? h->d_plan_ids + cp->ids_off : w.ids;
+  const int* ids = cp ? cp->d_ids + cp->ids_off : w.ids;
   if (!cp) DPG_CUDA_TRY(h, cudaMemcpyAsync(w.ids, ids_host, sizeof(int) * count, cudaMemcpyHostToDevice, s));
   const size_t nq3 = 3 * (size_t)S.nq;
   const bool fp64q = h->prec == DPG_PREC_FP64;
@@ -1214,7 +1215,7 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
   if (!real) {
     if (cp) {
       for (const int4& rb : cp->robin) {
-        int rc = robin_launch(h, g, h->d_plan_rent + rb.x, rb.y, h->d_plan_rent + rb.z, rb.w, s);
+        int rc = robin_launch(h, g, cp->d_rent + rb.x, rb.y, cp->d_rent + rb.z, rb.w, s);
         if (rc) return rc;
       }
     } else {
@@ -1231,10 +1232,17 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
     if (timed) DPG_CUDA_TRY(h, cudaStreamIsCapturing(s, &cap));
     const unsigned int rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (timed) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(cp->ev0, s, rec_flags));
-    if (real)
+    if (h->factor_arith == DPG_FACTOR_TC_SPLIT) {
+      if (factor_tc_launch(!real, count, S.N, S.N, S.n_v, S.n_v + S.n_u, ids, real ? (void*)Kr : (void*)w.K,
+                           h->d_status, h->d_status + h->ne, w.Q, s) != DPG_OK) {
+        h->err = "tensor-core factorisation launch failed";
+        return DPG_ERR_CUDA;
+      }
+    } else if (real) {
       k_factor<double><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, Kr, h->d_status);
-    else
+    } else {
       k_factor<double2><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, w.K, h->d_status);
+    }
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
     if (timed) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(cp->ev1, s, rec_flags));
@@ -1261,31 +1269,35 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
 }
 
 // ------------------------------------------------------ pass plan / graph --
-void free_plan(dpg_handle* h) {
-  for (ChunkPlan& c : h->plan) {
+static void free_chunks(std::vector<ChunkPlan>& plan, int** d_ids, int** d_rent) {
+  for (ChunkPlan& c : plan) {
     if (c.ev0) cudaEventDestroy(c.ev0);
     if (c.ev1) cudaEventDestroy(c.ev1);
   }
-  h->plan.clear();
-  if (h->d_plan_ids) cudaFree(h->d_plan_ids);
-  if (h->d_plan_rent) cudaFree(h->d_plan_rent);
-  h->d_plan_ids = nullptr;
-  h->d_plan_rent = nullptr;
+  plan.clear();
+  if (*d_ids) cudaFree(*d_ids);
+  if (*d_rent) cudaFree(*d_rent);
+  *d_ids = nullptr;
+  *d_rent = nullptr;
+}
+
+void free_plan(dpg_handle* h) {
+  free_chunks(h->plan, &h->d_plan_ids, &h->d_plan_rent);
+  free_chunks(h->est_plan, &h->d_est_ids, &h->d_est_rent);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
   h->plan_valid = false;
   h->graph_valid = false;
 }
 
-// Chunks of every group (lossless elements on the real path first), their
-// device id lists and Robin sub-batches.  Synchronous (setup-time work).
-int build_plan(dpg_handle* h) {
-  free_plan(h);
+// Chunks of every group (with real: lossless elements on the real path
+// first), their device id lists and Robin sub-batches.  Synchronous.
+static int make_chunks(dpg_handle* h, bool real, std::vector<ChunkPlan>& plan, int** d_ids, int** d_rent) {
   std::vector<int> ids_all, rent_all;
   for (int g = 0; g < (int)h->grp.size(); ++g) {
     const Group& G = h->grp[g];
     const std::vector<int>* lists[2] = {&G.real_elems, &G.cplx_elems};
-    if (!h->allow_real) {
+    if (!real) {
       lists[0] = &G.elems;
       lists[1] = nullptr;
     }
@@ -1295,7 +1307,7 @@ int build_plan(dpg_handle* h) {
       for (size_t c0 = 0; c0 < L.size(); c0 += G.cap) {
         ChunkPlan cp;
         cp.g = g;
-        cp.real = h->allow_real && li == 0;
+        cp.real = real && li == 0;
         cp.count = (int)std::min<size_t>(G.cap, L.size() - c0);
         cp.ids_off = (int64_t)ids_all.size();
         ids_all.insert(ids_all.end(), L.begin() + c0, L.begin() + c0 + cp.count);
@@ -1316,17 +1328,31 @@ int build_plan(dpg_handle* h) {
         }
         DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev0));
         DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev1));
-        h->plan.push_back(std::move(cp));
+        plan.push_back(std::move(cp));
       }
     }
   }
-  DPG_CUDA_TRY(h, cudaMalloc(&h->d_plan_ids, sizeof(int) * std::max<size_t>(1, ids_all.size())));
-  DPG_CUDA_TRY(h, cudaMalloc(&h->d_plan_rent, sizeof(int) * std::max<size_t>(1, rent_all.size())));
+  DPG_CUDA_TRY(h, cudaMalloc(d_ids, sizeof(int) * std::max<size_t>(1, ids_all.size())));
+  DPG_CUDA_TRY(h, cudaMalloc(d_rent, sizeof(int) * std::max<size_t>(1, rent_all.size())));
   if (!ids_all.empty())
-    DPG_CUDA_TRY(h, cudaMemcpy(h->d_plan_ids, ids_all.data(), sizeof(int) * ids_all.size(), cudaMemcpyHostToDevice));
+    DPG_CUDA_TRY(h, cudaMemcpy(*d_ids, ids_all.data(), sizeof(int) * ids_all.size(), cudaMemcpyHostToDevice));
   if (!rent_all.empty())
-    DPG_CUDA_TRY(h, cudaMemcpy(h->d_plan_rent, rent_all.data(), sizeof(int) * rent_all.size(),
-                               cudaMemcpyHostToDevice));
+    DPG_CUDA_TRY(h, cudaMemcpy(*d_rent, rent_all.data(), sizeof(int) * rent_all.size(), cudaMemcpyHostToDevice));
+  for (ChunkPlan& cp : plan) {
+    cp.d_ids = *d_ids;
+    cp.d_rent = *d_rent;
+  }
+  return DPG_OK;
+}
+
+// The element pass's plan (real path as allowed) and the estimator's
+// recompute plan (every element complex), both built once per workspace.
+int build_plan(dpg_handle* h) {
+  free_plan(h);
+  int rc = make_chunks(h, h->allow_real, h->plan, &h->d_plan_ids, &h->d_plan_rent);
+  if (rc == DPG_OK) rc = make_chunks(h, false, h->est_plan, &h->d_est_ids, &h->d_est_rent);
+  if (rc == DPG_OK && !h->d_est_neg) DPG_CUDA_TRY(h, cudaMalloc(&h->d_est_neg, sizeof(int)));
+  if (rc) return rc;
   h->plan_valid = true;
   h->graph_valid = false;
   return DPG_OK;
@@ -1444,12 +1470,258 @@ int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem,
 // Cholesky of the G block alone for the current chunk (rows below untouched).
 int factor_gram_only(dpg_handle* h, int g, int count, cudaStream_t s) {
   const Sizes& S = h->grp[g].sz;
-  const size_t smem = factor_smem<double2>();
-  k_factor<double2><<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status);
+  if (h->factor_arith == DPG_FACTOR_TC_SPLIT) {
+    if (factor_tc_launch(true, count, S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status,
+                         h->d_status + h->ne, h->ws.Q, s) != DPG_OK) {
+      h->err = "tensor-core factorisation launch failed";
+      return DPG_ERR_CUDA;
+    }
+  } else {
+    const size_t smem = factor_smem<double2>();
+    k_factor<double2><<<count, 256, smem, s>>>(S.N, S.n_v, S.n_v, S.n_v, h->ws.ids, h->ws.K, h->d_status);
+  }
   h->launches += 1;
   DPG_CUDA_TRY(h, cudaGetLastError());
   return DPG_OK;
 }
+
+// ------------------------------------------------- recovery and estimator --
+// Local recovery u_K = M1^{-1}(M4 l - M2 uhat) (Sec. 2.3) from the stored
+// Z = M1^{-1} M2 and z = M1^{-1} M4 l of the element pass, and the residual
+// estimator eta_K = ||Psi_K||_V with Psi_K = G_K^{-1} r_K, r_K = l - B u - B-hat uhat,
+// by its definition: G_K, B_K, B-hat_K, l_K are formed again, r_K replaces the
+// first column after G in the augmented matrix, and the factorisation kernel
+// takes the n_v pivots of G; the entry below them is then
+// 0 - ||L^{-1} r_K||^2 = -eta_K^2, accumulated as a sum of squares (no
+// cancellation beyond the one inside r_K itself).
+
+__device__ __forceinline__ double2 trace_value(const int32_t* l2g, const double2* fix, const double2* x, size_t k) {
+  const int g = l2g[k];
+  if (g >= 0) return x[g];
+  if (g == -1) return fix[k];
+  return make_double2(0.0, 0.0);
+}
+
+__device__ __forceinline__ double est_wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// u = z - Z uhat_slots for the elements of one group (one CTA per element).
+__global__ void __launch_bounds__(256) k_recover_u(int nh, int nu, const int* __restrict__ elems,
+                                                   const ElemOff* __restrict__ off, const int32_t* __restrict__ l2g,
+                                                   const double2* __restrict__ xfix, const double2* __restrict__ xhat,
+                                                   const double2* __restrict__ Zst, const double2* __restrict__ zst,
+                                                   double2* u_out) {
+  extern __shared__ double2 su_sh[];
+  const int e = elems[blockIdx.x];
+  const ElemOff of = off[e];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) su_sh[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
+  __syncthreads();
+  const double2* Ze = Zst + of.Z;
+  for (int i = wid; i < nu; i += nw) {
+    double yr = 0.0, yi = 0.0;
+    for (int j = lane; j < nh; j += 32) {
+      const double2 v = Ze[(size_t)i * nh + j], x = su_sh[j];
+      yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
+      yi = fma(v.x, x.y, fma(v.y, x.x, yi));
+    }
+    yr = est_wsum(yr);
+    yi = est_wsum(yi);
+    if (lane == 0) {
+      const double2 zi = zst[of.u + i];
+      u_out[of.u + i] = make_double2(zi.x - yr, zi.y - yi);
+    }
+  }
+}
+
+// Per element of a chunk (K freshly formed, not factored): u, the element's
+// own trace coefficients uhat_K = R_K uhat_slots, r = l - B u - B-hat uhat_K
+// (B[i][j] = conj(K[n_v + j][i]), l_i = conj(K[N-1][i])); K[n_v][i] = conj(r_i),
+// K[n_v][n_v] = 0.
+__global__ void __launch_bounds__(256) k_est_residual(Sizes S, const int* __restrict__ ids,
+                                                      const ElemOff* __restrict__ off, const int* __restrict__ sig,
+                                                      const RSig* __restrict__ rsig, const int32_t* __restrict__ rint,
+                                                      const double* __restrict__ rdbl, const int32_t* __restrict__ l2g,
+                                                      const double2* __restrict__ xfix,
+                                                      const double2* __restrict__ xhat,
+                                                      const double2* __restrict__ Zst,
+                                                      const double2* __restrict__ zst, double2* K, double2* u_out) {
+  extern __shared__ double2 er_sh[];
+  const int slot = blockIdx.x, e = ids[slot];
+  const ElemOff of = off[e];
+  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h, m = nu + nh;
+  double2* w = er_sh;       // m: u, then uhat_K
+  double2* us = w + m;      // nh: uhat in the trace slots
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double2* A = K + (size_t)slot * N * N;
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) us[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
+  __syncthreads();
+  const double2* Ze = Zst + of.Z;
+  for (int i = wid; i < nu; i += nw) {
+    double yr = 0.0, yi = 0.0;
+    for (int j = lane; j < nh; j += 32) {
+      const double2 v = Ze[(size_t)i * nh + j], x = us[j];
+      yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
+      yi = fma(v.x, x.y, fma(v.y, x.x, yi));
+    }
+    yr = est_wsum(yr);
+    yi = est_wsum(yi);
+    if (lane == 0) {
+      const double2 zi = zst[of.u + i];
+      const double2 ui = make_double2(zi.x - yr, zi.y - yi);
+      w[i] = ui;
+      if (u_out) u_out[of.u + i] = ui;
+    }
+  }
+  const int sg = sig[e];
+  if (sg >= 0) {  // element trace coefficients from the slots: uhat_K = R uhat
+    const RSig R = rsig[sg];
+    const int32_t* rp = rint + R.rptr;
+    const int32_t* ri = rint + R.ridx;
+    const double* rw = rdbl + R.rw;
+    const int nt = nh / 2;
+    for (int t = threadIdx.x; t < nh; t += blockDim.x) {
+      const int tt = t < nt ? t : t - nt, base = t < nt ? 0 : nt;
+      double2 a = make_double2(0.0, 0.0);
+      for (int k = rp[tt]; k < rp[tt + 1]; ++k) {
+        const double2 x = us[base + ri[k]];
+        a.x = fma(rw[k], x.x, a.x);
+        a.y = fma(rw[k], x.y, a.y);
+      }
+      w[nu + t] = a;
+    }
+  } else {
+    for (int t = threadIdx.x; t < nh; t += blockDim.x) w[nu + t] = us[t];
+  }
+  __syncthreads();
+  for (int i = wid; i < nv; i += nw) {
+    const double2* col = A + (size_t)i * N + nv;
+    double rr = 0.0, ri2 = 0.0;
+    for (int j = lane; j < m; j += 32) {
+      const double2 b = col[j], x = w[j];  // B[i][j] = conj(b)
+      rr = fma(b.x, x.x, fma(b.y, x.y, rr));
+      ri2 = fma(b.x, x.y, fma(-b.y, x.x, ri2));
+    }
+    rr = est_wsum(rr);
+    ri2 = est_wsum(ri2);
+    if (lane == 0) {
+      const double2 lc = col[m];  // conj(l_i)
+      A[(size_t)nv + (size_t)i * N] = make_double2(lc.x - rr, -(-lc.y - ri2));  // conj(l_i - (B w)_i)
+    }
+  }
+  if (threadIdx.x == 0) A[(size_t)nv + (size_t)nv * N] = make_double2(0.0, 0.0);
+}
+
+// eta_K^2 = -K[n_v][n_v] after the n_v pivots of G (negative values, possible
+// only through rounding when eta_K ~ 0, are clamped to 0 and counted).
+__global__ void k_est_eta(int count, int N, int nv, const int* __restrict__ ids, const double2* __restrict__ K,
+                          double* eta2, int* nneg) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= count) return;
+  double v = -K[(size_t)slot * N * N + (size_t)nv + (size_t)nv * N].x;
+  if (v < 0.0) {
+    atomicAdd(nneg, 1);
+    v = 0.0;
+  }
+  eta2[ids[slot]] = v;
+}
+
+void recover_u(dpg_handle* h, const double2* xhat, double2* u, cudaStream_t s) {
+  for (const Group& G : h->grp) {
+    const Sizes& S = G.sz;
+    k_recover_u<<<(int)G.elems.size(), 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, G.d_elems, h->d_off,
+                                                                          h->d_l2g, h->d_xfix, xhat, h->d_Z, h->d_z, u);
+    h->launches += 1;
+  }
+}
+
+// The estimator's recompute pass over the est_plan chunks: eta_K^2 into eta2[e]
+// (and u when given).  Uses the chunk workspace only; allocates nothing.
+int estimate_pass(dpg_handle* h, const double2* xhat, double2* u, double* eta2, cudaStream_t s) {
+  if (!h->plan_valid) {
+    h->err = "the estimator's launch plan is built by dpg_element_batch";
+    return DPG_ERR_STATE;
+  }
+  DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_est_neg, 0, sizeof(int), s));
+  for (const ChunkPlan& cp : h->est_plan) {
+    const Group& G = h->grp[cp.g];
+    const Sizes& S = G.sz;
+    int rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, false, false, false, &cp);
+    if (rc) return rc;
+    const int* ids = cp.d_ids + cp.ids_off;
+    const size_t sh = sizeof(double2) * (size_t)(S.n_u + 2 * S.n_h);
+    k_est_residual<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_sig, h->d_rsig, h->d_rint, h->d_rdbl, h->d_l2g,
+                                             h->d_xfix, xhat, h->d_Z, h->d_z, h->ws.K, u);
+    if (h->factor_arith == DPG_FACTOR_TC_SPLIT) {
+      if (factor_tc_launch(true, cp.count, S.N, S.n_v + 1, S.n_v, S.n_v, ids, h->ws.K, h->d_status,
+                           h->d_status + h->ne, h->ws.Q, s) != DPG_OK) {
+        h->err = "tensor-core factorisation launch failed";
+        return DPG_ERR_CUDA;
+      }
+    } else {
+      k_factor<double2><<<cp.count, 256, factor_smem<double2>(), s>>>(S.N, S.n_v + 1, S.n_v, S.n_v, ids, h->ws.K,
+                                                                      h->d_status);
+    }
+    k_est_eta<<<(cp.count + 127) / 128, 128, 0, s>>>(cp.count, S.N, S.n_v, ids, h->ws.K, eta2, h->d_est_neg);
+    h->launches += 3;
+    DPG_CUDA_TRY(h, cudaGetLastError());
+  }
+  return DPG_OK;
+}
+
+}  // namespace dpg
+
+// Check hook of the factorisation kernels (declared in dpg.h).
+extern "C" int dpg_factor_check(int32_t arith, int32_t cplx, int32_t N, int32_t nact, int32_t nv, int32_t npiv,
+                                const double* A, double* out, int32_t* not_hpd) {
+  using namespace dpg;
+  if (!A || !out || N <= 0 || nact < 0 || nact > N || nv < 0 || npiv < 0 || npiv > nact || nv > npiv ||
+      (arith != DPG_FACTOR_FP64 && arith != DPG_FACTOR_TC_SPLIT))
+    return DPG_ERR_ARG;
+  if (N > 3315) return DPG_ERR_UNSUPPORTED;
+  const size_t elems = (size_t)N * N * (cplx ? 2 : 1);
+  double* dA = nullptr;
+  int* dst = nullptr;  // [0]: ids, [1]: pivot flag, [2]: timeout flag
+  uint8_t* dQ = nullptr;
+  const size_t qbytes = factor_tc_scratch_bytes(N, cplx != 0);
+  int rc = DPG_OK;
+  if (cudaMalloc(&dA, elems * 8) != cudaSuccess || cudaMalloc(&dst, 3 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&dQ, qbytes) != cudaSuccess)
+    rc = DPG_ERR_NOMEM;
+  const int zero3[3] = {0, 0, 0};
+  if (rc == DPG_OK && (cudaMemcpy(dA, A, elems * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+                       cudaMemcpy(dst, zero3, sizeof(zero3), cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = DPG_ERR_CUDA;
+  if (rc == DPG_OK) {
+    if (arith == DPG_FACTOR_TC_SPLIT) {
+      rc = factor_tc_init();
+      if (rc == DPG_OK) rc = factor_tc_launch(cplx != 0, 1, N, nact, nv, npiv, dst, dA, dst + 1, dst + 2, dQ, nullptr);
+    } else if (cplx) {
+      cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)factor_smem<double2>());
+      k_factor<double2><<<1, 256, factor_smem<double2>()>>>(N, nact, nv, npiv, dst, reinterpret_cast<double2*>(dA),
+                                                             dst + 1);
+    } else {
+      cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)factor_smem<double>());
+      k_factor<double><<<1, 256, factor_smem<double>()>>>(N, nact, nv, npiv, dst, dA, dst + 1);
+    }
+  }
+  int hst[3] = {0, 0, 0};
+  if (rc == DPG_OK && (cudaDeviceSynchronize() != cudaSuccess ||
+                       cudaMemcpy(hst, dst, sizeof(hst), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                       cudaMemcpy(out, dA, elems * 8, cudaMemcpyDeviceToHost) != cudaSuccess))
+    rc = DPG_ERR_CUDA;
+  if (rc == DPG_OK && hst[2]) rc = DPG_ERR_TIMEOUT;
+  if (not_hpd) *not_hpd = hst[1];
+  cudaFree(dA);
+  cudaFree(dst);
+  cudaFree(dQ);
+  return rc;
+}
+
+namespace dpg {
 
 // Reference matrices on the unit cube: X_ref = Cu^T V (metric free) and the
 // per-face trace pairings T_f = Vt^T NxP, T_all = sum_f T_f.

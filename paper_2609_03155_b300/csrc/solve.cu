@@ -823,70 +823,11 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
 }
 
 // ------------------------------------------------------------ estimate --
-// Per element: uhat_K gathered from x (free) and the Dirichlet values,
-// eta^2 = c - 2 Re(uhat^H s) + uhat^H S uhat, u = z - Z uhat.
-__global__ void __launch_bounds__(256) k_estimate(int nh, int nu, const int* __restrict__ elems,
-                                                  const ElemOff* __restrict__ off, const int32_t* __restrict__ l2g,
-                                                  const double2* __restrict__ xfix, const double2* __restrict__ xhat,
-                                                  const double2* __restrict__ Sst, const double2* __restrict__ sst,
-                                                  const double* __restrict__ cst, const double2* __restrict__ Zst,
-                                                  const double2* __restrict__ zst, double2* u_out, double* eta2) {
-  extern __shared__ double2 su[];
-  const int e = elems[blockIdx.x];
-  const ElemOff of = off[e];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) {
-    const int g = l2g[of.h + t];
-    su[t] = g >= 0 ? xhat[g] : (g == -1 ? xfix[of.h + t] : make_double2(0.0, 0.0));
-  }
-  __syncthreads();
-  const double2* Se = Sst + of.S;
-  double q = 0.0;  // sum over rows of Re(conj(uhat_i) (S uhat)_i)
-  for (int i = wid; i < nh; i += nw) {
-    double yr = 0.0, yi = 0.0;
-    for (int j = lane; j < nh; j += 32) {
-      const double2 v = Se[(size_t)i * nh + j], x = su[j];
-      yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
-      yi = fma(v.x, x.y, fma(v.y, x.x, yi));
-    }
-    yr = warp_sum(yr);
-    yi = warp_sum(yi);
-    const double2 ui = su[i], si = sst[of.h + i];
-    q += (lane == 0) ? (ui.x * yr + ui.y * yi) - 2.0 * (ui.x * si.x + ui.y * si.y) : 0.0;
-  }
-  if (u_out) {
-    const double2* Ze = Zst + of.Z;
-    for (int i = wid; i < nu; i += nw) {
-      double yr = 0.0, yi = 0.0;
-      for (int j = lane; j < nh; j += 32) {
-        const double2 v = Ze[(size_t)i * nh + j], x = su[j];
-        yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
-        yi = fma(v.x, x.y, fma(v.y, x.x, yi));
-      }
-      yr = warp_sum(yr);
-      yi = warp_sum(yi);
-      if (lane == 0) {
-        const double2 zi = zst[of.u + i];
-        u_out[of.u + i] = make_double2(zi.x - yr, zi.y - yi);
-      }
-    }
-  }
-  __shared__ double sq[32];
-  q = warp_sum(q);
-  if (lane == 0) sq[wid] = q;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = cst[e];
-    for (int k = 0; k < nw; ++k) t += sq[k];
-    eta2[e] = t;
-  }
-}
-
 __global__ void k_sqrt_sum(int n, const double* __restrict__ eta2, double* eta, double* total) {
   __shared__ double sw[32];
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = fmax(eta2[i], 0.0);
+    const double v = eta2[i];  // >= 0 (the recompute pass clamps and counts negatives)
     if (eta) eta[i] = sqrt(v);
     acc += v;
   }
@@ -900,15 +841,34 @@ __global__ void k_sqrt_sum(int n, const double* __restrict__ eta2, double* eta, 
   }
 }
 
-// eta_K^2 of every element into eta2[e] (and u), one launch per order group.
-static void launch_estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta2, cudaStream_t s) {
-  for (const Group& G : h->grp) {
-    const Sizes& S = G.sz;
-    k_estimate<<<(int)G.elems.size(), 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, G.d_elems, h->d_off, h->d_l2g,
-                                                                        h->d_xfix, xhat, h->d_S, h->d_s, h->d_c,
-                                                                        h->d_Z, h->d_z, u, eta2);
-    h->launches += 1;
+// u (optional), eta_K^2 into eta2[0, ne) and their sum into eta2[ne]; the
+// host value (if asked) after a synchronisation that also reports a timed-out
+// tensor-core wait of the recompute pass.
+static int estimate_into(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
+                         double* eta2, cudaStream_t s) {
+  if (!eta && !eta_global) {  // recovery only
+    if (u) recover_u(h, xhat, u, s);
+    DPG_CUDA_TRY(h, cudaGetLastError());
+    return DPG_OK;
   }
+  int rc = estimate_pass(h, xhat, u, eta2, s);
+  if (rc) return rc;
+  k_sqrt_sum<<<1, 1024, 0, s>>>(h->ne, eta2, eta, eta2 + h->ne);
+  h->launches += 1;
+  DPG_CUDA_TRY(h, cudaGetLastError());
+  if (eta_global) {
+    double tot = 0;
+    int terr = 0;
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(&tot, eta2 + h->ne, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DPG_CUDA_TRY(h, cudaMemcpyAsync(&terr, h->d_status + h->ne, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (terr) {
+      h->err = "a tensor-core wait of the estimator gave up";
+      return DPG_ERR_TIMEOUT;
+    }
+    *eta_global = std::sqrt(std::max(tot, 0.0));
+  }
+  return DPG_OK;
 }
 
 int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global, cudaStream_t s) {
@@ -921,18 +881,18 @@ int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double
     return DPG_ERR_ARG;
   }
   double* d_eta2 = nullptr;
-  DPG_CUDA_TRY(h, cudaMallocAsync(&d_eta2, sizeof(double) * (h->ne + 1), s));
-  launch_estimate(h, xhat, u, d_eta2, s);
-  k_sqrt_sum<<<1, 1024, 0, s>>>(h->ne, d_eta2, eta, d_eta2 + h->ne);
-  h->launches += 1;
-  DPG_CUDA_TRY(h, cudaGetLastError());
-  if (eta_global) {
-    double tot = 0;
-    DPG_CUDA_TRY(h, cudaMemcpyAsync(&tot, d_eta2 + h->ne, sizeof(double), cudaMemcpyDeviceToHost, s));
-    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
-    *eta_global = std::sqrt(std::max(tot, 0.0));
+  if (eta || eta_global) DPG_CUDA_TRY(h, cudaMallocAsync(&d_eta2, sizeof(double) * (h->ne + 1), s));
+  const int rc = estimate_into(h, xhat, u, eta, eta_global, d_eta2, s);
+  if (d_eta2) cudaFreeAsync(d_eta2, s);
+  return rc;
+}
+
+int estimate_negatives(dpg_handle* h, int* count) {
+  if (!h->d_est_neg) {
+    *count = 0;
+    return DPG_OK;
   }
-  DPG_CUDA_TRY(h, cudaFreeAsync(d_eta2, s));
+  DPG_CUDA_TRY(h, cudaMemcpy(count, h->d_est_neg, sizeof(int), cudaMemcpyDeviceToHost));
   return DPG_OK;
 }
 
@@ -997,17 +957,8 @@ int estimate_noalloc(dpg_handle* h, const double2* xhat, double2* u, double* eta
   double* scratch = nullptr;
   int rc = noalloc_scratch(h, &scratch);
   if (rc) return rc;
-  launch_estimate(h, xhat, u, scratch, s);
-  k_sqrt_sum<<<1, 1024, 0, s>>>(h->ne, scratch, eta, scratch + h->ne);
-  h->launches += 1;
-  DPG_CUDA_TRY(h, cudaGetLastError());
-  if (eta_global) {
-    double tot = 0;
-    DPG_CUDA_TRY(h, cudaMemcpyAsync(&tot, scratch + h->ne, sizeof(double), cudaMemcpyDeviceToHost, s));
-    DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
-    *eta_global = std::sqrt(std::max(tot, 0.0));
-  }
-  return DPG_OK;
+  // the recompute pass runs in the handle's chunk workspace, allocated at setup
+  return estimate_into(h, xhat, u, eta, eta_global, scratch, s);
 }
 
 }  // namespace dpg

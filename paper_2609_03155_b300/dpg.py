@@ -122,6 +122,11 @@ class DPG:
             u = u.view(self.n_elem, self.n_u)
         return u, eta, tot.value
 
+    def estimate_clamped(self):
+        c = C.c_int32(0)
+        check(_lib.lib().dpg_estimate_clamped(self.h, C.byref(c)), self.h)
+        return c.value
+
     def update_elements(self, corners=None, eps=None, mu=None, stream=None):
         """Host -> device copy of per-element corners (n_elem x 8 x 3), eps, mu (use pinned tensors)."""
         check(_lib.lib().dpg_update_elements(self.h, ptr(corners), ptr(eps), ptr(mu), stream_handle(stream)), self.h)
@@ -136,6 +141,9 @@ class DPG:
 
     def set_graph(self, enable=True):
         check(_lib.lib().dpg_set_graph(self.h, int(enable)), self.h)
+
+    def set_factor_arith(self, arith=_lib.DPG_FACTOR_TC_SPLIT):
+        check(_lib.lib().dpg_set_factor_arith(self.h, int(arith)), self.h)
 
     def set_wait_limit(self, wait_ns=5_000_000_000, hold=False):
         check(_lib.lib().dpg_set_wait_limit(self.h, int(wait_ns), int(hold)), self.h)
@@ -235,6 +243,23 @@ def tc_gemm(A, B, split=1, upper_only=False, C=None):
     C = np.zeros((Ma, Nb)) if C is None else np.ascontiguousarray(C, np.float64).copy()
     check(_lib.lib().dpg_tc_gemm(split, Ma, Nb, Kd, ptr(A), ptr(B), ptr(C), int(upper_only)))
     return C
+
+
+def factor_check(A, nv, npiv, nact=None, arith=_lib.DPG_FACTOR_TC_SPLIT):
+    """Element factorisation kernel on one host matrix A (N x N, real or complex; lower triangle used).
+
+    Returns (factored matrix, not_hpd flag) with the same layout (row-major
+    numpy view of the column-major device layout is handled here).
+    """
+    A = np.asarray(A)
+    N = A.shape[0]
+    cplx = np.iscomplexobj(A)
+    buf = np.ascontiguousarray(A.T, dtype=np.complex128 if cplx else np.float64)  # column-major
+    out = np.empty_like(buf)
+    bad = C.c_int32(0)
+    check(_lib.lib().dpg_factor_check(int(arith), int(cplx), N, N if nact is None else int(nact), int(nv), int(npiv),
+                                      buf.ctypes.data, out.ctypes.data, C.byref(bad)))
+    return out.T.copy(), bool(bad.value)
 
 
 def probe_peaks(stream=None):

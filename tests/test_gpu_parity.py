@@ -7,7 +7,11 @@ Tolerances (each follows from the arithmetic of its step):
   full-size guide (kappa ~ 5e8) ten times the measured two-route floor.
 * trace solution and interior field vs the oracle's direct solve: relative 1e-10
   (CG run to 1e-13 relative residual).
-* eta_K: relative 1e-7 (quadratic-form route vs the oracle's Cholesky route).
+* eta_K (Sec. 2.3, ||Psi_K||_V = ||L^{-1} r_K||): per element, relative 1e-9,
+  against the oracle's eta_K at the same trace solution (the GPU's), so that
+  the comparison isolates the estimator.  Both sides form r_K = l - B u - B-hat uhat
+  and apply L^{-1}; the oracle's own two routes (Cholesky and eigen) agree
+  to ~1e-11 per element on these cases.
 """
 import numpy as np
 import pytest
@@ -116,9 +120,12 @@ def test_solution_matches_oracle_direct_solve(dpg_mod, case):
     u, eta, etag = d.estimate(x)
     u_or = np.stack([r['u'] for r in sol['rec']])
     assert rel(u.cpu().numpy(), u_or) < 1e-10
-    eta_or = sol['eta']
-    assert np.max(np.abs(eta.cpu().numpy() - eta_or) / eta_or.max()) < 1e-7
-    assert abs(etag - np.sqrt(np.sum(eta_or ** 2))) < 1e-7 * np.sqrt(np.sum(eta_or ** 2))
+    # the oracle's estimator at the GPU's trace solution, element by element
+    eta_or = np.array([oel.recover(sol['elements'][e], sol['conds'][e], uh[e])['eta'] for e in range(len(uh))])
+    eta_g = eta.cpu().numpy()
+    assert np.all(np.abs(eta_g - eta_or) <= 1e-9 * eta_or), np.max(np.abs(eta_g - eta_or) / eta_or)
+    assert abs(etag - np.sqrt(np.sum(eta_or ** 2))) < 1e-9 * np.sqrt(np.sum(eta_or ** 2))
+    assert d.estimate_clamped() == 0
     d.destroy()
 
 
@@ -278,7 +285,8 @@ def test_real_path_matches_complex_path(dpg_mod):
         assert rel(out_r['S'][k], out_c['S'][k]) < 1e-10
     assert rel(x_r.cpu().numpy(), x_c.cpu().numpy()) < 1e-10
     assert rel(u_r.cpu().numpy(), u_c.cpu().numpy()) < 1e-10
-    assert np.max(np.abs(eta_r.cpu().numpy() - eta_c.cpu().numpy())) < 1e-7 * eta_c.cpu().numpy().max()
+    er, ec = eta_r.cpu().numpy(), eta_c.cpu().numpy()
+    assert np.all(np.abs(er - ec) <= 1e-9 * ec), np.max(np.abs(er - ec) / ec)
     d.destroy()
 
 

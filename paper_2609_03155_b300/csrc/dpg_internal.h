@@ -192,6 +192,21 @@ struct dpg_handle {
   double2* d_val = nullptr;
   double2* d_b = nullptr;
   float2* d_val32 = nullptr;    // FP32 copy for IR inner solves (lazily built)
+  // Hermitian half storage of the FP32 inner matrix (lazily built): per row
+  // the prefix of its entity's column list up to and including the entity's
+  // own unknowns (blocks of lower entities and the diagonal block); the upper
+  // blocks are applied as conjugate transposes through per-block partial
+  // sums T (block a's strictly lower part, n_low(a) values) that the rows of
+  // the upper neighbours' blocks gather in a fixed order (rev lists).
+  bool have_half = false, have_val32h = false;
+  int64_t nnz_h = 0, t_len = 0, rev_len = 0;
+  int half_wmax = 0;                // widest half row
+  int64_t* d_rowptr_h = nullptr;    // n + 1
+  int64_t* d_toff = nullptr;        // nblk + 1: offset of block a's partial sums in T
+  int64_t* d_rev_ptr = nullptr;     // nblk + 1
+  int64_t* d_rev_off = nullptr;     // rev_len: T offsets of the segments that belong to block b's rows
+  float2* d_val32h = nullptr;       // nnz_h
+  float2* d_T = nullptr;            // t_len
   bool have_elements = false, have_system = false, have_val32 = false, have_dinv = false;
   double* d_dinv = nullptr;     // inverse diagonal (Jacobi)
   float* d_dinv32 = nullptr;

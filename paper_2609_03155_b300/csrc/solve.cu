@@ -88,6 +88,7 @@ int assemble_system(dpg_handle* h, cudaStream_t s) {
   DPG_CUDA_TRY(h, cudaGetLastError());
   h->have_system = true;
   h->have_val32 = false;
+  h->have_val32h = false;
   h->have_dinv = false;
   h->have_binv = false;
   return DPG_OK;
@@ -110,6 +111,11 @@ struct SysView {
   const int32_t* cols;
   const int64_t* binv_ptr;
   int dmax;  // rows of the largest entity block
+  // Hermitian half storage (FP32 inner solves)
+  const int64_t* rowptr_h;
+  const int64_t* toff;
+  const int64_t* rev_ptr;
+  const int64_t* rev_off;
 };
 
 struct CgState {          // device-resident
@@ -328,15 +334,79 @@ __device__ __forceinline__ void block_precond(const SysView& S, int b, int preco
   }
 }
 
+// Half-storage SpMV, first half: block a (one warp): for each of its rows
+// y_row = sum over the stored prefix (lower blocks and the diagonal block) of
+// A[row][c] x_c, into y; and the conjugate-transpose partial sums of the
+// strictly lower part, T[toff[a] + q] = sum_rows conj(A[row][q]) x_row, one
+// per prefix position q < n_low(a).  Positions are taken in windows of
+// 32 x HW per lane pass (lane owns q = window + lane + 32 k).
+constexpr int HW = 8;
+template <typename V, typename Mv>
+__device__ __forceinline__ void half_block_lower(const SysView& S, int a, const Mv* __restrict__ valh,
+                                                 const V* __restrict__ x, V* y, V* T) {
+  using R = typename RealOf<Mv>::T;
+  const int lane = threadIdx.x & 31;
+  const int4 B = S.blk[a];
+  const int wl = B.w, Wh = B.w + B.y;
+  const int32_t* c = S.cols + S.colptr[a];
+  for (int q0 = 0; q0 < Wh; q0 += 32 * HW) {
+    R tr[HW], ti[HW];
+#pragma unroll
+    for (int k = 0; k < HW; ++k) tr[k] = ti[k] = 0;
+    for (int i = 0; i < B.y; ++i) {
+      const int64_t row = B.x + i;
+      const Mv* v = valh + S.rowptr_h[row];
+      const V xi = x[row];
+      R ar = 0, ai = 0;
+#pragma unroll
+      for (int k = 0; k < HW; ++k) {
+        const int q = q0 + lane + 32 * k;
+        if (q < Wh) {
+          const Mv av = v[q];
+          const V xc = x[c[q]];
+          ar = fma(av.x, (R)xc.x, fma(-av.y, (R)xc.y, ar));
+          ai = fma(av.x, (R)xc.y, fma(av.y, (R)xc.x, ai));
+          if (q < wl) {  // conj(A[row][q]) x_row
+            tr[k] = fma(av.x, (R)xi.x, fma(av.y, (R)xi.y, tr[k]));
+            ti[k] = fma(av.x, (R)xi.y, fma(-av.y, (R)xi.x, ti[k]));
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+      }
+      if (lane == 0) {
+        if (q0 == 0) {
+          y[row] = mkv(ar, ai, (V*)nullptr);
+        } else {
+          V yv = y[row];
+          yv.x += ar;
+          yv.y += ai;
+          y[row] = yv;
+        }
+      }
+    }
+    V* Ta = T + S.toff[a];
+#pragma unroll
+    for (int k = 0; k < HW; ++k) {
+      const int q = q0 + lane + 32 * k;
+      if (q < wl) Ta[q] = mkv(tr[k], ti[k], (V*)nullptr);
+    }
+  }
+}
+
 // One whole CG solve of A x = r0 (x = 0 at entry, r holds r0 at entry).
 // V: precision of the vectors and recurrences; Mv: precision of the stored
 // matrix and of the SpMV products (FP32 values with FP64 recurrences keeps the
 // convergence rate of FP64 CG at the bandwidth of an FP32 matrix).
-template <typename V, typename Mv>
+template <typename V, typename Mv, bool HALF>
 __global__ void __launch_bounds__(CG_THREADS, 5) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
                                                              V* Ap, V* z, int precond,
                                                              const typename RealOf<V>::T* __restrict__ dinv,
-                                                             const V* __restrict__ binv, double* red, CgState* st) {
+                                                             const V* __restrict__ binv, double* red, CgState* st,
+                                                             V* T) {
   using R = typename RealOf<V>::T;
   extern __shared__ __align__(16) unsigned char cg_smem[];
   V* rs = reinterpret_cast<V*>(cg_smem) + (threadIdx.x >> 5) * S.dmax;
@@ -369,12 +439,35 @@ __global__ void __launch_bounds__(CG_THREADS, 5) k_cg_persistent(SysView S, cons
   while (!done && it < max_iter) {
     // A: Ap = A p and Re(p^H A p)
     R pap = 0;
-    for (int64_t row = gw; row < S.n; row += warps) {
-      const V y = row_spmv<V, Mv>(S, row, val, p);
-      if ((threadIdx.x & 31) == 0) {
-        Ap[row] = y;
-        const V pr = p[row];
-        pap += pr.x * y.x + pr.y * y.y;
+    if (HALF) {
+      // lower blocks and diagonal blocks, conjugate-transpose partial sums
+      for (int b = gw; b < S.nblk; b += warps) half_block_lower<V, Mv>(S, b, val, p, Ap, T);
+      if (!grid_barrier(st, gen)) return;
+      // the upper blocks: the partial sums of the upper neighbours, in list order
+      for (int b = gw; b < S.nblk; b += warps) {
+        const int4 B = S.blk[b];
+        const int64_t k0 = S.rev_ptr[b], k1 = S.rev_ptr[b + 1];
+        for (int i = threadIdx.x & 31; i < B.y; i += 32) {
+          const int64_t row = B.x + i;
+          V yv = Ap[row];
+          for (int64_t k = k0; k < k1; ++k) {
+            const V t = T[S.rev_off[k] + i];
+            yv.x += t.x;
+            yv.y += t.y;
+          }
+          Ap[row] = yv;
+          const V pr = p[row];
+          pap += pr.x * yv.x + pr.y * yv.y;
+        }
+      }
+    } else {
+      for (int64_t row = gw; row < S.n; row += warps) {
+        const V y = row_spmv<V, Mv>(S, row, val, p);
+        if ((threadIdx.x & 31) == 0) {
+          Ap[row] = y;
+          const V pr = p[row];
+          pap += pr.x * y.x + pr.y * y.y;
+        }
       }
     }
     block_partial(pap, (R)0, redA, nullptr);
@@ -550,6 +643,10 @@ static SysView sys_view(dpg_handle* h) {
   v.cols = h->d_cols;
   v.binv_ptr = h->d_binv_ptr;
   v.dmax = h->blk_dmax;
+  v.rowptr_h = h->d_rowptr_h;
+  v.toff = h->d_toff;
+  v.rev_ptr = h->d_rev_ptr;
+  v.rev_off = h->d_rev_off;
   return v;
 }
 
@@ -563,7 +660,7 @@ static int ensure_buf(dpg_handle* h, void** p, size_t bytes) {
   return DPG_OK;
 }
 
-template <typename V, typename Mv>
+template <typename V, typename Mv, bool HALF>
 static int persistent_grid(dpg_handle* h, int* grid, size_t smem) {
   int dev = 0, sms = 0, per = 0, coop = 0;
   DPG_CUDA_TRY(h, cudaGetDevice(&dev));
@@ -573,22 +670,23 @@ static int persistent_grid(dpg_handle* h, int* grid, size_t smem) {
     h->err = "device does not support cooperative launches";
     return DPG_ERR_UNSUPPORTED;
   }
-  DPG_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<V, Mv>, CG_THREADS, smem));
+  DPG_CUDA_TRY(h,
+               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<V, Mv, HALF>, CG_THREADS, smem));
   *grid = std::max(1, std::min(per, 8) * sms);
   return DPG_OK;
 }
 
 // One persistent solve of A d = r0 (d = 0 at entry; r holds r0 at entry).
-template <typename V, typename Mv>
+template <typename V, typename Mv, bool HALF>
 static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
                           const typename RealOf<V>::T* dinv, const V* binv, double tol2, int max_iter,
-                          cudaStream_t s, int* iters, double* rr_out) {
+                          cudaStream_t s, int* iters, double* rr_out, V* T = nullptr) {
   int grid = 0;
   const size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
   if (smem > 48 * 1024)
-    DPG_CUDA_TRY(h,
-                 cudaFuncSetAttribute(k_cg_persistent<V, Mv>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int rc = persistent_grid<V, Mv>(h, &grid, smem);
+    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_cg_persistent<V, Mv, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+  int rc = persistent_grid<V, Mv, HALF>(h, &grid, smem);
   if (rc) return rc;
   CgState host{};
   host.tol2 = tol2;
@@ -599,15 +697,15 @@ static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap,
   DPG_CUDA_TRY(h, cudaMemcpyAsync(st, &host, sizeof(CgState), cudaMemcpyHostToDevice, s));
   SysView S = sys_view(h);
   double* red = h->d_red;
-  void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st};
+  void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st, &T};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->timing) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  DPG_CUDA_TRY(h,
-               cudaLaunchCooperativeKernel((void*)k_cg_persistent<V, Mv>, dim3(grid), dim3(CG_THREADS), args, smem, s));
+  DPG_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_cg_persistent<V, Mv, HALF>, dim3(grid), dim3(CG_THREADS), args,
+                                              smem, s));
   h->launches += 1;
   if (h->timing) cudaEventRecord(e1, s);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(&host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
@@ -672,6 +770,74 @@ static int prepare_preconditioner(dpg_handle* h, cudaStream_t s) {
   return DPG_OK;
 }
 
+// Hermitian half storage of the FP32 inner matrix: row pointers of the stored
+// prefixes, the partial-sum offsets per block and, per block b, the T offsets
+// of b's segments in its upper neighbours' partial sums (in block order, so
+// every sum is taken in one fixed order).  Host-side construction, once.
+static int build_half(dpg_handle* h) {
+  if (h->have_half) return DPG_OK;
+  const int nb = h->nblk;
+  std::vector<int32_t> row2blk(h->n);
+  for (int b = 0; b < nb; ++b)
+    for (int i = 0; i < h->blk[b].y; ++i) row2blk[h->blk[b].x + i] = b;
+  std::vector<int64_t> rowptr_h(h->n + 1, 0), toff(nb + 1, 0);
+  int wmax = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int4& B = h->blk[b];
+    const int Wh = B.w + B.y;
+    wmax = std::max(wmax, Wh);
+    for (int i = 0; i < B.y; ++i) rowptr_h[B.x + i + 1] = Wh;
+    toff[b + 1] = toff[b] + B.w;
+  }
+  for (int64_t i = 0; i < h->n; ++i) rowptr_h[i + 1] += rowptr_h[i];
+  std::vector<std::vector<int64_t>> rev(nb);
+  for (int a = 0; a < nb; ++a) {
+    const int4& A = h->blk[a];
+    const int32_t* c = &h->cols[h->blk_colptr[a]];
+    for (int q = 0; q < A.w; ++q) {
+      const int b = row2blk[c[q]];
+      if (c[q] == h->blk[b].x) rev[b].push_back(toff[a] + q);  // first column of b's segment
+    }
+  }
+  std::vector<int64_t> rev_ptr(nb + 1, 0), rev_off;
+  for (int b = 0; b < nb; ++b) {
+    rev_ptr[b + 1] = rev_ptr[b] + (int64_t)rev[b].size();
+    rev_off.insert(rev_off.end(), rev[b].begin(), rev[b].end());
+  }
+  h->nnz_h = rowptr_h[h->n];
+  h->t_len = toff[nb];
+  h->rev_len = (int64_t)rev_off.size();
+  h->half_wmax = wmax;
+  int rc = 0;
+  rc |= ensure_buf(h, (void**)&h->d_rowptr_h, sizeof(int64_t) * (h->n + 1));
+  rc |= ensure_buf(h, (void**)&h->d_toff, sizeof(int64_t) * (nb + 1));
+  rc |= ensure_buf(h, (void**)&h->d_rev_ptr, sizeof(int64_t) * (nb + 1));
+  rc |= ensure_buf(h, (void**)&h->d_rev_off, sizeof(int64_t) * std::max<int64_t>(1, h->rev_len));
+  rc |= ensure_buf(h, (void**)&h->d_val32h, sizeof(float2) * h->nnz_h);
+  rc |= ensure_buf(h, (void**)&h->d_T, sizeof(float2) * std::max<int64_t>(1, h->t_len));
+  if (rc) return DPG_ERR_NOMEM;
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_rowptr_h, rowptr_h.data(), sizeof(int64_t) * rowptr_h.size(), cudaMemcpyHostToDevice));
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_toff, toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_rev_ptr, rev_ptr.data(), sizeof(int64_t) * rev_ptr.size(), cudaMemcpyHostToDevice));
+  if (!rev_off.empty())
+    DPG_CUDA_TRY(h, cudaMemcpy(h->d_rev_off, rev_off.data(), sizeof(int64_t) * rev_off.size(), cudaMemcpyHostToDevice));
+  h->have_half = true;
+  return DPG_OK;
+}
+
+// FP32 copy of each row's stored prefix (one warp per row).
+__global__ void __launch_bounds__(256) k_to_f32_half(SysView S, const double2* __restrict__ val, float2* valh) {
+  const int warps = gridDim.x * (blockDim.x / 32);
+  const int lane = threadIdx.x & 31;
+  for (int64_t row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); row < S.n; row += warps) {
+    const int4 B = S.blk[S.row2blk[row]];
+    const int Wh = B.w + B.y;
+    const double2* v = val + S.rowptr[row];
+    float2* o = valh + S.rowptr_h[row];
+    for (int q = lane; q < Wh; q += 32) o[q] = make_float2((float)v[q].x, (float)v[q].y);
+  }
+}
+
 // Algorithmic bytes of one CG iteration: the matrix values (16 B per complex
 // non-zero in FP64, 8 B in FP32), the per-entity column lists, the
 // preconditioner data, and the vector traffic of the three phases
@@ -681,7 +847,20 @@ int64_t cg_bytes_per_iteration(const dpg_handle* h, int mode) {
   const bool ir = (mode & DPG_CG_IR_FP32) != 0;
   const int64_t mb = ir ? 8 : 16, vb = ir ? 8 : 16;
   int64_t ncol = (int64_t)h->cols.size();
-  int64_t bytes = mb * h->nnz + 4 * ncol + 13 * vb * h->n;
+  int64_t bytes = 0;
+  if (ir) {
+    // half storage: stored prefixes, their column lists, the partial sums T
+    // (written once, read once) and their offsets
+    int64_t nh = 0, ncol_h = 0, tl = 0;
+    for (const int4& B : h->blk) {
+      nh += (int64_t)B.y * (B.w + B.y);
+      ncol_h += B.w + B.y;
+      tl += B.w;
+    }
+    bytes = mb * nh + 4 * ncol_h + 2 * vb * tl + 8 * h->rev_len + 14 * vb * h->n;
+  } else {
+    bytes = mb * h->nnz + 4 * ncol + 13 * vb * h->n;
+  }
   if (mode & DPG_CG_BLOCK_JACOBI) {
     int64_t inv = 0;
     for (const int4& B : h->blk) inv += (int64_t)B.y * B.y;
@@ -724,9 +903,12 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     rc |= ensure_buf(h, (void**)&h->d_Ap32, sizeof(float2) * n);
     rc |= ensure_buf(h, (void**)&h->d_x32, sizeof(float2) * n);
     rc |= ensure_buf(h, (void**)&h->d_z32, sizeof(float2) * n);
-    rc |= ensure_buf(h, (void**)&h->d_val32, sizeof(float2) * h->nnz);
   }
   if (rc) return DPG_ERR_NOMEM;
+  if (ir) {
+    rc = build_half(h);
+    if (rc) return rc;
+  }
   const double2* rhs = b ? b : h->d_b;
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
@@ -736,10 +918,10 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     rc = prepare_preconditioner(h, s);
     if (rc) return rc;
   }
-  if (ir && !h->have_val32) {
-    k_to_f32<<<1184, 256, 0, s>>>(h->nnz, h->d_val, h->d_val32);
+  if (ir && !h->have_val32h) {
+    k_to_f32_half<<<1184, 256, 0, s>>>(sys_view(h), h->d_val, h->d_val32h);
     h->launches += 1;
-    h->have_val32 = true;
+    h->have_val32h = true;
   }
   // ||b|| (and r = b for x0 = 0)
   double bb = 0;
@@ -771,13 +953,14 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
       const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
       k_to_f32<<<1184, 256, 0, s>>>((int64_t)n, h->d_r, h->d_r32);
       h->launches += 1;
-      rc = run_persistent<float2, float2>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32, precond,
-                                          h->d_dinv32, h->d_binv32, itol * itol, max_iter - total_iters, s, &it, &rr);
+      rc = run_persistent<float2, float2, true>(h, h->d_val32h, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
+                                                precond, h->d_dinv32, h->d_binv32, itol * itol, max_iter - total_iters,
+                                                s, &it, &rr, h->d_T);
       if (rc) return rc;
       k_add_correction<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_x32);
     } else {
       const double itol = 0.5 * tol;
-      rc = run_persistent<double2, double2>(h, h->d_val, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond,
+      rc = run_persistent<double2, double2, false>(h, h->d_val, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond,
                                             h->d_dinv, h->d_binv, itol * itol, max_iter - total_iters, s, &it, &rr);
       if (rc) return rc;
       k_add_correction64<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_d64);

@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DPG elements/s (local solve+η_K) & CG time-to-1e-10; mixed/batched vs FP64"
 UNIT = "elements/s"
-CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3, "fp64-bjacobi": 4, "ir-bjacobi": 5}
+CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3, "fp64-bjacobi": 4, "ir-bjacobi": 5,
+            "ir-bjacobi-half": 5 | 16}
 PRECISIONS = {"fp64": 0, "tf32": 1, "3xtf32": 2}
 
 
@@ -401,7 +402,9 @@ def main():
         pass
     bpi = d.cg_bytes_per_iteration(mode)
     vb = 8 if mode & 1 else 16
-    algo_bpi = vb * int(d.nnz) + 6 * vb * int(d.n)
+    # Hermitian half storage reads each off-diagonal block once: half the values
+    mb = vb // 2 if mode & 16 else vb
+    algo_bpi = mb * int(d.nnz) + 6 * vb * int(d.n)
     # DRAM traffic per iteration / implementation bytes of the FP32 inner CG
     # kernel, from the ncu capture of the 12x6x24 guide (dram__bytes_read.sum +
     # dram__bytes_write.sum over 279 iterations); the traffic per iteration
@@ -416,7 +419,7 @@ def main():
                            if mode & 1 else None),
                "traffic_unit": "bytes per launch (ncu ratio 1.022 x implementation bytes, from the 12x6x24 capture)",
                "peak_source": hbm_src, "bytes_per_iteration": algo_bpi,
-               "bytes_rule": f"{vb} B x nnz + 6 x {vb} B x n (matrix values and six vector passes)",
+               "bytes_rule": f"{mb} B x nnz + 6 x {vb} B x n (matrix values and six vector passes)",
                "overhead_bytes_per_iteration": bpi - algo_bpi,
                "overhead_rule": "per-entity column lists, block-Jacobi inverses and the other vector passes",
                "achieved_with_overhead": bpi * tim["cg_kernel_iterations"] / cg_s / 1e9,

@@ -95,7 +95,7 @@ enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2
  * error against FP64 is a reported quantity, not a parity bound. */
 enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
-enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8 };
+enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8, DPG_CG_HALF = 16 };
 enum { DPG_FLAG_ADJOINT = 1 };
 /* Arithmetic of the element factorisation's trailing updates (dpg_set_factor_arith). */
 enum { DPG_FACTOR_FP64 = 0, DPG_FACTOR_TC_SPLIT = 1 };
@@ -199,6 +199,10 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * preconditioning to future work; the stopping test stays on the
  * unpreconditioned residual.  Each (inner) solve is one cooperative kernel
  * whose grid barriers give up after a bounded wait (DPG_ERR_TIMEOUT).
+ * DPG_CG_HALF may be or-ed to DPG_CG_IR_FP32: the inner solves read a
+ * Hermitian half storage of the FP32 matrix (each pair of entity blocks once;
+ * the upper blocks are applied as conjugate transposes through per-block
+ * partial sums gathered in a fixed order, so results stay deterministic).
  * DPG_CG_X0 may be or-ed too: start from the x passed in (resume a stopped
  * solve, or warm-start from a nearby problem's solution) instead of x0 = 0.
  * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or

@@ -848,7 +848,7 @@ int64_t cg_bytes_per_iteration(const dpg_handle* h, int mode) {
   const int64_t mb = ir ? 8 : 16, vb = ir ? 8 : 16;
   int64_t ncol = (int64_t)h->cols.size();
   int64_t bytes = 0;
-  if (ir) {
+  if (ir && (mode & DPG_CG_HALF)) {
     // half storage: stored prefixes, their column lists, the partial sums T
     // (written once, read once) and their offsets
     int64_t nh = 0, ncol_h = 0, tl = 0;
@@ -881,7 +881,7 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     h->err = "bad CG arguments";
     return DPG_ERR_ARG;
   }
-  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0) ||
+  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0 | DPG_CG_HALF) ||
       ((mode & DPG_CG_JACOBI) && (mode & DPG_CG_BLOCK_JACOBI))) {
     h->err = "unknown CG mode";
     return DPG_ERR_ARG;
@@ -905,8 +905,12 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     rc |= ensure_buf(h, (void**)&h->d_z32, sizeof(float2) * n);
   }
   if (rc) return DPG_ERR_NOMEM;
-  if (ir) {
+  const bool half = ir && (mode & DPG_CG_HALF);
+  if (half) {
     rc = build_half(h);
+    if (rc) return rc;
+  } else if (ir) {
+    rc = ensure_buf(h, (void**)&h->d_val32, sizeof(float2) * h->nnz);
     if (rc) return rc;
   }
   const double2* rhs = b ? b : h->d_b;
@@ -918,10 +922,15 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     rc = prepare_preconditioner(h, s);
     if (rc) return rc;
   }
-  if (ir && !h->have_val32h) {
+  if (half && !h->have_val32h) {
     k_to_f32_half<<<1184, 256, 0, s>>>(sys_view(h), h->d_val, h->d_val32h);
     h->launches += 1;
     h->have_val32h = true;
+  }
+  if (ir && !half && !h->have_val32) {
+    k_to_f32<<<1184, 256, 0, s>>>(h->nnz, h->d_val, h->d_val32);
+    h->launches += 1;
+    h->have_val32 = true;
   }
   // ||b|| (and r = b for x0 = 0)
   double bb = 0;
@@ -953,9 +962,14 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
       const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
       k_to_f32<<<1184, 256, 0, s>>>((int64_t)n, h->d_r, h->d_r32);
       h->launches += 1;
-      rc = run_persistent<float2, float2, true>(h, h->d_val32h, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
-                                                precond, h->d_dinv32, h->d_binv32, itol * itol, max_iter - total_iters,
-                                                s, &it, &rr, h->d_T);
+      if (half)
+        rc = run_persistent<float2, float2, true>(h, h->d_val32h, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
+                                                  precond, h->d_dinv32, h->d_binv32, itol * itol,
+                                                  max_iter - total_iters, s, &it, &rr, h->d_T);
+      else
+        rc = run_persistent<float2, float2, false>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
+                                                   precond, h->d_dinv32, h->d_binv32, itol * itol,
+                                                   max_iter - total_iters, s, &it, &rr);
       if (rc) return rc;
       k_add_correction<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_x32);
     } else {

@@ -217,10 +217,6 @@ struct dpg_handle {
   bool plan_valid = false;
   int* d_plan_ids = nullptr;
   int* d_plan_rent = nullptr;
-  // launch plan of the estimator's recompute pass (every element on the complex path)
-  std::vector<dpg::ChunkPlan> est_plan;
-  int* d_est_ids = nullptr;
-  int* d_est_rent = nullptr;
   int* d_est_neg = nullptr;       // count of clamped negative eta_K^2 (one int)
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;

@@ -1283,7 +1283,6 @@ static void free_chunks(std::vector<ChunkPlan>& plan, int** d_ids, int** d_rent)
 
 void free_plan(dpg_handle* h) {
   free_chunks(h->plan, &h->d_plan_ids, &h->d_plan_rent);
-  free_chunks(h->est_plan, &h->d_est_ids, &h->d_est_rent);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
   h->plan_valid = false;
@@ -1345,12 +1344,11 @@ static int make_chunks(dpg_handle* h, bool real, std::vector<ChunkPlan>& plan, i
   return DPG_OK;
 }
 
-// The element pass's plan (real path as allowed) and the estimator's
-// recompute plan (every element complex), both built once per workspace.
+// The element pass's plan (real path as allowed), built once per workspace;
+// the estimator's recompute pass runs the same chunks.
 int build_plan(dpg_handle* h) {
   free_plan(h);
   int rc = make_chunks(h, h->allow_real, h->plan, &h->d_plan_ids, &h->d_plan_rent);
-  if (rc == DPG_OK) rc = make_chunks(h, false, h->est_plan, &h->d_est_ids, &h->d_est_rent);
   if (rc == DPG_OK && !h->d_est_neg) DPG_CUDA_TRY(h, cudaMalloc(&h->d_est_neg, sizeof(int)));
   if (rc) return rc;
   h->plan_valid = true;
@@ -1615,6 +1613,106 @@ __global__ void __launch_bounds__(256) k_est_residual(Sizes S, const int* __rest
   if (threadIdx.x == 0) A[(size_t)nv + (size_t)nv * N] = make_double2(0.0, 0.0);
 }
 
+// Real path (lossless element, no Robin face, no load): the chunk holds the
+// phase-scaled real matrix K_r = D^H K D with D = diag(1 on F, -i on I | -i on E,
+// 1 on H | -i on E-hat, 1 on H-hat).  With w_r = D_w^H (u, uhat_K),
+// r_r = D_t^H r = -B_r w_r and eta_K^2 = r_r^H G_r^{-1} r_r
+// = ||L_r^{-1} Re r_r||^2 + ||L_r^{-1} Im r_r||^2: Re r_r and Im r_r become
+// rows n_v and n_v + 1 of K_r (two more columns of the real factorisation).
+__global__ void __launch_bounds__(256) k_est_residual_real(Sizes S, const int* __restrict__ ids,
+                                                           const ElemOff* __restrict__ off,
+                                                           const int* __restrict__ sig, const RSig* __restrict__ rsig,
+                                                           const int32_t* __restrict__ rint,
+                                                           const double* __restrict__ rdbl,
+                                                           const int32_t* __restrict__ l2g,
+                                                           const double2* __restrict__ xfix,
+                                                           const double2* __restrict__ xhat,
+                                                           const double2* __restrict__ Zst,
+                                                           const double2* __restrict__ zst, double* K, double2* u_out) {
+  extern __shared__ double2 err_sh[];
+  const int slot = blockIdx.x, e = ids[slot];
+  const ElemOff of = off[e];
+  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h, m = nu + nh, nE = 3 * S.nL, nt = S.nt;
+  double2* w = err_sh;      // m: u_r, then uhat_r
+  double2* us = w + m;      // nh: uhat in the trace slots
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* A = K + (size_t)slot * N * N;
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) us[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
+  __syncthreads();
+  const double2* Ze = Zst + of.Z;
+  for (int i = wid; i < nu; i += nw) {
+    double yr = 0.0, yi = 0.0;
+    for (int j = lane; j < nh; j += 32) {
+      const double2 v = Ze[(size_t)i * nh + j], x = us[j];
+      yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
+      yi = fma(v.x, x.y, fma(v.y, x.x, yi));
+    }
+    yr = est_wsum(yr);
+    yi = est_wsum(yi);
+    if (lane == 0) {
+      const double2 zi = zst[of.u + i];
+      const double2 ui = make_double2(zi.x - yr, zi.y - yi);
+      if (u_out) u_out[of.u + i] = ui;
+      w[i] = i < nE ? make_double2(-ui.y, ui.x) : ui;  // times conj(-i) = i on E
+    }
+  }
+  const int sg = sig[e];
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) {
+    double2 a;
+    if (sg >= 0) {  // uhat_K = R uhat (slots)
+      const RSig R = rsig[sg];
+      const int32_t* rp = rint + R.rptr;
+      const int32_t* ri = rint + R.ridx;
+      const double* rw = rdbl + R.rw;
+      const int tt = t < nt ? t : t - nt, base = t < nt ? 0 : nt;
+      a = make_double2(0.0, 0.0);
+      for (int k = rp[tt]; k < rp[tt + 1]; ++k) {
+        const double2 x = us[base + ri[k]];
+        a.x = fma(rw[k], x.x, a.x);
+        a.y = fma(rw[k], x.y, a.y);
+      }
+    } else {
+      a = us[t];
+    }
+    w[nu + t] = t < nt ? make_double2(-a.y, a.x) : a;  // times i on E-hat
+  }
+  __syncthreads();
+  for (int i = wid; i < nv; i += nw) {
+    const double* col = A + (size_t)i * N + nv;
+    double rr = 0.0, ri2 = 0.0;
+    for (int j = lane; j < m; j += 32) {
+      const double b = col[j];
+      const double2 x = w[j];
+      rr = fma(b, x.x, rr);
+      ri2 = fma(b, x.y, ri2);
+    }
+    rr = est_wsum(rr);
+    ri2 = est_wsum(ri2);
+    if (lane == 0) {  // r_r = -B_r w_r
+      A[(size_t)nv + (size_t)i * N] = -rr;
+      A[(size_t)nv + 1 + (size_t)i * N] = -ri2;
+    }
+  }
+  if (threadIdx.x == 0) {
+    A[(size_t)nv + (size_t)nv * N] = 0.0;
+    A[(size_t)nv + 1 + (size_t)nv * N] = 0.0;
+    A[(size_t)nv + 1 + (size_t)(nv + 1) * N] = 0.0;
+  }
+}
+
+__global__ void k_est_eta_real(int count, int N, int nv, const int* __restrict__ ids, const double* __restrict__ K,
+                               double* eta2, int* nneg) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= count) return;
+  const double* A = K + (size_t)slot * N * N;
+  double v = -(A[(size_t)nv + (size_t)nv * N] + A[(size_t)nv + 1 + (size_t)(nv + 1) * N]);
+  if (v < 0.0) {
+    atomicAdd(nneg, 1);
+    v = 0.0;
+  }
+  eta2[ids[slot]] = v;
+}
+
 // eta_K^2 = -K[n_v][n_v] after the n_v pivots of G (negative values, possible
 // only through rounding when eta_K ~ 0, are clamped to 0 and counted).
 __global__ void k_est_eta(int count, int N, int nv, const int* __restrict__ ids, const double2* __restrict__ K,
@@ -1646,26 +1744,39 @@ int estimate_pass(dpg_handle* h, const double2* xhat, double2* u, double* eta2, 
     return DPG_ERR_STATE;
   }
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_est_neg, 0, sizeof(int), s));
-  for (const ChunkPlan& cp : h->est_plan) {
+  for (const ChunkPlan& cp : h->plan) {
     const Group& G = h->grp[cp.g];
     const Sizes& S = G.sz;
-    int rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, false, false, false, &cp);
+    int rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, false, false, cp.real, &cp);
     if (rc) return rc;
     const int* ids = cp.d_ids + cp.ids_off;
     const size_t sh = sizeof(double2) * (size_t)(S.n_u + 2 * S.n_h);
-    k_est_residual<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_sig, h->d_rsig, h->d_rint, h->d_rdbl, h->d_l2g,
-                                             h->d_xfix, xhat, h->d_Z, h->d_z, h->ws.K, u);
+    double* Kr = reinterpret_cast<double*>(h->ws.K);
+    const int extra = cp.real ? 2 : 1;  // columns after G: Re r, Im r (real path) or r
+    if (cp.real)
+      k_est_residual_real<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_sig, h->d_rsig, h->d_rint, h->d_rdbl,
+                                                    h->d_l2g, h->d_xfix, xhat, h->d_Z, h->d_z, Kr, u);
+    else
+      k_est_residual<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_sig, h->d_rsig, h->d_rint, h->d_rdbl, h->d_l2g,
+                                               h->d_xfix, xhat, h->d_Z, h->d_z, h->ws.K, u);
     if (h->factor_arith == DPG_FACTOR_TC_SPLIT) {
-      if (factor_tc_launch(true, cp.count, S.N, S.n_v + 1, S.n_v, S.n_v, ids, h->ws.K, h->d_status,
-                           h->d_status + h->ne, h->ws.Q, s) != DPG_OK) {
+      if (factor_tc_launch(!cp.real, cp.count, S.N, S.n_v + extra, S.n_v, S.n_v, ids,
+                           cp.real ? (void*)Kr : (void*)h->ws.K, h->d_status, h->d_status + h->ne, h->ws.Q,
+                           s) != DPG_OK) {
         h->err = "tensor-core factorisation launch failed";
         return DPG_ERR_CUDA;
       }
+    } else if (cp.real) {
+      k_factor<double><<<cp.count, 256, factor_smem<double>(), s>>>(S.N, S.n_v + extra, S.n_v, S.n_v, ids, Kr,
+                                                                    h->d_status);
     } else {
-      k_factor<double2><<<cp.count, 256, factor_smem<double2>(), s>>>(S.N, S.n_v + 1, S.n_v, S.n_v, ids, h->ws.K,
-                                                                      h->d_status);
+      k_factor<double2><<<cp.count, 256, factor_smem<double2>(), s>>>(S.N, S.n_v + extra, S.n_v, S.n_v, ids,
+                                                                      h->ws.K, h->d_status);
     }
-    k_est_eta<<<(cp.count + 127) / 128, 128, 0, s>>>(cp.count, S.N, S.n_v, ids, h->ws.K, eta2, h->d_est_neg);
+    if (cp.real)
+      k_est_eta_real<<<(cp.count + 127) / 128, 128, 0, s>>>(cp.count, S.N, S.n_v, ids, Kr, eta2, h->d_est_neg);
+    else
+      k_est_eta<<<(cp.count + 127) / 128, 128, 0, s>>>(cp.count, S.N, S.n_v, ids, h->ws.K, eta2, h->d_est_neg);
     h->launches += 3;
     DPG_CUDA_TRY(h, cudaGetLastError());
   }

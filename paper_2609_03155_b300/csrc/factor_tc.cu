@@ -39,12 +39,13 @@
 // Data flow per panel: the thread that solves a panel row also writes its
 // digits (FP16, in the K-major core-matrix layout of the MMA operands) to a
 // per-element scratch area; the trailing lower triangle is then covered by
-// 128-row x NJ-column tiles (NJ = 64 real, 32 complex): the 128-row operand is
+// 128-row x NJ-column tiles (NJ = 32 real, 16 complex): the 128-row operand is
 // copied from the scratch into shared memory once per row block, the NJ-row
 // operand per tile (or taken from the row block on diagonal tiles), one thread
 // issues the 28 (x 2 or x 8) MMAs into 7 (x 2) accumulators of tensor memory
-// (448 of 512 columns), and all threads run the epilogue.  Every wait on the
-// MMAs is bounded in time; on a timeout the CTA records it and returns.
+// (224 columns per tile, two tiles in flight), and all threads run the
+// epilogue, which overlaps the next tile's MMAs.  Every wait on the MMAs is
+// bounded in time; on a timeout the CTA records it and returns.
 #include <cuda_fp16.h>
 
 #include <cstdint>
@@ -66,14 +67,17 @@ constexpr unsigned long long FT_WAIT_NS = 100000000ull;  // a wait on the MMAs g
 template <typename T> struct TcCfg;
 template <> struct TcCfg<double> {
   static constexpr int K = 32;      // reals per panel row
-  static constexpr int NJ = 64;     // tile columns
+  static constexpr int NJ = 32;     // tile columns
   static constexpr int PARTS = 1;   // accumulator sets (real)
+  static_assert(NSL * (K / 8) * NJ <= 4 * FT_THREADS, "one J-operand copy is at most four per thread");
 };
 template <> struct TcCfg<double2> {
   static constexpr int K = 64;      // real parts, then imaginary parts
-  static constexpr int NJ = 32;
+  static constexpr int NJ = 16;
   static constexpr int PARTS = 2;   // real and imaginary part of P P^H
 };
+// tensor-memory columns of one tile's accumulators: 7 levels x NJ x parts = 224
+constexpr int BUFC = 224;
 
 __device__ __forceinline__ uint32_t ft_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -271,8 +275,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
   constexpr uint32_t LBO_I = TM * 16, LBO_J = NJ * 16;
   extern __shared__ __align__(1024) unsigned char ftsm[];
   unsigned char* sI = ftsm;
-  unsigned char* sJ = ftsm + NSL * ISLICE;
-  T* sD = reinterpret_cast<T*>(sJ + NSL * JSLICE);
+  unsigned char* sJ = ftsm + NSL * ISLICE;  // two buffers
+  T* sD = reinterpret_cast<T*>(sJ + 2 * NSL * JSLICE);
   int* s_exp = reinterpret_cast<int*>(sD + TB * TB);
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
@@ -397,108 +401,142 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
       }
     }
     __syncthreads();
-    // --- trailing update of the lower triangle of rows/cols [k1, nact) on the tensor cores
+    // --- trailing update of the lower triangle of rows/cols [k1, nact) on the
+    // tensor cores, pipelined over the tiles of a row block: the J operand of
+    // tile j + 1 is copied while the MMAs of tile j run, and the epilogue of
+    // tile j runs while the MMAs of tile j + 1 run (two accumulator sets in
+    // tensor memory, two J buffers; at most one MMA group in flight at a wait)
     for (int rhoI = 0; rhoI < R && ok; rhoI += TM) {
       // row block operand: slice t, chunk kc = 2 KB contiguous in the scratch
-      for (int q = tid; q < NSL * KC * (TM / 8) * 8; q += blockDim.x) {
-        const int r16 = q % TM, tk = q / TM;  // tk = t * KC + kc
-        const uint4 u = *reinterpret_cast<const uint4*>(Q + ((size_t)tk * RP + rhoI + r16) * 16);
-        const int t = tk / KC, kc = tk - t * KC;
-        *reinterpret_cast<uint4*>(sI + t * ISLICE + kc * LBO_I + r16 * 16) = u;
-      }
-      for (int rhoJ = 0; rhoJ < rhoI + TM && rhoJ < R && ok; rhoJ += NJ) {
-        const bool diag = rhoJ >= rhoI;
-        if (!diag) {
-          for (int q = tid; q < NSL * KC * NJ; q += blockDim.x) {
-            const int r16 = q % NJ, tk = q / NJ;
-            const uint4 u = *reinterpret_cast<const uint4*>(Q + ((size_t)tk * RP + rhoJ + r16) * 16);
-            const int t = tk / KC, kc = tk - t * KC;
-            *reinterpret_cast<uint4*>(sJ + t * JSLICE + kc * LBO_J + r16 * 16) = u;
-          }
+      // four independent loads per thread in flight
+      for (int q0 = tid; q0 < NSL * KC * TM; q0 += 4 * FT_THREADS) {
+        uint4 u[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int q = q0 + k * FT_THREADS, r16 = q % TM, tk = q / TM;  // tk = t * KC + kc
+          if (q < NSL * KC * TM) u[k] = *reinterpret_cast<const uint4*>(Q + ((size_t)tk * RP + rhoI + r16) * 16);
         }
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
-        if (tid == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t aI = ft_smem_u32(sI);
-          const uint32_t bJ = diag ? aI + (uint32_t)((rhoJ - rhoI) / 8 * 128) : ft_smem_u32(sJ);
-          const uint32_t bslice = diag ? ISLICE : JSLICE, lbo_b = diag ? LBO_I : LBO_J;
-          const uint32_t id_pos = ft_idesc(TM, NJ, false), id_neg = ft_idesc(TM, NJ, true);
-#pragma unroll 1
-          for (int s = 0; s < NLEV; ++s) {
-            const uint32_t dre = tmem + (uint32_t)(s * NJ);
-            const uint32_t dim = tmem + (uint32_t)((NLEV + s) * NJ);
-            uint32_t first_re = 0, first_im = 0;
-#pragma unroll 1
-            for (int a = 0; a <= s; ++a) {
-              const int b = s - a;
-              const uint32_t abase = aI + (uint32_t)(a * ISLICE), bbase = bJ + (uint32_t)(b * bslice);
-              // real part: all K steps of 16 (two 16-byte chunks each)
 #pragma unroll
-              for (int kk = 0; kk < KC / 2; ++kk) {
-                ft_mma(dre, ft_desc(abase + kk * 2 * LBO_I, LBO_I, 128), ft_desc(bbase + kk * 2 * lbo_b, lbo_b, 128),
-                       id_pos, first_re);
-                first_re = 1;
-              }
-              if (Cf::PARTS == 2) {
-                // imaginary part: Im P_I (Re P_J)^T - Re P_I (Im P_J)^T
+        for (int k = 0; k < 4; ++k) {
+          const int q = q0 + k * FT_THREADS, r16 = q % TM, tk = q / TM;
+          const int t = tk / KC, kc = tk - t * KC;
+          if (q < NSL * KC * TM) *reinterpret_cast<uint4*>(sI + t * ISLICE + kc * LBO_I + r16 * 16) = u[k];
+        }
+      }
+      const int nJ = (min(rhoI + TM, R) + NJ - 1) / NJ;
+      auto load_J = [&](int j) {
+        const int rhoJ = j * NJ;
+        if (rhoJ >= rhoI) return;  // diagonal tiles take B from the row block
+        unsigned char* dst = sJ + (j & 1) * (NSL * JSLICE);
+        // NSL KC NJ = 896 copies (real and complex): up to four per thread
+        uint4 u[4];
 #pragma unroll
-                for (int kk = 0; kk < KC / 4; ++kk) {
-                  ft_mma(dim, ft_desc(abase + (kk + KC / 4) * 2 * LBO_I, LBO_I, 128),
-                         ft_desc(bbase + kk * 2 * lbo_b, lbo_b, 128), id_pos, first_im);
-                  first_im = 1;
-                  ft_mma(dim, ft_desc(abase + kk * 2 * LBO_I, LBO_I, 128),
-                         ft_desc(bbase + (kk + KC / 4) * 2 * lbo_b, lbo_b, 128), id_neg, 1u);
-                }
+        for (int k = 0; k < 4; ++k) {
+          const int q = tid + k * FT_THREADS, r16 = q % NJ, tk = q / NJ;
+          if (q < NSL * KC * NJ) u[k] = *reinterpret_cast<const uint4*>(Q + ((size_t)tk * RP + rhoJ + r16) * 16);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int q = tid + k * FT_THREADS, r16 = q % NJ, tk = q / NJ;
+          const int t = tk / KC, kc = tk - t * KC;
+          if (q < NSL * KC * NJ) *reinterpret_cast<uint4*>(dst + t * JSLICE + kc * LBO_J + r16 * 16) = u[k];
+        }
+      };
+      auto issue = [&](int j) {  // one thread: all digit-pair MMAs of tile j, then one commit
+        const int rhoJ = j * NJ;
+        const bool diag = rhoJ >= rhoI;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t aI = ft_smem_u32(sI);
+        const uint32_t bJ = diag ? aI + (uint32_t)((rhoJ - rhoI) * 16) : ft_smem_u32(sJ + (j & 1) * (NSL * JSLICE));
+        const uint32_t bslice = diag ? ISLICE : JSLICE, lbo_b = diag ? LBO_I : LBO_J;
+        const uint32_t id_pos = ft_idesc(TM, NJ, false), id_neg = ft_idesc(TM, NJ, true);
+        const uint32_t buf = tmem + (uint32_t)((j & 1) * BUFC);
+#pragma unroll 1
+        for (int sl = 0; sl < NLEV; ++sl) {
+          const uint32_t dre = buf + (uint32_t)(sl * NJ);
+          const uint32_t dim = buf + (uint32_t)((NLEV + sl) * NJ);
+          uint32_t first_re = 0, first_im = 0;
+#pragma unroll 1
+          for (int a = 0; a <= sl; ++a) {
+            const int b = sl - a;
+            const uint32_t abase = aI + (uint32_t)(a * ISLICE), bbase = bJ + (uint32_t)(b * bslice);
+            // real part: all K steps of 16 (two 16-byte chunks each)
+#pragma unroll
+            for (int kk = 0; kk < KC / 2; ++kk) {
+              ft_mma(dre, ft_desc(abase + kk * 2 * LBO_I, LBO_I, 128), ft_desc(bbase + kk * 2 * lbo_b, lbo_b, 128),
+                     id_pos, first_re);
+              first_re = 1;
+            }
+            if (Cf::PARTS == 2) {
+              // imaginary part: Im P_I (Re P_J)^T - Re P_I (Im P_J)^T
+#pragma unroll
+              for (int kk = 0; kk < KC / 4; ++kk) {
+                ft_mma(dim, ft_desc(abase + (kk + KC / 4) * 2 * LBO_I, LBO_I, 128),
+                       ft_desc(bbase + kk * 2 * lbo_b, lbo_b, 128), id_pos, first_im);
+                first_im = 1;
+                ft_mma(dim, ft_desc(abase + kk * 2 * LBO_I, LBO_I, 128),
+                       ft_desc(bbase + (kk + KC / 4) * 2 * lbo_b, lbo_b, 128), id_neg, 1u);
               }
             }
           }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a));
         }
-        ok = __syncthreads_and(ft_mbar_wait(mbar_a, phase) ? 1 : 0) != 0;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a));
+      };
+      // epilogue of tile j: warp w reads accumulator lanes 32 (w % 4) .. + 31
+      // (tile rows) and 16 columns: real, column half w / 4; complex, all 16
+      // columns of the real (w < 4) or imaginary (w >= 4) part
+      auto epilogue = [&](int j) {
+        const int rhoJ = j * NJ;
+        const int qd = warp & 3, hsel = warp >> 2;
+        const int rho = rhoI + 32 * qd + lane;
+        const int row = k1 + rho;
+        const int cbase = (Cf::PARTS == 2) ? 0 : hsel * 16;
+        const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((j & 1) * BUFC) +
+                              ((Cf::PARTS == 2) ? (uint32_t)(hsel * NLEV * NJ) : 0u) + (uint32_t)cbase;
+        long long acc[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) acc[jj] = 0;
+#pragma unroll
+        for (int sl = 0; sl < NLEV; ++sl) {
+          uint32_t v[16];
+          ft_tmem_ld16(base + (uint32_t)(sl * NJ), v);
+          acc_level<Cf::PARTS == 1>(v, sl, acc);
+        }
+        if (rho < R) {
+          // all 16 loads of the trailing entries first, then the updates (the
+          // entries are distinct, so the loads need not wait on the stores)
+          const int er = s_exp[rho];
+          double* p0 = reinterpret_cast<double*>(&A[(size_t)row + (size_t)(k1 + rhoJ + cbase) * N]) +
+                       ((Cf::PARTS == 2) ? hsel : 0);
+          constexpr size_t cstride = (size_t)(sizeof(T) / sizeof(double));
+          double cv[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj)
+            if (rhoJ + cbase + jj <= rho) cv[jj] = p0[(size_t)jj * N * cstride];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int cr = rhoJ + cbase + jj;  // column, relative to k1
+            if (cr <= rho) p0[(size_t)jj * N * cstride] = cv[jj] - scaled_i64(acc[jj], er + s_exp[cr] - 54);
+          }
+        }
+      };
+      load_J(0);
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (tid == 0) issue(0);
+      for (int j = 0; j < nJ; ++j) {
+        if (j + 1 < nJ) load_J(j + 1);  // its buffer was read by the MMAs of tile j - 1 (completed)
+        asm volatile("fence.proxy.async.shared::cta;");
+        ok = __syncthreads_and(ft_mbar_wait(mbar_a, phase) ? 1 : 0) != 0;  // MMAs of tile j done
         phase ^= 1u;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // --- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 (tile
-        // rows); real: warps w / 4 = 0, 1 take column halves; complex: the
-        // real (w < 4) and imaginary (w >= 4) part of all NJ columns
-        {
-          const int qd = warp & 3, hsel = warp >> 2;
-          const int rho = rhoI + 32 * qd + lane;
-          const int row = k1 + rho;
-          const int er = s_exp[rho];
-          const uint32_t lane_addr = tmem + ((uint32_t)(32 * qd) << 16);
-          constexpr int NCOL = (Cf::PARTS == 2) ? NJ : NJ / 2;  // columns per warp
-          const int cbase = (Cf::PARTS == 2) ? 0 : hsel * (NJ / 2);
-          const uint32_t pbase = (Cf::PARTS == 2) ? (uint32_t)(hsel * NLEV * NJ) : 0u;
-#pragma unroll 1
-          for (int g = 0; g < NCOL / 16; ++g) {
-            long long acc[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0;
-#pragma unroll
-            for (int s = 0; s < NLEV; ++s) {
-              uint32_t v[16];
-              ft_tmem_ld16(lane_addr + pbase + (uint32_t)(s * NJ + cbase + 16 * g), v);
-              acc_level<Cf::PARTS == 1>(v, s, acc);
-            }
-            if (rho < R) {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int cr = rhoJ + cbase + 16 * g + j;  // column, relative to k1
-                if (cr <= rho) {
-                  const double dlt = scaled_i64(acc[j], er + s_exp[cr] - 54);
-                  double* p = reinterpret_cast<double*>(&A[(size_t)row + (size_t)(k1 + cr) * N]) +
-                              ((Cf::PARTS == 2) ? hsel : 0);
-                  *p -= dlt;
-                }
-              }
-            }
-          }
-        }
+        // the accumulator set of tile j + 1 was drained by the epilogue of tile j - 1
+        if (tid == 0 && j + 1 < nJ) issue(j + 1);
+        epilogue(j);
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
       }
+      __syncthreads();  // the row block operand is reloaded next
     }
     __syncthreads();
     k0 = k1;
@@ -529,9 +567,9 @@ size_t factor_tc_scratch_bytes(int N, bool cplx) {
 
 static size_t ft_smem(bool cplx) {
   if (cplx)
-    return (size_t)NSL * TM * TcCfg<double2>::K * 2 + (size_t)NSL * TcCfg<double2>::NJ * TcCfg<double2>::K * 2 +
+    return (size_t)NSL * TM * TcCfg<double2>::K * 2 + 2 * (size_t)NSL * TcCfg<double2>::NJ * TcCfg<double2>::K * 2 +
            sizeof(double2) * TB * TB;
-  return (size_t)NSL * TM * TcCfg<double>::K * 2 + (size_t)NSL * TcCfg<double>::NJ * TcCfg<double>::K * 2 +
+  return (size_t)NSL * TM * TcCfg<double>::K * 2 + 2 * (size_t)NSL * TcCfg<double>::NJ * TcCfg<double>::K * 2 +
          sizeof(double) * TB * TB;
 }
 

@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "DPG elements/s (local solve+η_K) & CG time-to-1e-10; mixed/batched vs FP64"
 UNIT = "elements/s"
 CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3, "fp64-bjacobi": 4, "ir-bjacobi": 5,
-            "ir-bjacobi-half": 5 | 16}
+            "ir-bjacobi-half": 5 | 16, "ir64v-bjacobi": 5 | 32, "ir64v": 1 | 32,
+            "dw": 64, "dw-bjacobi": 64 | 4}
 PRECISIONS = {"fp64": 0, "tf32": 1, "3xtf32": 2}
 
 

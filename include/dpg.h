@@ -95,7 +95,8 @@ enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2
  * error against FP64 is a reported quantity, not a parity bound. */
 enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
-enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8, DPG_CG_HALF = 16 };
+enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8, DPG_CG_HALF = 16,
+       DPG_CG_IR_V64 = 32, DPG_CG_DW = 64 };
 enum { DPG_FLAG_ADJOINT = 1 };
 /* Arithmetic of the element factorisation's trailing updates (dpg_set_factor_arith). */
 enum { DPG_FACTOR_FP64 = 0, DPG_FACTOR_TC_SPLIT = 1 };
@@ -203,6 +204,17 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * Hermitian half storage of the FP32 matrix (each pair of entity blocks once;
  * the upper blocks are applied as conjugate transposes through per-block
  * partial sums gathered in a fixed order, so results stay deterministic).
+ * DPG_CG_IR_V64 may be or-ed to DPG_CG_IR_FP32 (not with DPG_CG_HALF): the
+ * inner solves keep their vectors, recurrences and reductions in FP64 and
+ * only the matrix (values and products) in FP32, so an inner solve converges
+ * like FP64 CG on the FP32-rounded matrix and can go to a smaller inner_rtol.
+ * DPG_CG_DW (alone or with DPG_CG_BLOCK_JACOBI): CG with FP64 vectors,
+ * recurrences and reductions whose matrix, direction vector and block
+ * inverses are double-word FP32 pairs (hi + lo, about 48 bits), every SpMV and
+ * preconditioner product and sum formed with error-free transformations
+ * (Dekker's two-product by FMA, Knuth's two-sum) on the FP32 pipes: FP64-class
+ * accuracy (the convergence of FP64 CG) at the speed of the memory system
+ * instead of the FP64 pipe.  The stopping test is on the FP64 residual.
  * DPG_CG_X0 may be or-ed too: start from the x passed in (resume a stopped
  * solve, or warm-start from a nearby problem's solution) instead of x0 = 0.
  * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or

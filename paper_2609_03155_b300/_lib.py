@@ -21,6 +21,8 @@ DPG_CG_FP64, DPG_CG_IR_FP32, DPG_CG_JACOBI, DPG_CG_BLOCK_JACOBI = 0, 1, 2, 4
 DPG_PREC_FP64, DPG_PREC_TF32, DPG_PREC_3XTF32 = 0, 1, 2
 DPG_CG_X0 = 8
 DPG_CG_HALF = 16
+DPG_CG_IR_V64 = 32
+DPG_CG_DW = 64
 DPG_FLAG_ADJOINT = 1
 DPG_FACTOR_FP64, DPG_FACTOR_TC_SPLIT = 0, 1
 

@@ -39,7 +39,8 @@ static void free_all(dpg_handle* h) {
                   h->d_dinv,  h->d_dinv32, h->d_L1, h->d_u, h->d_zg, h->d_gc, h->d_lam, h->d_rhs_adj,
                   h->d_Pk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_binv_ptr, h->d_binv, h->d_binv32,
                   h->d_zv, h->d_z32, h->d_d64, h->ws.Q, h->d_est_neg,
-                  h->d_rowptr_h, h->d_toff, h->d_rev_ptr, h->d_rev_off, h->d_val32h, h->d_T};
+                  h->d_rowptr_h, h->d_toff, h->d_rev_ptr, h->d_rev_off, h->d_val32h, h->d_T,
+                  h->d_valdw, h->d_pdw, h->d_binvdw};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }

@@ -207,6 +207,11 @@ struct dpg_handle {
   int64_t* d_rev_off = nullptr;     // rev_len: T offsets of the segments that belong to block b's rows
   float2* d_val32h = nullptr;       // nnz_h
   float2* d_T = nullptr;            // t_len
+  // double-word (FP32 pair) copies for the DW solver mode
+  float4* d_valdw = nullptr;        // nnz
+  float4* d_pdw = nullptr;          // n
+  float4* d_binvdw = nullptr;       // block inverses
+  bool have_valdw = false, have_binvdw = false;
   bool have_elements = false, have_system = false, have_val32 = false, have_dinv = false;
   double* d_dinv = nullptr;     // inverse diagonal (Jacobi)
   float* d_dinv32 = nullptr;

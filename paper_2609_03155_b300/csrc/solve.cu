@@ -89,6 +89,8 @@ int assemble_system(dpg_handle* h, cudaStream_t s) {
   h->have_system = true;
   h->have_val32 = false;
   h->have_val32h = false;
+  h->have_valdw = false;
+  h->have_binvdw = false;
   h->have_dinv = false;
   h->have_binv = false;
   return DPG_OK;
@@ -338,9 +340,11 @@ __device__ __forceinline__ void block_precond(const SysView& S, int b, int preco
 // y_row = sum over the stored prefix (lower blocks and the diagonal block) of
 // A[row][c] x_c, into y; and the conjugate-transpose partial sums of the
 // strictly lower part, T[toff[a] + q] = sum_rows conj(A[row][q]) x_row, one
-// per prefix position q < n_low(a).  Positions are taken in windows of
-// 32 x HW per lane pass (lane owns q = window + lane + 32 k).
-constexpr int HW = 8;
+// per prefix position q < n_low(a).  All rows of a block share its column
+// list, so each lane gathers its x_c once per window of 32 x HW positions
+// (lane owns q = window + lane + 32 k) and every row then streams only its
+// values; rows go in pairs so that two reductions are in flight.
+constexpr int HW = 4;
 template <typename V, typename Mv>
 __device__ __forceinline__ void half_block_lower(const SysView& S, int a, const Mv* __restrict__ valh,
                                                  const V* __restrict__ x, V* y, V* T) {
@@ -349,35 +353,52 @@ __device__ __forceinline__ void half_block_lower(const SysView& S, int a, const 
   const int4 B = S.blk[a];
   const int wl = B.w, Wh = B.w + B.y;
   const int32_t* c = S.cols + S.colptr[a];
+  const int64_t* rp = S.rowptr_h + B.x;
   for (int q0 = 0; q0 < Wh; q0 += 32 * HW) {
-    R tr[HW], ti[HW];
+    R xr[HW], xi[HW], tr[HW], ti[HW];
 #pragma unroll
-    for (int k = 0; k < HW; ++k) tr[k] = ti[k] = 0;
-    for (int i = 0; i < B.y; ++i) {
-      const int64_t row = B.x + i;
-      const Mv* v = valh + S.rowptr_h[row];
-      const V xi = x[row];
-      R ar = 0, ai = 0;
+    for (int k = 0; k < HW; ++k) {
+      const int q = q0 + lane + 32 * k;
+      const V xv = q < Wh ? x[c[q]] : mkv(0.0f, 0.0f, (V*)nullptr);
+      xr[k] = (R)xv.x;
+      xi[k] = (R)xv.y;
+      tr[k] = ti[k] = 0;
+    }
+    for (int i = 0; i < B.y; i += 2) {
+      const bool two = i + 1 < B.y;
+      const Mv* v0 = valh + rp[i];
+      const Mv* v1 = valh + rp[two ? i + 1 : i];
+      const V x0 = x[B.x + i];
+      const V x1 = two ? x[B.x + i + 1] : mkv(0.0f, 0.0f, (V*)nullptr);
+      R a0r = 0, a0i = 0, a1r = 0, a1i = 0;
 #pragma unroll
       for (int k = 0; k < HW; ++k) {
         const int q = q0 + lane + 32 * k;
         if (q < Wh) {
-          const Mv av = v[q];
-          const V xc = x[c[q]];
-          ar = fma(av.x, (R)xc.x, fma(-av.y, (R)xc.y, ar));
-          ai = fma(av.x, (R)xc.y, fma(av.y, (R)xc.x, ai));
-          if (q < wl) {  // conj(A[row][q]) x_row
-            tr[k] = fma(av.x, (R)xi.x, fma(av.y, (R)xi.y, tr[k]));
-            ti[k] = fma(av.x, (R)xi.y, fma(-av.y, (R)xi.x, ti[k]));
+          const Mv u0 = v0[q];
+          const Mv u1 = two ? v1[q] : Mv{0, 0};
+          a0r = fma(u0.x, xr[k], fma(-u0.y, xi[k], a0r));
+          a0i = fma(u0.x, xi[k], fma(u0.y, xr[k], a0i));
+          a1r = fma(u1.x, xr[k], fma(-u1.y, xi[k], a1r));
+          a1i = fma(u1.x, xi[k], fma(u1.y, xr[k], a1i));
+          if (q < wl) {  // conj(A[row][q]) x_row for both rows
+            tr[k] = fma(u0.x, (R)x0.x, fma(u0.y, (R)x0.y, tr[k]));
+            ti[k] = fma(u0.x, (R)x0.y, fma(-u0.y, (R)x0.x, ti[k]));
+            tr[k] = fma(u1.x, (R)x1.x, fma(u1.y, (R)x1.y, tr[k]));
+            ti[k] = fma(u1.x, (R)x1.y, fma(-u1.y, (R)x1.x, ti[k]));
           }
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        ar += __shfl_xor_sync(0xffffffffu, ar, o);
-        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        a0r += __shfl_xor_sync(0xffffffffu, a0r, o);
+        a0i += __shfl_xor_sync(0xffffffffu, a0i, o);
+        a1r += __shfl_xor_sync(0xffffffffu, a1r, o);
+        a1i += __shfl_xor_sync(0xffffffffu, a1i, o);
       }
-      if (lane == 0) {
+      if (lane < 2 && (lane == 0 || two)) {
+        const int64_t row = B.x + i + lane;
+        const R ar = lane ? a1r : a0r, ai = lane ? a1i : a0i;
         if (q0 == 0) {
           y[row] = mkv(ar, ai, (V*)nullptr);
         } else {
@@ -397,12 +418,247 @@ __device__ __forceinline__ void half_block_lower(const SysView& S, int a, const 
   }
 }
 
+// ------------------------------------------------- double-word FP32 arithmetic --
+// A double-word (DW) number is an unevaluated sum hi + lo of two FP32 values
+// (|lo| <= ulp(hi) / 2), about 48 significant bits.  The DW solver mode keeps
+// the matrix, the direction vector p and the block inverses as DW pairs and
+// forms every product and sum of the SpMV and the preconditioner with the
+// error-free transformations of Dekker (1971) and Knuth: the product of two
+// FP32 values is exact as p + fma(a, b, -p); the sum as TwoSum.  Only the
+// FP32 pipes do this work (B300 runs FP64 FMA at 1/64 of FP32), while the
+// values carry FP64-class accuracy, so CG keeps the convergence of FP64 CG.
+__device__ __forceinline__ void dw_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (sh, sl) += (ah + al) (xh + xl), the al xl term dropped (below 2^-46 relative).
+__device__ __forceinline__ void dw_mac(float& sh, float& sl, float ah, float al, float xh, float xl) {
+  const float pr = ah * xh;
+  const float pe = fmaf(ah, xh, -pr);  // exact error of the product
+  const float lo = fmaf(ah, xl, fmaf(al, xh, pe));
+  float t, e;
+  dw_two_sum(sh, pr, t, e);
+  sh = t;
+  sl += e + lo;
+}
+
+__device__ __forceinline__ void dw_warp_sum(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float t, e;
+    dw_two_sum(h, oh, t, e);
+    h = t;
+    l += e + ol;
+  }
+}
+
+__device__ __forceinline__ float4 dw_split(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+}
+
+// y_row = (A p)_row with DW matrix values (re_hi, im_hi, re_lo, im_lo) and the
+// DW copy of p; FP64 result.
+__device__ __forceinline__ double2 row_spmv_dw(const SysView& S, int64_t row, const float4* __restrict__ val,
+                                               const float4* __restrict__ pdw) {
+  const int lane = threadIdx.x & 31;
+  const int b = S.row2blk[row];
+  const int W = S.blk[b].z;
+  const int32_t* c = S.cols + S.colptr[b];
+  const float4* v = val + S.rowptr[row];
+  float rh0 = 0, rl0 = 0, ih0 = 0, il0 = 0, rh1 = 0, rl1 = 0, ih1 = 0, il1 = 0;
+  int k = lane;
+  for (; k + 32 < W; k += 64) {  // two independent column chains per lane
+    const float4 a0 = v[k], a1 = v[k + 32];
+    const float4 x0 = pdw[c[k]], x1 = pdw[c[k + 32]];
+    dw_mac(rh0, rl0, a0.x, a0.z, x0.x, x0.z);
+    dw_mac(rh0, rl0, -a0.y, -a0.w, x0.y, x0.w);
+    dw_mac(ih0, il0, a0.x, a0.z, x0.y, x0.w);
+    dw_mac(ih0, il0, a0.y, a0.w, x0.x, x0.z);
+    dw_mac(rh1, rl1, a1.x, a1.z, x1.x, x1.z);
+    dw_mac(rh1, rl1, -a1.y, -a1.w, x1.y, x1.w);
+    dw_mac(ih1, il1, a1.x, a1.z, x1.y, x1.w);
+    dw_mac(ih1, il1, a1.y, a1.w, x1.x, x1.z);
+  }
+  if (k < W) {
+    const float4 a0 = v[k];
+    const float4 x0 = pdw[c[k]];
+    dw_mac(rh0, rl0, a0.x, a0.z, x0.x, x0.z);
+    dw_mac(rh0, rl0, -a0.y, -a0.w, x0.y, x0.w);
+    dw_mac(ih0, il0, a0.x, a0.z, x0.y, x0.w);
+    dw_mac(ih0, il0, a0.y, a0.w, x0.x, x0.z);
+  }
+  float t, e;
+  dw_two_sum(rh0, rh1, t, e);
+  rh0 = t;
+  rl0 += e + rl1;
+  dw_two_sum(ih0, ih1, t, e);
+  ih0 = t;
+  il0 += e + il1;
+  dw_warp_sum(rh0, rl0);
+  dw_warp_sum(ih0, il0);
+  return make_double2((double)rh0 + (double)rl0, (double)ih0 + (double)il0);
+}
+
+// z = M^{-1} r on the rows of block b with the DW block inverses (conj of
+// Binv[i][j] read contiguously as row j); rs: this warp's DW staging of r.
+__device__ __forceinline__ void block_precond_dw(const SysView& S, int b, const double2* __restrict__ r, double2* z,
+                                                 const float4* __restrict__ binv, float4* rs, double& rr, double& rz) {
+  const int lane = threadIdx.x & 31;
+  const int4 B = S.blk[b];
+  for (int i = lane; i < B.y; i += 32) rs[i] = dw_split(r[B.x + i]);
+  __syncwarp();
+  const float4* Bi = binv + S.binv_ptr[b];
+  for (int i0 = 0; i0 < B.y; i0 += 32) {
+    const int i = i0 + lane;
+    if (i < B.y) {
+      float zrh = 0, zrl = 0, zih = 0, zil = 0;
+      for (int j = 0; j < B.y; ++j) {
+        const float4 a = Bi[(size_t)j * B.y + i];  // conj of Binv[i][j]
+        const float4 rj = rs[j];
+        // z += conj(a) r_j: re = a.re r.re + a.im r.im, im = a.re r.im - a.im r.re
+        dw_mac(zrh, zrl, a.x, a.z, rj.x, rj.z);
+        dw_mac(zrh, zrl, a.y, a.w, rj.y, rj.w);
+        dw_mac(zih, zil, a.x, a.z, rj.y, rj.w);
+        dw_mac(zih, zil, -a.y, -a.w, rj.x, rj.z);
+      }
+      const double2 zv = make_double2((double)zrh + (double)zrl, (double)zih + (double)zil);
+      const double2 ri = r[B.x + i];
+      z[B.x + i] = zv;
+      rr += ri.x * ri.x + ri.y * ri.y;
+      rz += ri.x * zv.x + ri.y * zv.y;
+    }
+  }
+  __syncwarp();
+}
+
+// One whole CG solve of A d = r0 (d = 0 at entry, r holds r0 at entry) in the
+// DW mode: FP64 vectors, recurrences and reductions; DW matrix, p copy and
+// block inverses (precond 2) or none (precond 0).
+__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_dw(SysView S, const float4* __restrict__ val, double2* x,
+                                                         double2* r, double2* p, float4* pdw, double2* Ap, double2* z,
+                                                         int precond, const float4* __restrict__ binv, double* red,
+                                                         CgState* st) {
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  float4* rs = reinterpret_cast<float4*>(cg_smem) + (threadIdx.x >> 5) * S.dmax;
+  const int G = gridDim.x;
+  double* redA = red;
+  double* redB0 = red + G;
+  double* redB1 = red + 2 * G;
+  const int warps = G * (CG_THREADS / 32);
+  const int gw = blockIdx.x * (CG_THREADS / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  unsigned int gen = *((volatile unsigned int*)&st->bar[1]);
+  const double tol2 = st->tol2;
+  const int max_iter = st->max_iter;
+  double rr0 = 0, rz0 = 0;
+  for (int b = gw; b < S.nblk; b += warps) {
+    const int4 B = S.blk[b];
+    if (precond == 2) {
+      block_precond_dw(S, b, r, z, binv, rs, rr0, rz0);
+    } else {
+      for (int i = lane; i < B.y; i += 32) {
+        const double2 ri = r[B.x + i];
+        z[B.x + i] = ri;
+        rr0 += ri.x * ri.x + ri.y * ri.y;
+        rz0 += ri.x * ri.x + ri.y * ri.y;
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < B.y; i += 32) {
+      const double2 zi = z[B.x + i];
+      p[B.x + i] = zi;
+      pdw[B.x + i] = dw_split(zi);
+      x[B.x + i] = make_double2(0.0, 0.0);
+    }
+  }
+  block_partial(rr0, rz0, redB0, redB1);
+  if (!grid_barrier(st, gen)) return;
+  double rr, rz;
+  grid_total(redB0, redB1, rr, rz);
+  int it = 0;
+  bool done = rr <= tol2;
+  while (!done && it < max_iter) {
+    double pap = 0;
+    for (int64_t row = gw; row < S.n; row += warps) {
+      const double2 y = row_spmv_dw(S, row, val, pdw);
+      if (lane == 0) {
+        Ap[row] = y;
+        const double2 pr = p[row];
+        pap += pr.x * y.x + pr.y * y.y;
+      }
+    }
+    block_partial(pap, 0.0, redA, nullptr);
+    if (!grid_barrier(st, gen)) return;
+    double tpap, dummy;
+    grid_total(redA, nullptr, tpap, dummy);
+    const double alpha = rz / tpap;
+    double rr2 = 0, rz2 = 0;
+    for (int b = gw; b < S.nblk; b += warps) {
+      const int4 B = S.blk[b];
+      for (int i = lane; i < B.y; i += 32) {
+        const int64_t row = B.x + i;
+        double2 xv = x[row], rv = r[row];
+        const double2 pv = p[row], av = Ap[row];
+        xv.x = fma(alpha, pv.x, xv.x);
+        xv.y = fma(alpha, pv.y, xv.y);
+        rv.x = fma(-alpha, av.x, rv.x);
+        rv.y = fma(-alpha, av.y, rv.y);
+        x[row] = xv;
+        r[row] = rv;
+      }
+      __syncwarp();
+      if (precond == 2) {
+        block_precond_dw(S, b, r, z, binv, rs, rr2, rz2);
+      } else {
+        for (int i = lane; i < B.y; i += 32) {
+          const double2 ri = r[B.x + i];
+          z[B.x + i] = ri;
+          rr2 += ri.x * ri.x + ri.y * ri.y;
+          rz2 += ri.x * ri.x + ri.y * ri.y;
+        }
+      }
+    }
+    block_partial(rr2, rz2, redB0, redB1);
+    if (!grid_barrier(st, gen)) return;
+    double trr, trz;
+    grid_total(redB0, redB1, trr, trz);
+    const double beta = trz / rz;
+    rz = trz;
+    rr = trr;
+    ++it;
+    if (rr <= tol2) break;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)G * blockDim.x) {
+      const double2 zv = z[i];
+      double2 pv = p[i];
+      pv.x = fma(beta, pv.x, zv.x);
+      pv.y = fma(beta, pv.y, zv.y);
+      p[i] = pv;
+      pdw[i] = dw_split(pv);
+    }
+    if (!grid_barrier(st, gen)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->iters = it;
+    st->rr = rr;
+    st->rz = rz;
+  }
+}
+
+__global__ void k_to_dw(int64_t n, const double2* __restrict__ a, float4* b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = dw_split(a[i]);
+}
+
 // One whole CG solve of A x = r0 (x = 0 at entry, r holds r0 at entry).
 // V: precision of the vectors and recurrences; Mv: precision of the stored
 // matrix and of the SpMV products (FP32 values with FP64 recurrences keeps the
 // convergence rate of FP64 CG at the bandwidth of an FP32 matrix).
 template <typename V, typename Mv, bool HALF>
-__global__ void __launch_bounds__(CG_THREADS, 5) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
+__global__ void __launch_bounds__(CG_THREADS, HALF ? 4 : 5) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
                                                              V* Ap, V* z, int precond,
                                                              const typename RealOf<V>::T* __restrict__ dinv,
                                                              const V* __restrict__ binv, double* red, CgState* st,
@@ -450,7 +706,20 @@ __global__ void __launch_bounds__(CG_THREADS, 5) k_cg_persistent(SysView S, cons
         for (int i = threadIdx.x & 31; i < B.y; i += 32) {
           const int64_t row = B.x + i;
           V yv = Ap[row];
-          for (int64_t k = k0; k < k1; ++k) {
+          int64_t k = k0;
+          for (; k + 3 < k1; k += 4) {  // four independent loads in flight, summed in list order
+            const int64_t o0 = S.rev_off[k], o1 = S.rev_off[k + 1], o2 = S.rev_off[k + 2], o3 = S.rev_off[k + 3];
+            const V t0 = T[o0 + i], t1 = T[o1 + i], t2 = T[o2 + i], t3 = T[o3 + i];
+            yv.x += t0.x;
+            yv.y += t0.y;
+            yv.x += t1.x;
+            yv.y += t1.y;
+            yv.x += t2.x;
+            yv.y += t2.y;
+            yv.x += t3.x;
+            yv.y += t3.y;
+          }
+          for (; k < k1; ++k) {
             const V t = T[S.rev_off[k] + i];
             yv.x += t.x;
             yv.y += t.y;
@@ -660,8 +929,8 @@ static int ensure_buf(dpg_handle* h, void** p, size_t bytes) {
   return DPG_OK;
 }
 
-template <typename V, typename Mv, bool HALF>
-static int persistent_grid(dpg_handle* h, int* grid, size_t smem) {
+// Grid of a persistent cooperative CG kernel: every block resident (at most 8 per SM).
+static int persistent_grid(dpg_handle* h, const void* kernel, size_t smem, int* grid) {
   int dev = 0, sms = 0, per = 0, coop = 0;
   DPG_CUDA_TRY(h, cudaGetDevice(&dev));
   DPG_CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -670,23 +939,19 @@ static int persistent_grid(dpg_handle* h, int* grid, size_t smem) {
     h->err = "device does not support cooperative launches";
     return DPG_ERR_UNSUPPORTED;
   }
-  DPG_CUDA_TRY(h,
-               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<V, Mv, HALF>, CG_THREADS, smem));
+  if (smem > 48 * 1024)
+    DPG_CUDA_TRY(h, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DPG_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, CG_THREADS, smem));
   *grid = std::max(1, std::min(per, 8) * sms);
   return DPG_OK;
 }
 
-// One persistent solve of A d = r0 (d = 0 at entry; r holds r0 at entry).
-template <typename V, typename Mv, bool HALF>
-static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
-                          const typename RealOf<V>::T* dinv, const V* binv, double tol2, int max_iter,
-                          cudaStream_t s, int* iters, double* rr_out, V* T = nullptr) {
+// One cooperative launch of a persistent CG kernel whose last argument is the
+// CgState; the state is initialised before and read back after the solve.
+static int launch_persistent(dpg_handle* h, const void* kernel, void** args, CgState** st_arg, size_t smem,
+                             double tol2, int max_iter, bool fp32, cudaStream_t s, int* iters, double* rr_out) {
   int grid = 0;
-  const size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
-  if (smem > 48 * 1024)
-    DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_cg_persistent<V, Mv, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-  int rc = persistent_grid<V, Mv, HALF>(h, &grid, smem);
+  int rc = persistent_grid(h, kernel, smem, &grid);
   if (rc) return rc;
   CgState host{};
   host.tol2 = tol2;
@@ -694,18 +959,15 @@ static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap,
   host.wait_ns = (unsigned long long)h->wait_ns;
   host.hold = h->wait_hold ? 1 : 0;
   CgState* st = static_cast<CgState*>(h->d_cgstate);
+  *st_arg = st;
   DPG_CUDA_TRY(h, cudaMemcpyAsync(st, &host, sizeof(CgState), cudaMemcpyHostToDevice, s));
-  SysView S = sys_view(h);
-  double* red = h->d_red;
-  void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st, &T};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->timing) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  DPG_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_cg_persistent<V, Mv, HALF>, dim3(grid), dim3(CG_THREADS), args,
-                                              smem, s));
+  DPG_CUDA_TRY(h, cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(CG_THREADS), args, smem, s));
   h->launches += 1;
   if (h->timing) cudaEventRecord(e1, s);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(&host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
@@ -718,7 +980,7 @@ static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap,
     h->cgk_ms += ms;
     h->cgk_launches += 1;
     h->cgk_iters += host.iters;
-    if (sizeof(Mv) == sizeof(float2)) h->cgk_fp32 = true;
+    if (fp32) h->cgk_fp32 = true;
   }
   if (host.status != 0) {
     h->err = "a grid barrier of the CG kernel timed out";
@@ -727,6 +989,35 @@ static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap,
   *iters = host.iters;
   *rr_out = host.rr;
   return DPG_OK;
+}
+
+// One persistent solve of A d = r0 (d = 0 at entry; r holds r0 at entry).
+template <typename V, typename Mv, bool HALF>
+static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
+                          const typename RealOf<V>::T* dinv, const V* binv, double tol2, int max_iter,
+                          cudaStream_t s, int* iters, double* rr_out, V* T = nullptr) {
+  const size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
+  SysView S = sys_view(h);
+  double* red = h->d_red;
+  CgState* st = nullptr;
+  void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st, &T};
+  return launch_persistent(h, (const void*)k_cg_persistent<V, Mv, HALF>, args, &st, smem, tol2, max_iter,
+                           sizeof(Mv) == sizeof(float2), s, iters, rr_out);
+}
+
+// The same in the double-word mode (k_cg_dw).
+static int run_dw(dpg_handle* h, double2* x, double2* r, int precond, double tol2, int max_iter, cudaStream_t s,
+                  int* iters, double* rr_out) {
+  const size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(float4);
+  SysView S = sys_view(h);
+  const float4* val = h->d_valdw;
+  double2 *p = h->d_p, *Ap = h->d_Ap, *z = h->d_zv;
+  float4* pdw = h->d_pdw;
+  const float4* binv = h->d_binvdw;
+  double* red = h->d_red;
+  CgState* st = nullptr;
+  void* args[] = {&S, &val, &x, &r, &p, &pdw, &Ap, &z, &precond, &binv, &red, &st};
+  return launch_persistent(h, (const void*)k_cg_dw, args, &st, smem, tol2, max_iter, false, s, iters, rr_out);
 }
 
 static int residual(dpg_handle* h, const double2* x, const double2* b, double2* r, cudaStream_t s, double* rr) {
@@ -845,7 +1136,8 @@ __global__ void __launch_bounds__(256) k_to_f32_half(SysView S, const double2* _
 // x, r, z; the direction update reads z, p and writes p): 13 vector passes.
 int64_t cg_bytes_per_iteration(const dpg_handle* h, int mode) {
   const bool ir = (mode & DPG_CG_IR_FP32) != 0;
-  const int64_t mb = ir ? 8 : 16, vb = ir ? 8 : 16;
+  const bool v64 = ir && (mode & DPG_CG_IR_V64);
+  const int64_t mb = ir ? 8 : 16, vb = (ir && !v64) ? 8 : 16;  // DW: 16 B values (two FP32 pairs), FP64 vectors
   int64_t ncol = (int64_t)h->cols.size();
   int64_t bytes = 0;
   if (ir && (mode & DPG_CG_HALF)) {
@@ -881,7 +1173,10 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     h->err = "bad CG arguments";
     return DPG_ERR_ARG;
   }
-  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0 | DPG_CG_HALF) ||
+  if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0 | DPG_CG_HALF | DPG_CG_IR_V64 |
+               DPG_CG_DW) ||
+      ((mode & DPG_CG_HALF) && (mode & DPG_CG_IR_V64)) ||
+      ((mode & DPG_CG_DW) && (mode & (DPG_CG_IR_FP32 | DPG_CG_JACOBI))) ||
       ((mode & DPG_CG_JACOBI) && (mode & DPG_CG_BLOCK_JACOBI))) {
     h->err = "unknown CG mode";
     return DPG_ERR_ARG;
@@ -905,7 +1200,13 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     rc |= ensure_buf(h, (void**)&h->d_z32, sizeof(float2) * n);
   }
   if (rc) return DPG_ERR_NOMEM;
-  const bool half = ir && (mode & DPG_CG_HALF);
+  const bool half = ir && (mode & DPG_CG_HALF) && !(mode & DPG_CG_IR_V64);
+  const bool dw = (mode & DPG_CG_DW) != 0;
+  if (dw) {
+    rc |= ensure_buf(h, (void**)&h->d_valdw, sizeof(float4) * h->nnz);
+    rc |= ensure_buf(h, (void**)&h->d_pdw, sizeof(float4) * n);
+    if (rc) return DPG_ERR_NOMEM;
+  }
   if (half) {
     rc = build_half(h);
     if (rc) return rc;
@@ -921,6 +1222,20 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
   if (precond) {
     rc = prepare_preconditioner(h, s);
     if (rc) return rc;
+  }
+  if (dw && !h->have_valdw) {
+    k_to_dw<<<1184, 256, 0, s>>>(h->nnz, h->d_val, h->d_valdw);
+    h->launches += 1;
+    h->have_valdw = true;
+  }
+  if (dw && precond == 2 && !h->have_binvdw) {
+    int64_t inv = 0;
+    for (const int4& B : h->blk) inv += (int64_t)B.y * B.y;
+    rc = ensure_buf(h, (void**)&h->d_binvdw, sizeof(float4) * inv);
+    if (rc) return rc;
+    k_to_dw<<<1184, 256, 0, s>>>(inv, h->d_binv, h->d_binvdw);
+    h->launches += 1;
+    h->have_binvdw = true;
   }
   if (half && !h->have_val32h) {
     k_to_f32_half<<<1184, 256, 0, s>>>(sys_view(h), h->d_val, h->d_val32h);
@@ -958,7 +1273,20 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
   while (!conv && total_iters < max_iter && outer < max_outer) {
     int it = 0;
     double rr = 0;
-    if (ir) {
+    if (dw) {
+      const double itol = 0.5 * tol;
+      rc = run_dw(h, h->d_d64, h->d_r, precond, itol * itol, max_iter - total_iters, s, &it, &rr);
+      if (rc) return rc;
+      k_add_correction64<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_d64);
+    } else if (ir && (mode & DPG_CG_IR_V64)) {
+      // inner CG over the FP32 matrix (FP32 products) with FP64 vectors and recurrences
+      const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
+      rc = run_persistent<double2, float2, false>(h, h->d_val32, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond,
+                                                  h->d_dinv, h->d_binv, itol * itol, max_iter - total_iters, s, &it,
+                                                  &rr);
+      if (rc) return rc;
+      k_add_correction64<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_d64);
+    } else if (ir) {
       const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
       k_to_f32<<<1184, 256, 0, s>>>((int64_t)n, h->d_r, h->d_r32);
       h->launches += 1;

@@ -183,9 +183,10 @@ def test_te10_waveguide_field_error(dpg_mod):
     d.destroy()
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 1 | 16, 5 | 16])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 1 | 16, 5 | 16, 5 | 32, 64, 64 | 4])
 def test_cg_modes_match_fp64(dpg_mod, mode):
-    """IR (FP32 inner, full or Hermitian half storage), Jacobi and entity-block Jacobi reach the plain FP64 CG solution."""
+    """IR (FP32 inner: full or Hermitian half storage, FP32 or FP64 inner vectors), Jacobi, entity-block Jacobi
+    and the double-word (FP32 pair) solver reach the plain FP64 CG solution."""
     mesh = _lossy_jittered(1, n=(2, 2, 2))
     d = dpg_mod.DPG(mesh)
     d.element_batch()

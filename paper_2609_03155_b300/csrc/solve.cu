@@ -471,9 +471,10 @@ __device__ __forceinline__ double2 row_spmv_dw(const SysView& S, int64_t row, co
   const float4* v = val + S.rowptr[row];
   float rh0 = 0, rl0 = 0, ih0 = 0, il0 = 0, rh1 = 0, rl1 = 0, ih1 = 0, il1 = 0;
   int k = lane;
-  for (; k + 32 < W; k += 64) {  // two independent column chains per lane
-    const float4 a0 = v[k], a1 = v[k + 32];
-    const float4 x0 = pdw[c[k]], x1 = pdw[c[k + 32]];
+  for (; k + 96 < W; k += 128) {  // four column chains per lane in flight, two accumulator pairs
+    const float4 a0 = v[k], a1 = v[k + 32], a2 = v[k + 64], a3 = v[k + 96];
+    const int c0 = c[k], c1 = c[k + 32], c2 = c[k + 64], c3 = c[k + 96];
+    const float4 x0 = pdw[c0], x1 = pdw[c1], x2 = pdw[c2], x3 = pdw[c3];
     dw_mac(rh0, rl0, a0.x, a0.z, x0.x, x0.z);
     dw_mac(rh0, rl0, -a0.y, -a0.w, x0.y, x0.w);
     dw_mac(ih0, il0, a0.x, a0.z, x0.y, x0.w);
@@ -482,8 +483,16 @@ __device__ __forceinline__ double2 row_spmv_dw(const SysView& S, int64_t row, co
     dw_mac(rh1, rl1, -a1.y, -a1.w, x1.y, x1.w);
     dw_mac(ih1, il1, a1.x, a1.z, x1.y, x1.w);
     dw_mac(ih1, il1, a1.y, a1.w, x1.x, x1.z);
+    dw_mac(rh0, rl0, a2.x, a2.z, x2.x, x2.z);
+    dw_mac(rh0, rl0, -a2.y, -a2.w, x2.y, x2.w);
+    dw_mac(ih0, il0, a2.x, a2.z, x2.y, x2.w);
+    dw_mac(ih0, il0, a2.y, a2.w, x2.x, x2.z);
+    dw_mac(rh1, rl1, a3.x, a3.z, x3.x, x3.z);
+    dw_mac(rh1, rl1, -a3.y, -a3.w, x3.y, x3.w);
+    dw_mac(ih1, il1, a3.x, a3.z, x3.y, x3.w);
+    dw_mac(ih1, il1, a3.y, a3.w, x3.x, x3.z);
   }
-  if (k < W) {
+  for (; k < W; k += 32) {
     const float4 a0 = v[k];
     const float4 x0 = pdw[c[k]];
     dw_mac(rh0, rl0, a0.x, a0.z, x0.x, x0.z);
@@ -538,7 +547,7 @@ __device__ __forceinline__ void block_precond_dw(const SysView& S, int b, const 
 // One whole CG solve of A d = r0 (d = 0 at entry, r holds r0 at entry) in the
 // DW mode: FP64 vectors, recurrences and reductions; DW matrix, p copy and
 // block inverses (precond 2) or none (precond 0).
-__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_dw(SysView S, const float4* __restrict__ val, double2* x,
+__global__ void __launch_bounds__(CG_THREADS, 3) k_cg_dw(SysView S, const float4* __restrict__ val, double2* x,
                                                          double2* r, double2* p, float4* pdw, double2* Ap, double2* z,
                                                          int precond, const float4* __restrict__ binv, double* red,
                                                          CgState* st) {

@@ -256,6 +256,10 @@ def main():
                     help="after the timed steps, solve the same system with the plain FP64 CG and report it")
     ap.add_argument("--adjoint", action="store_true",
                     help="after the timed steps, time the adjoint gradient of the absorbed power (obstacle elements)")
+    ap.add_argument("--adapt", type=int, default=0,
+                    help="run the adaptive loop of Sec. 4.2 (fixed-fraction marking 0.30 / 0.05, 2:1 octree) on the "
+                         "Fichera oven for this many adaptation steps instead of the timed steps")
+    ap.add_argument("--adapt-p", type=int, default=2)
     ap.add_argument("--precision-report", action="store_true",
                     help="after the timed steps, solve again with FP64 quadrature and report the differences")
     args = ap.parse_args()
@@ -266,10 +270,14 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank)
     # the CPU baseline's process pool starts (spawn) before this process touches the GPU
-    pool = OraclePool() if rank == 0 else None
+    pool = OraclePool() if rank == 0 and not args.adapt else None
 
     import torch
     torch.cuda.set_device(local)
+    if args.adapt:
+        if pool:
+            pool.close()
+        return adaptive_run(args, rank)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -479,6 +487,55 @@ def main():
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def adaptive_run(args, rank):
+    """The adaptive loop of Sec. 4.2 on the Fichera oven: estimate, mark (fixed fractions 0.30 / 0.05), refine /
+    coarsen a 2:1 octree, set up again; one JSON line with the per-step sizes, estimates and device times."""
+    import torch
+    from paper_2609_03155_b300 import dpg, inputs
+    tree = inputs.fichera_octree(p=args.adapt_p)
+    mode = CG_MODES[args.cg]
+    stream = torch.cuda.current_stream()
+    steps = []
+    for step in range(args.adapt + 1):
+        mesh, leaves = tree.mesh()
+        t0 = time.perf_counter()
+        d = dpg.DPG(mesh)
+        setup_s = time.perf_counter() - t0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        d.element_batch()
+        ev[1].record(stream)
+        d.assemble()
+        ev[2].record(stream)
+        x, rep = d.cg_solve(mode=mode, rtol=args.rtol, max_iter=args.max_iter, inner_rtol=args.inner_rtol,
+                            raise_on_nonconvergence=False)
+        ev[3].record(stream)
+        _, eta, etag = d.estimate(x, want_u=False)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        marks = d.mark_fraction(eta, 0.30, 0.05)
+        levels = sorted({c[0] for c in leaves})
+        steps.append({"step": step, "elements": int(mesh.n_elem), "trace_unknowns": int(d.n), "nnz": int(d.nnz),
+                      "levels": [int(levels[0]), int(levels[-1])], "global_estimate": etag,
+                      "refine": int((marks > 0).sum()), "coarsen": int((marks < 0).sum()),
+                      "setup_s": setup_s, "element_pass_s": ev[0].elapsed_time(ev[1]) / 1e3,
+                      "assemble_s": ev[1].elapsed_time(ev[2]) / 1e3, "cg_s": ev[2].elapsed_time(ev[3]) / 1e3,
+                      "cg_iterations": rep["iterations"], "cg_rel_residual": rep["rel_residual"],
+                      "estimate_s": ev[3].elapsed_time(ev[4]) / 1e3})
+        d.destroy()
+        if step < args.adapt:
+            tree.adapt(leaves, marks)
+    if rank == 0:
+        tot_el = sum(s["elements"] for s in steps)
+        dev_s = sum(s["element_pass_s"] + s["assemble_s"] + s["cg_s"] + s["estimate_s"] for s in steps)
+        print(json.dumps({"metric": METRIC, "value": tot_el / dev_s, "unit": UNIT, "n_gpus": 1,
+                          "higher_is_better": True, "dtype": "f64+f32(IR inner)", "data": "synthetic",
+                          "config": {"workload": f"fichera_oven_adaptive_p{args.adapt_p}", "adaptation_steps": args.adapt,
+                                     "marking": "fixed fraction 0.30 refine / 0.05 coarsen of sum eta^2",
+                                     "cg": args.cg, "cg_rtol": args.rtol},
+                          "adaptive": steps}), flush=True)
 
 
 def fp64_step(d, mesh, x_mixed, args):

@@ -101,6 +101,7 @@ def lib():
     L.dpg_set_wait_limit.argtypes = [vp, i64, i32]
     L.dpg_set_factor_arith.argtypes = [vp, i32]
     L.dpg_estimate_clamped.argtypes = [vp, C.POINTER(i32)]
+    L.dpg_mark_fraction.argtypes = [vp, vp, dbl, dbl, vp, vp]
     L.dpg_factor_check.argtypes = [i32, i32, i32, i32, i32, i32, vp, vp, C.POINTER(i32)]
     L.dpg_power.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_autotune.argtypes = [vp, dbl, vp, vp, vp]
@@ -123,7 +124,7 @@ def lib():
                  "dpg_sizes", "dpg_trace_map", "dpg_element_dump", "dpg_csr_copy", "dpg_probe_peaks",
                  "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps",
                  "dpg_set_real_path", "dpg_cg_bytes_per_iteration", "dpg_element_layout", "dpg_tc_gemm", "dpg_set_graph", "dpg_autotune", "dpg_power",
-                 "dpg_set_wait_limit", "dpg_set_factor_arith", "dpg_factor_check", "dpg_estimate_clamped",
+                 "dpg_set_wait_limit", "dpg_set_factor_arith", "dpg_factor_check", "dpg_estimate_clamped", "dpg_mark_fraction",
                  "dpg_group_info"):
         getattr(L, name).restype = C.c_int
     _lib = L

@@ -148,6 +148,43 @@ extern "C" int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex*
   return estimate(h, reinterpret_cast<const double2*>(xhat), reinterpret_cast<double2*>(u), eta, eta_global, S_(st));
 }
 
+// Fixed-fraction marking of Sec. 4.2 (host logic after one copy of eta).
+extern "C" int dpg_mark_fraction(dpg_handle* h, const double* eta, double refine_frac, double coarsen_frac,
+                                 int8_t* marks, dpg_stream st) {
+  Range range_("dpg_mark_fraction");
+  if (!h || !eta || !marks || !(refine_frac >= 0.0 && refine_frac <= 1.0) ||
+      !(coarsen_frac >= 0.0 && coarsen_frac <= 1.0))
+    return DPG_ERR_ARG;
+  const int ne = h->ne;
+  std::vector<double> e2(ne);
+  cudaStream_t s = S_(st);
+  DPG_CUDA_TRY(h, cudaMemcpyAsync(e2.data(), eta, sizeof(double) * ne, cudaMemcpyDeviceToHost, s));
+  DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+  double total = 0.0;
+  for (int e = 0; e < ne; ++e) {
+    e2[e] = e2[e] * e2[e];
+    total += e2[e];
+  }
+  std::memset(marks, 0, (size_t)ne);
+  if (ne == 0 || !(total > 0.0)) return DPG_OK;
+  std::vector<int> order(ne);
+  for (int e = 0; e < ne; ++e) order[e] = e;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return e2[a] > e2[b] || (e2[a] == e2[b] && a < b); });
+  double acc = 0.0;
+  for (int k = 0; k < ne && acc < refine_frac * total; ++k) {  // largest first, up to the crossing cell
+    marks[order[k]] = 1;
+    acc += e2[order[k]];
+  }
+  acc = 0.0;
+  for (int k = ne - 1; k >= 0; --k) {  // smallest first, within the coarsening share
+    const int e = order[k];
+    if (marks[e] == 1 || acc + e2[e] > coarsen_frac * total) break;
+    marks[e] = -1;
+    acc += e2[e];
+  }
+  return DPG_OK;
+}
+
 extern "C" int dpg_estimate_clamped(dpg_handle* h, int32_t* count) {
   if (!h || !count) return DPG_ERR_ARG;
   int c = 0;

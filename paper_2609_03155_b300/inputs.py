@@ -404,3 +404,140 @@ def fichera_amr(n_unit, radius=0.75, mix=(0.4, 0.3, 0.2, 0.1), p=None, seed=2026
     n = (2 * n_unit, 2 * n_unit, 3 * n_unit)
     return amr_box(n, (2.0, 2.0, 3.0), keep, refine, p=p if p is not None else 1,
                    mix=None if p is not None else mix, seed=seed, name=f"fichera_amr_{n_unit}_r{radius}")
+
+
+class OctreeHexMesh:
+    """Axis-aligned hexahedra refined as an octree over kept coarse cells (geometry only).
+
+    The coarse grid has n = (nx, ny, nz) cells over [0, lx] x [0, ly] x [0, lz];
+    ``keep(centre)`` selects the coarse cells of the domain.  A leaf is
+    (level, i, j, k) on the level's grid (2^level cells per coarse cell and
+    direction).  The mesh stays 2:1 balanced across faces, edges and vertices:
+    refining a leaf first refines every coarser leaf that touches it
+    (recursively), and a family of eight children is merged back only when no
+    leaf touching the parent is more than one level finer than the parent.
+    Walls (faces without a domain cell across) are PEC, and the plane x3 = lz
+    carries n x E = (sin(pi x2), 0, 0) (the excitation of Sec. 4.2).
+    """
+
+    _OFF = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy, dz) != (0, 0, 0)]
+
+    def __init__(self, n, lengths, keep, p=2, omega=5.0, name="octree"):
+        self.n = tuple(int(v) for v in n)
+        self.lengths = tuple(float(v) for v in lengths)
+        h = [lengths[d] / n[d] for d in range(3)]
+        self.kept = {(i, j, k) for k in range(n[2]) for j in range(n[1]) for i in range(n[0])
+                     if keep(np.array([(i + 0.5) * h[0], (j + 0.5) * h[1], (k + 0.5) * h[2]]))}
+        self.leaves = {(0, i, j, k) for (i, j, k) in self.kept}
+        self.p, self.omega, self.name = p, omega, name
+
+    def in_domain(self, l, i, j, k):
+        if min(i, j, k) < 0:
+            return False
+        c = (i >> l, j >> l, k >> l)
+        return c[0] < self.n[0] and c[1] < self.n[1] and c[2] < self.n[2] and c in self.kept
+
+    def leaf_at(self, l, i, j, k):
+        """The leaf covering cell (l, i, j, k) at its level or coarser, or None (refined further, or outside)."""
+        for lev in range(l, -1, -1):
+            s = l - lev
+            c = (lev, i >> s, j >> s, k >> s)
+            if c in self.leaves:
+                return c
+        return None
+
+    def refine(self, c):
+        if c not in self.leaves:
+            return
+        l, i, j, k = c
+        for dx, dy, dz in self._OFF:  # every touching leaf must be at least as fine as c first
+            q = (l, i + dx, j + dy, k + dz)
+            if self.in_domain(*q):
+                L = self.leaf_at(*q)
+                if L is not None and L[0] < l:
+                    self.refine(L)
+        self.leaves.discard(c)
+        for ch in range(8):
+            self.leaves.add((l + 1, 2 * i + (ch & 1), 2 * j + ((ch >> 1) & 1), 2 * k + ((ch >> 2) & 1)))
+
+    def _children(self, c):
+        l, i, j, k = c
+        return [(l + 1, 2 * i + (ch & 1), 2 * j + ((ch >> 1) & 1), 2 * k + ((ch >> 2) & 1)) for ch in range(8)]
+
+    def can_coarsen(self, parent):
+        if parent[0] < 0 or any(ch not in self.leaves for ch in self._children(parent)):
+            return False
+        l, i, j, k = parent
+        for dx, dy, dz in self._OFF:
+            q = (l, i + dx, j + dy, k + dz)
+            if not self.in_domain(*q) or self.leaf_at(*q) is not None:
+                continue  # outside, or covered by a leaf of level <= l
+            # q is refined: none of its children may be refined further
+            if any(ch not in self.leaves for ch in self._children(q)):
+                return False
+        return True
+
+    def adapt(self, leaves, marks):
+        """Refine the leaves marked +1, then merge the families whose eight children are all marked -1."""
+        for c, m in zip(leaves, marks):
+            if m > 0:
+                self.refine(c)
+        parents = sorted({(c[0] - 1, c[1] >> 1, c[2] >> 1, c[3] >> 1) for c, m in zip(leaves, marks)
+                          if m < 0 and c[0] > 0})
+        want = {c for c, m in zip(leaves, marks) if m < 0}
+        for P in parents:
+            if all(ch in want for ch in self._children(P)) and self.can_coarsen(P):
+                for ch in self._children(P):
+                    self.leaves.discard(ch)
+                self.leaves.add(P)
+
+    def ordered_leaves(self):
+        top = max(c[0] for c in self.leaves)
+        key = lambda c: ((c[3] << (top - c[0])), (c[2] << (top - c[0])), (c[1] << (top - c[0])), c[0])
+        return sorted(self.leaves, key=key)
+
+    def mesh(self):
+        """Mesh of the current leaves (and the leaf of each element, in element order)."""
+        leaves = self.ordered_leaves()
+        top = max(c[0] for c in leaves)
+        scale = 1 << top
+        ids, elems = {}, []
+        for (l, i, j, k) in leaves:
+            s = 1 << (top - l)
+            row = []
+            for v in range(8):
+                key = ((i + (v & 1)) * s, (j + ((v >> 1) & 1)) * s, (k + ((v >> 2) & 1)) * s)
+                row.append(ids.setdefault(key, len(ids)))
+            elems.append(row)
+        pts = np.zeros((len(ids), 3))
+        for key, v in ids.items():
+            pts[v] = [key[d] * self.lengths[d] / (self.n[d] * scale) for d in range(3)]
+        elem = np.array(elems, dtype=np.int32)
+        ne = elem.shape[0]
+        bc = np.zeros((ne, 6), dtype=np.int8)
+        grp = np.zeros((ne, 6), dtype=np.int16)
+        for e, (l, i, j, k) in enumerate(leaves):
+            for d in range(3):
+                for s in (0, 1):
+                    q = [i, j, k]
+                    q[d] += 1 if s else -1
+                    if not self.in_domain(l, *q):
+                        bc[e, 2 * d + s] = BC_DIRICHLET
+                        top_plane = d == 2 and s == 1 and (k + 1) == self.n[2] << l
+                        grp[e, 2 * d + s] = 1 if top_plane else 0
+        pk = np.full(ne, self.p, dtype=np.int8)
+        m = Mesh(vert=pts, elem=elem, p=pk, eps=np.ones(ne, dtype=complex), mu=np.ones(ne, dtype=complex),
+                 face_bc=bc, face_grp=grp, omega=self.omega, robin=[],
+                 dirichlet=[{'kind': DIRICHLET_ZERO, 'port': None}, {'kind': DIRICHLET_SIN_PI_X2, 'port': None}],
+                 name=f"{self.name}_{ne}")
+        return m, leaves
+
+
+def fichera_octree(p=2, omega=5.0):
+    """The Fichera oven of Sec. 4.2 as an octree mesh: (0,2)^3 minus [0,1]^3, plus [1,2]^2 x [2,3], starting
+    from its eight unit cells (the initial mesh of Sec. 4.2)."""
+    def keep(c):
+        lower = c[2] < 2.0 and not (c[0] < 1.0 and c[1] < 1.0 and c[2] < 1.0)
+        top = c[0] > 1.0 and c[1] > 1.0 and c[2] > 2.0
+        return lower or top
+    return OctreeHexMesh((2, 2, 3), (2.0, 2.0, 3.0), keep, p=p, omega=omega, name=f"fichera_octree_p{p}")

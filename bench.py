@@ -515,7 +515,7 @@ def adaptive_run(args, rank):
         _, eta, etag = d.estimate(x, want_u=False)
         ev[4].record(stream)
         torch.cuda.synchronize()
-        marks = d.mark_fraction(eta, 0.30, 0.05)
+        marks = d.mark_fraction(eta, 0.30, 0.05, power=1)
         levels = sorted({c[0] for c in leaves})
         steps.append({"step": step, "elements": int(mesh.n_elem), "trace_unknowns": int(d.n), "nnz": int(d.nnz),
                       "levels": [int(levels[0]), int(levels[-1])], "global_estimate": etag,
@@ -533,7 +533,7 @@ def adaptive_run(args, rank):
         print(json.dumps({"metric": METRIC, "value": tot_el / dev_s, "unit": UNIT, "n_gpus": 1,
                           "higher_is_better": True, "dtype": "f64+f32(IR inner)", "data": "synthetic",
                           "config": {"workload": f"fichera_oven_adaptive_p{args.adapt_p}", "adaptation_steps": args.adapt,
-                                     "marking": "fixed fraction 0.30 refine / 0.05 coarsen of sum eta^2",
+                                     "marking": "fixed fraction 0.30 refine / 0.05 coarsen of sum eta_K",
                                      "cg": args.cg, "cg_rtol": args.rtol},
                           "adaptive": steps}), flush=True)
 

@@ -249,15 +249,17 @@ int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex* u, double*
  * fraction 0.30 and coarsening fraction 0.05 in its parameter table of
  * App. C.2): with eta (device, n_elem doubles, e.g. from dpg_estimate) the
  * cells are ranked by eta_K; the largest are marked +1 (refine) until their
- * share of sum eta_K^2 reaches refine_frac (the crossing cell included), the
- * smallest -1 (coarsen) while their share stays within coarsen_frac; a cell
- * marked +1 is never marked -1; ties go by element index.  The paper names
- * the fractions but not the measure; the squares of eta_K are this reading
- * (the global estimate is sqrt(sum eta_K^2)).  marks: host, n_elem int8.
- * Host logic after one device-to-host copy; synchronises the stream.
- * Errors: DPG_ERR_ARG. */
-int dpg_mark_fraction(dpg_handle* h, const double* eta, double refine_frac, double coarsen_frac, int8_t* marks,
-                      dpg_stream s);
+ * share of sum eta_K^power reaches refine_frac (the crossing cell included),
+ * the smallest -1 (coarsen) while their share stays within coarsen_frac; a
+ * cell marked +1 is never marked -1; ties go by element index.  The paper
+ * names the fractions but not the measure: power 1 sums the residual norms
+ * themselves ("their combined residual"), power 2 is Doerfler's bulk
+ * criterion on the squared global estimate sqrt(sum eta_K^2).
+ * marks: host, n_elem int8.  Host logic after one device-to-host copy;
+ * synchronises the stream.  Errors: DPG_ERR_ARG (power not 1 or 2, fraction
+ * outside [0, 1]). */
+int dpg_mark_fraction(dpg_handle* h, const double* eta, double refine_frac, double coarsen_frac, int32_t power,
+                      int8_t* marks, dpg_stream s);
 
 /* Number of elements whose eta_K^2 came out negative (through rounding, when
  * eta_K ~ 0) in the last dpg_estimate or dpg_estimate_noalloc and was set to

@@ -5,8 +5,9 @@ the largest for refinement until their combined share reaches 30 % of the
 total, and the smallest for coarsening until their combined share reaches
 5 % (parameter table of App. C.2: refinement fraction 0.30, coarsening
 fraction 0.05).  Reading taken here (the paper names the fractions but not
-the measure): shares are of sum_K eta_K^2, the square of the global estimate
-sqrt(sum eta_K^2) of Sec. 4.2; refinement takes the smallest set of largest
+the measure): shares are of sum_K eta_K ("their combined residual", power 1,
+the default) or of sum_K eta_K^2 (power 2, Doerfler's bulk criterion on the
+squared global estimate of Sec. 4.2); refinement takes the smallest set of largest
 cells whose sum reaches the fraction (the cell that crosses it included);
 coarsening takes the largest set of smallest cells whose sum stays within
 its fraction; a cell marked for refinement is never marked for coarsening;
@@ -15,9 +16,9 @@ ties are ordered by element index.
 import numpy as np
 
 
-def mark_fraction(eta, refine=0.30, coarsen=0.05):
+def mark_fraction(eta, refine=0.30, coarsen=0.05, power=1):
     """Marks per element: +1 refine, -1 coarsen, 0 keep."""
-    e2 = np.asarray(eta, dtype=np.float64) ** 2
+    e2 = np.abs(np.asarray(eta, dtype=np.float64)) ** power
     ne = e2.shape[0]
     total = float(np.sum(e2))
     marks = np.zeros(ne, dtype=np.int8)

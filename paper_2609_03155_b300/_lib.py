@@ -101,7 +101,7 @@ def lib():
     L.dpg_set_wait_limit.argtypes = [vp, i64, i32]
     L.dpg_set_factor_arith.argtypes = [vp, i32]
     L.dpg_estimate_clamped.argtypes = [vp, C.POINTER(i32)]
-    L.dpg_mark_fraction.argtypes = [vp, vp, dbl, dbl, vp, vp]
+    L.dpg_mark_fraction.argtypes = [vp, vp, dbl, dbl, i32, vp, vp]
     L.dpg_factor_check.argtypes = [i32, i32, i32, i32, i32, i32, vp, vp, C.POINTER(i32)]
     L.dpg_power.argtypes = [vp, vp, vp, vp, vp]
     L.dpg_autotune.argtypes = [vp, dbl, vp, vp, vp]

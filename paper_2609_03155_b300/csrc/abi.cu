@@ -1,5 +1,6 @@
 // extern "C" entry points of libdpg (declared in include/dpg.h).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -150,10 +151,10 @@ extern "C" int dpg_estimate(dpg_handle* h, const dpg_complex* xhat, dpg_complex*
 
 // Fixed-fraction marking of Sec. 4.2 (host logic after one copy of eta).
 extern "C" int dpg_mark_fraction(dpg_handle* h, const double* eta, double refine_frac, double coarsen_frac,
-                                 int8_t* marks, dpg_stream st) {
+                                 int32_t power, int8_t* marks, dpg_stream st) {
   Range range_("dpg_mark_fraction");
   if (!h || !eta || !marks || !(refine_frac >= 0.0 && refine_frac <= 1.0) ||
-      !(coarsen_frac >= 0.0 && coarsen_frac <= 1.0))
+      !(coarsen_frac >= 0.0 && coarsen_frac <= 1.0) || (power != 1 && power != 2))
     return DPG_ERR_ARG;
   const int ne = h->ne;
   std::vector<double> e2(ne);
@@ -162,7 +163,7 @@ extern "C" int dpg_mark_fraction(dpg_handle* h, const double* eta, double refine
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
   double total = 0.0;
   for (int e = 0; e < ne; ++e) {
-    e2[e] = e2[e] * e2[e];
+    e2[e] = power == 2 ? e2[e] * e2[e] : std::fabs(e2[e]);
     total += e2[e];
   }
   std::memset(marks, 0, (size_t)ne);

@@ -122,11 +122,11 @@ class DPG:
             u = u.view(self.n_elem, self.n_u)
         return u, eta, tot.value
 
-    def mark_fraction(self, eta, refine=0.30, coarsen=0.05, stream=None):
+    def mark_fraction(self, eta, refine=0.30, coarsen=0.05, power=1, stream=None):
         """Per-element marks (+1 refine, -1 coarsen, 0 keep) from eta (device tensor) by fixed fractions."""
         marks = np.zeros(self.n_elem, dtype=np.int8)
-        check(_lib.lib().dpg_mark_fraction(self.h, ptr(eta), float(refine), float(coarsen), marks.ctypes.data,
-                                           stream_handle(stream)), self.h)
+        check(_lib.lib().dpg_mark_fraction(self.h, ptr(eta), float(refine), float(coarsen), int(power),
+                                           marks.ctypes.data, stream_handle(stream)), self.h)
         return marks
 
     def estimate_clamped(self):

@@ -48,9 +48,10 @@ def test_adaptive_loop_matches_oracle(dpg_mod):
             assert rel(u[d.u_off[e]:d.u_off[e + 1]], sol['rec'][e]['u']) < 1e-10, (step, e)
         eta_g = eta.cpu().numpy()
         assert np.all(np.abs(eta_g - sol['eta']) <= 1e-9 * sol['eta']), (step, np.max(np.abs(eta_g - sol['eta']) / sol['eta']))
-        marks = d.mark_fraction(eta, 0.30, 0.05)
-        marks_or = adapt.mark_fraction(sol['eta'], 0.30, 0.05)
-        assert np.array_equal(marks, marks_or), step
+        for power in (2, 1):
+            marks = d.mark_fraction(eta, 0.30, 0.05, power=power)
+            marks_or = adapt.mark_fraction(sol['eta'], 0.30, 0.05, power=power)
+            assert np.array_equal(marks, marks_or), (step, power)
         E.append(etag)
         d.destroy()
         t_gpu.adapt(leaves, marks)

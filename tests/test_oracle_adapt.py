@@ -2,7 +2,7 @@
 
 Pins (not the oracle against itself):
 * marking: the marked-for-refinement set is the minimal set of largest cells
-  reaching the fraction of sum eta^2 (checked against brute force over all
+  reaching the fraction of sum eta^power (checked against brute force over all
   prefix lengths), the coarsening set the maximal set of smallest cells within
   its fraction, and the two are disjoint;
 * octree: every pair of touching leaves differs by at most one level (brute
@@ -19,13 +19,14 @@ from oracle import adapt, hanging
 from paper_2609_03155_b300 import inputs
 
 
-def test_marking_is_minimal_and_maximal_prefix():
+@pytest.mark.parametrize("power", [1, 2])
+def test_marking_is_minimal_and_maximal_prefix(power):
     rng = np.random.default_rng(5)
     for trial in range(50):
         ne = int(rng.integers(1, 60))
         eta = rng.exponential(1.0, ne) ** 2
-        m = adapt.mark_fraction(eta, 0.3, 0.05)
-        e2 = eta ** 2
+        m = adapt.mark_fraction(eta, 0.3, 0.05, power=power)
+        e2 = eta ** power
         tot = e2.sum()
         order = np.argsort(-e2, kind="stable")
         k = int((m > 0).sum())

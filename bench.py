@@ -62,6 +62,19 @@ def config_mesh(name):
         # Fichera cavity, 12 coarse cells per unit, cells within 0.3 of the
         # re-entrant corner refined once (2:1 hanging faces), degrees 1..4 mixed
         return inputs.fichera_amr(12, radius=0.3)
+    if name == "cavity3-32":
+        # the 32^3 sub-box of the jittered p = 3 cavity with random lossy permittivity (2^18 elements at p = 3
+        # need a CSR of ~661 GB; the element rate is the same per element)
+        return inputs.cavity(32, 3, jitter=0.1, eps_mode='random', name="cavity3_32x32x32_p3_jitter0.1")
+    if name == "fichera-amr-1e5":
+        # Fichera cavity, 20 coarse cells per unit, cells within 0.6 of the re-entrant corner refined
+        # once (2:1 hanging faces), degrees 1..4 in a 40/30/20/10 % mix: 108,149 elements
+        return inputs.fichera_amr(20, radius=0.6)
+    if name in ("obstacle-48", "obstacle-64"):
+        n = int(name.split("-")[1])
+        m = inputs.cavity(n, 2, name=f"obstacle_cavity_{n}x{n}x{n}_p2")
+        inputs.sphere_obstacle(m, radius=0.2, eps=20.0 + 5.0j)
+        return m
     if name == "obstacle":
         # unit cavity 32^3, p = 2, dielectric sphere eps = 20 + 5i of radius 0.2
         m = inputs.cavity(32, 2, name="obstacle_cavity_32x32x32_p2")
@@ -252,6 +265,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--chunk", type=int, default=0, help="elements per launch (0: library default)")
     ap.add_argument("--autotune", action="store_true", help="measure chunk sizes per degree before the warm-up")
+    ap.add_argument("--stream", action="store_true",
+                    help="streaming element pass (no per-element condensation data; for the full-size configs)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="after the timed steps, solve the same system with the plain FP64 CG and report it")
     ap.add_argument("--adjoint", action="store_true",
@@ -285,7 +300,9 @@ def main():
 
     from paper_2609_03155_b300 import dpg
     mesh = config_mesh(args.config)
-    d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk, adjoint=args.adjoint)
+    streaming = args.stream or args.config in ("cavity3-32", "fichera-amr-1e5", "obstacle-48", "obstacle-64")
+    d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk, adjoint=args.adjoint,
+                streaming=streaming)
     mode = CG_MODES[args.cg]
     tuned = d.autotune() if args.autotune else None
     stream = torch.cuda.current_stream()
@@ -457,7 +474,7 @@ def main():
                    "p": p if len(pvals) == 1 else {str(q): int((mesh.p == q).sum()) for q in pvals}, "dp": 1,
                    "quadrature": args.precision,
                    "chunks": {str(g[0]): g[2] for g in d.group_info()} if d.h else None,
-                   "autotuned": tuned is not None,
+                   "autotuned": tuned is not None, "streaming": streaming,
                    "trace_unknowns": int(d.n), "nnz": int(d.nnz), "cg": args.cg, "cg_rtol": args.rtol,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-element stores and CSR are tens of GB)"},

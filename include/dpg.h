@@ -97,7 +97,7 @@ enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
 enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8, DPG_CG_HALF = 16,
        DPG_CG_IR_V64 = 32, DPG_CG_DW = 64 };
-enum { DPG_FLAG_ADJOINT = 1 };
+enum { DPG_FLAG_ADJOINT = 1, DPG_FLAG_STREAM = 2 };
 /* Arithmetic of the element factorisation's trailing updates (dpg_set_factor_arith). */
 enum { DPG_FACTOR_FP64 = 0, DPG_FACTOR_TC_SPLIT = 1 };
 
@@ -148,7 +148,14 @@ typedef struct {
   int32_t dp;        /* enrichment, must be 1 in this build */
   int32_t precision; /* DPG_PREC_* */
   int32_t chunk;     /* elements per batched launch, 0 = automatic */
-  int32_t flags;     /* DPG_FLAG_*: DPG_FLAG_ADJOINT keeps the M1 factors dpg_grad_eps needs */
+  int32_t flags;     /* DPG_FLAG_*: DPG_FLAG_ADJOINT keeps the M1 factors dpg_grad_eps needs;
+                        DPG_FLAG_STREAM keeps no per-element condensation data: the element
+                        pass assembles each chunk (one colour) as soon as it is condensed
+                        and dpg_assemble has nothing left to do; recovery and the estimator
+                        condense every chunk again.  Memory then scales with the CSR system
+                        instead of n_elem (n_h^2 + n_u n_h) complex values, which lets
+                        meshes of 1e5 elements and more fit.  Not with DPG_FLAG_ADJOINT,
+                        dpg_autotune or dpg_grad_eps (DPG_ERR_UNSUPPORTED). */
 } dpg_params;
 
 typedef struct {

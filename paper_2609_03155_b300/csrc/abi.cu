@@ -44,6 +44,7 @@ static void free_all(dpg_handle* h) {
                   h->d_valdw, h->d_pdw, h->d_binvdw};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (h->stream && h->d_soff) cudaFree(h->d_soff);
 }
 
 extern "C" int dpg_setup_mesh(dpg_handle** out, const dpg_mesh_desc* m, const dpg_params* prm, dpg_stream st) {
@@ -120,6 +121,7 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
   }
   // only a pass whose every pivot was positive feeds assembly and estimation
   h->have_elements = true;
+  if (h->stream) system_changed(h);  // assembled during the pass
   return DPG_OK;
 }
 
@@ -207,6 +209,10 @@ extern "C" int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_
                             dpg_stream st) {
   Range range_("dpg_grad_eps");
   if (!h) return DPG_ERR_ARG;
+  if (h->stream) {
+    h->err = "dpg_grad_eps needs the stored condensation data (not kept with DPG_FLAG_STREAM)";
+    return DPG_ERR_UNSUPPORTED;
+  }
   return grad_eps(h, reinterpret_cast<const double2*>(xhat), obstacle_mask, P, dP_deps_re, dP_deps_im, cg_mode, cg_rtol,
                   max_iter, S_(st));
 }
@@ -302,7 +308,22 @@ extern "C" int dpg_element_dump(dpg_handle* h, const int32_t* ids, int32_t n_ids
           l[q * nv + i] = {v.x, -v.y};
         }
     }
-    if (Sout || sout) {
+    if ((Sout || sout) && h->stream) {
+      // chunk-sized stores: one element at a time, read from its slot
+      for (int k = 0; k < cnt; ++k) {
+        const int e = ids[k0 + k];
+        rc = run_element_chunk(h, g, &e, 1, s, true, true, h->allow_real && h->is_real[e]);
+        if (rc) return rc;
+        const size_t q = (size_t)(k0 + k);
+        if (Sout)
+          DPG_CUDA_TRY(h, cudaMemcpyAsync(Sout + q * nh * nh, h->d_S + h->soff_host[e].S, sizeof(double2) * nh * nh,
+                                          cudaMemcpyDeviceToHost, s));
+        if (sout)
+          DPG_CUDA_TRY(h, cudaMemcpyAsync(sout + q * nh, h->d_s + h->soff_host[e].h, sizeof(double2) * nh,
+                                          cudaMemcpyDeviceToHost, s));
+        DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
+      }
+    } else if (Sout || sout) {
       std::vector<int> re, cx;
       for (int k = 0; k < cnt; ++k) (h->allow_real && h->is_real[ids[k0 + k]] ? re : cx).push_back(ids[k0 + k]);
       if (!re.empty()) {
@@ -518,6 +539,10 @@ extern "C" int dpg_autotune(dpg_handle* h, double max_workspace_bytes, int32_t* 
                             dpg_stream st) {
   Range range_("dpg_autotune");
   if (!h || !(max_workspace_bytes > 0)) return DPG_ERR_ARG;
+  if (h->stream) {
+    h->err = "dpg_autotune is not available with DPG_FLAG_STREAM";
+    return DPG_ERR_UNSUPPORTED;
+  }
   int rc = autotune(h, max_workspace_bytes, caps, ms_per_element, S_(st));
   h->have_elements = false;
   h->have_system = false;

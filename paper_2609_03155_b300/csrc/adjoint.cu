@@ -451,7 +451,8 @@ int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_
   rc |= ensure(h, (void**)&h->d_lam, sizeof(double2) * h->n);
   rc |= ensure(h, (void**)&h->d_rhs_adj, sizeof(double2) * h->n);
   if (rc) return DPG_ERR_NOMEM;
-  recover_u(h, xhat, h->d_u, s);
+  rc = recover_u(h, xhat, h->d_u, s);
+  if (rc) return rc;
   double* Pk = h->d_Pk;
   double* ekv = h->d_Pk + ne;
   for (const Group& G : h->grp) {

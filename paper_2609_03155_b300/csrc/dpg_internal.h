@@ -144,6 +144,14 @@ struct dpg_handle {
   std::vector<int32_t> l2g;                    // element-major, n_h(K) per element (offsets ElemOff::h)
   std::vector<dpg::ElemOff> off;               // ne + 1 (the last holds the totals)
   dpg::ElemOff* d_off = nullptr;
+  // Streaming (DPG_FLAG_STREAM): the element stores S, s, Z, z hold one chunk
+  // only, at slot-based offsets d_soff[e] (the element's slot in its chunk of
+  // the launch plan); the chunks are colour-homogeneous and assembled as they
+  // are condensed.  Without streaming d_soff == d_off.
+  bool stream = false;
+  std::vector<int> elem_color;
+  dpg::ElemOff* d_soff = nullptr;
+  std::vector<dpg::ElemOff> soff_host;
   // trace restrictions of elements with a lower-order entity (-1: identity)
   std::vector<int> elem_sig;
   std::vector<dpg::RSig> rsig;
@@ -259,7 +267,7 @@ void set_default_caps(dpg_handle* h, int chunk);
 int alloc_workspace(dpg_handle* h);
 int init_kernel_attributes(dpg_handle* h);
 int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s, bool factor,
-                      bool extract, bool real = false, const ChunkPlan* cp = nullptr);
+                      bool extract, bool real = false, const ChunkPlan* cp = nullptr, bool quad = true);
 int build_plan(dpg_handle* h);
 void free_plan(dpg_handle* h);
 int element_pass(dpg_handle* h, cudaStream_t s);
@@ -267,7 +275,7 @@ int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem,
 int compute_reference_matrices(dpg_handle* h, int g, cudaStream_t s);
 int factor_gram_only(dpg_handle* h, int g, int count, cudaStream_t s);
 int estimate_pass(dpg_handle* h, const double2* xhat, double2* u, double* eta2, cudaStream_t s);
-void recover_u(dpg_handle* h, const double2* xhat, double2* u, cudaStream_t s);
+int recover_u(dpg_handle* h, const double2* xhat, double2* u, cudaStream_t s);
 // power.cu
 int power(dpg_handle* h, const double2* xhat, double* q, double* flux_host, cudaStream_t s);
 // factor_tc.cu
@@ -284,6 +292,8 @@ int grad_eps(dpg_handle* h, const double2* xhat, const uint8_t* mask, double* P_
              int cg_mode, double cg_rtol, int max_iter, cudaStream_t s);
 // solve.cu
 int assemble_system(dpg_handle* h, cudaStream_t s);
+int assemble_chunk(dpg_handle* h, int g, const int* ids, int count, cudaStream_t s);
+void system_changed(dpg_handle* h);
 int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, double inner_rtol,
              double2* x, const double2* b, dpg_cg_report* rep, cudaStream_t s);
 int estimate(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,

@@ -1053,6 +1053,30 @@ int alloc_workspace(dpg_handle* h) {
   w.cap = capmax;
   h->plan_valid = false;
   h->graph_valid = false;
+  if (h->stream) {
+    // chunk-sized element stores: slot k of a chunk of group g at k times the
+    // group's per-element sizes
+    size_t bS = 16, bs = 16, bZ = 16, bz = 16;
+    for (const Group& G : h->grp) {
+      const Sizes& S = G.sz;
+      bS = std::max(bS, sizeof(double2) * (size_t)S.n_h * S.n_h * G.cap);
+      bs = std::max(bs, sizeof(double2) * (size_t)S.n_h * G.cap);
+      bZ = std::max(bZ, sizeof(double2) * (size_t)S.n_u * S.n_h * G.cap);
+      bz = std::max(bz, sizeof(double2) * (size_t)S.n_u * G.cap);
+    }
+    void* olds[] = {h->d_S, h->d_s, h->d_Z, h->d_z};
+    for (void* b : olds)
+      if (b) cudaFree(b);
+    h->d_S = h->d_s = h->d_Z = h->d_z = nullptr;
+    if (cudaMalloc(&h->d_S, bS) != cudaSuccess || cudaMalloc(&h->d_s, bs) != cudaSuccess ||
+        cudaMalloc(&h->d_Z, bZ) != cudaSuccess || cudaMalloc(&h->d_z, bz) != cudaSuccess) {
+      cudaGetLastError();
+      h->err = "chunk store allocation failed";
+      return DPG_ERR_NOMEM;
+    }
+    // the slot offsets of the stores come with the plan
+    return build_plan(h);
+  }
   return DPG_OK;
 }
 
@@ -1139,8 +1163,10 @@ static int run_robin(dpg_handle* h, int g, const int* ids_host, int count, cudaS
   return DPG_OK;
 }
 
+// quad = false reuses the quadrature matrices already in the workspace (the
+// same chunk was formed just before) and only forms K again.
 int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s, bool factor,
-                      bool extract, bool real, const ChunkPlan* cp) {
+                      bool extract, bool real, const ChunkPlan* cp, bool quad) {
   Workspace& w = h->ws;
   const Group& G = h->grp[g];
   const Sizes& S = G.sz;
@@ -1148,58 +1174,60 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
   // element ids of the chunk: the plan's device list, or a copy of the host list
   const int* ids = cp ? cp->d_ids + cp->ids_off : w.ids;
   if (!cp) DPG_CUDA_TRY(h, cudaMemcpyAsync(w.ids, ids_host, sizeof(int) * count, cudaMemcpyHostToDevice, s));
-  const size_t nq3 = 3 * (size_t)S.nq;
-  const bool fp64q = h->prec == DPG_PREC_FP64;
-  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(G.tab, S, h->d_X, ids, w.V, w.Cu, w.PhiL,
-                                                                   fp64q ? w.F : nullptr, fp64q ? w.KW : nullptr);
-  const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
-  const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
-  const int nL3 = 3 * S.nL;
-  // M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL (FP64, or the tensor cores)
-  if (h->prec == DPG_PREC_FP64) {
-    // M_ij = sum_q w det f_i f_j (J^{-1} J^{-T})_{c_i c_j}: test functions are
-    // component-major (n_f / 3 per reference component), so the upper triangle
-    // of M is six weighted products over the n_q points (one per component
-    // pair) instead of one product over 3 n_q rows
-    {
-      const int nc = S.n_f / 3;
-      const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
-      const long long sF = (long long)S.nq * S.n_f;
-      for (int k = 0; k < 6; ++k)
-        gemm_tn(nc, nc, S.nq, w.F + (size_t)pa[k] * nc, S.n_f, sF, w.F + (size_t)pb[k] * nc, S.n_f, sF,
-                w.MC + (size_t)pa[k] * nc * S.n_f + (size_t)pb[k] * nc, S.n_f, (long long)mcs, count, s,
-                pa[k] == pb[k] ? 1 : 0, w.KW + (size_t)k * S.nq, 6LL * S.nq);
-      h->launches += 5;
-    }
-    gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f, S.n_f,
-            (long long)mcs, count, s, 1);
-    // PhiL is block diagonal over the component d (row q*3+d holds s_q L_l(q) in
-    // columns d nL + l only): P[:, d nL + l] = sum_q V[q*3+d][:] PhiL[q*3+d][d nL + l],
-    // one K = n_q product per d (rows of stride 3) instead of K = 3 n_q over the zero blocks
-    const int nL = S.nL;
-    for (int d = 0; d < 3; ++d) {
-      gemm_tn(S.n_f, nL, S.nq, w.V + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
-              3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)d * nL, nL3, (long long)mcs, count, s);
-      gemm_tn(S.n_f, nL, S.nq, w.Cu + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
-              3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3 + (size_t)d * nL, nL3,
-              (long long)mcs, count, s);
-    }
-    h->launches += 4;
-  } else {
-    const int split = h->prec == DPG_PREC_3XTF32 ? 3 : 1;
-    int* terr = h->d_status + h->ne;
-    int rc = 0;
-    rc |= gemm_tn_tc(split, S.n_f, S.n_f, (int)nq3, w.V, S.n_f, sV, w.V, S.n_f, sV, w.MC, S.n_f, (long long)mcs,
-                     count, 1, terr, s);
-    rc |= gemm_tn_tc(split, S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f,
-                     S.n_f, (long long)mcs, count, 1, terr, s);
-    rc |= gemm_tn_tc(split, S.n_f, nL3, (int)nq3, w.V, S.n_f, sV, w.PhiL, nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f,
-                     nL3, (long long)mcs, count, 0, terr, s);
-    rc |= gemm_tn_tc(split, S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
-                     w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, 0, terr, s);
-    if (rc) {
-      h->err = "tensor-core contraction launch failed";
-      return DPG_ERR_CUDA;
+  if (quad) {
+    const size_t nq3 = 3 * (size_t)S.nq;
+    const bool fp64q = h->prec == DPG_PREC_FP64;
+    k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(G.tab, S, h->d_X, ids, w.V, w.Cu, w.PhiL,
+                                                                     fp64q ? w.F : nullptr, fp64q ? w.KW : nullptr);
+    const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
+    const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
+    const int nL3 = 3 * S.nL;
+    // M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL (FP64, or the tensor cores)
+    if (h->prec == DPG_PREC_FP64) {
+      // M_ij = sum_q w det f_i f_j (J^{-1} J^{-T})_{c_i c_j}: test functions are
+      // component-major (n_f / 3 per reference component), so the upper triangle
+      // of M is six weighted products over the n_q points (one per component
+      // pair) instead of one product over 3 n_q rows
+      {
+        const int nc = S.n_f / 3;
+        const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+        const long long sF = (long long)S.nq * S.n_f;
+        for (int k = 0; k < 6; ++k)
+          gemm_tn(nc, nc, S.nq, w.F + (size_t)pa[k] * nc, S.n_f, sF, w.F + (size_t)pb[k] * nc, S.n_f, sF,
+                  w.MC + (size_t)pa[k] * nc * S.n_f + (size_t)pb[k] * nc, S.n_f, (long long)mcs, count, s,
+                  pa[k] == pb[k] ? 1 : 0, w.KW + (size_t)k * S.nq, 6LL * S.nq);
+        h->launches += 5;
+      }
+      gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f, S.n_f,
+              (long long)mcs, count, s, 1);
+      // PhiL is block diagonal over the component d (row q*3+d holds s_q L_l(q) in
+      // columns d nL + l only): P[:, d nL + l] = sum_q V[q*3+d][:] PhiL[q*3+d][d nL + l],
+      // one K = n_q product per d (rows of stride 3) instead of K = 3 n_q over the zero blocks
+      const int nL = S.nL;
+      for (int d = 0; d < 3; ++d) {
+        gemm_tn(S.n_f, nL, S.nq, w.V + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
+                3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)d * nL, nL3, (long long)mcs, count, s);
+        gemm_tn(S.n_f, nL, S.nq, w.Cu + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
+                3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3 + (size_t)d * nL, nL3,
+                (long long)mcs, count, s);
+      }
+      h->launches += 4;
+    } else {
+      const int split = h->prec == DPG_PREC_3XTF32 ? 3 : 1;
+      int* terr = h->d_status + h->ne;
+      int rc = 0;
+      rc |= gemm_tn_tc(split, S.n_f, S.n_f, (int)nq3, w.V, S.n_f, sV, w.V, S.n_f, sV, w.MC, S.n_f, (long long)mcs,
+                       count, 1, terr, s);
+      rc |= gemm_tn_tc(split, S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f,
+                       S.n_f, (long long)mcs, count, 1, terr, s);
+      rc |= gemm_tn_tc(split, S.n_f, nL3, (int)nq3, w.V, S.n_f, sV, w.PhiL, nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f,
+                       nL3, (long long)mcs, count, 0, terr, s);
+      rc |= gemm_tn_tc(split, S.n_f, nL3, (int)nq3, w.Cu, S.n_f, sV, w.PhiL, nL3, sP,
+                       w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3, nL3, (long long)mcs, count, 0, terr, s);
+      if (rc) {
+        h->err = "tensor-core contraction launch failed";
+        return DPG_ERR_CUDA;
+      }
     }
   }
   double* Kr = reinterpret_cast<double*>(w.K);
@@ -1249,16 +1277,16 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
   }
   if (extract) {
     if (real)
-      k_extract_real<<<count, 256, 0, s>>>(S, ids, Kr, h->d_off, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1,
+      k_extract_real<<<count, 256, 0, s>>>(S, ids, Kr, h->d_soff, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1,
                                            w.V);
     else
-      k_extract<<<count, 256, 0, s>>>(S, ids, w.K, h->d_off, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
+      k_extract<<<count, 256, 0, s>>>(S, ids, w.K, h->d_soff, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
     bool any = cp ? cp->restricted : false;
     for (int k = 0; !cp && k < count && !any; ++k) any = h->elem_sig[ids_host[k]] >= 0;
     if (any) {
-      k_restrict<<<count, 256, sizeof(double2) * S.n_h, s>>>(S.nt, S.n_u, ids, h->d_off, h->d_sig, h->d_rsig,
+      k_restrict<<<count, 256, sizeof(double2) * S.n_h, s>>>(S.nt, S.n_u, ids, h->d_soff, h->d_sig, h->d_rsig,
                                                             h->d_rint, h->d_rdbl, h->d_S, h->d_s, h->d_Z, w.K,
                                                             (size_t)S.N * S.N);
       DPG_CUDA_TRY(h, cudaGetLastError());
@@ -1293,23 +1321,48 @@ void free_plan(dpg_handle* h) {
 // first), their device id lists and Robin sub-batches.  Synchronous.
 static int make_chunks(dpg_handle* h, bool real, std::vector<ChunkPlan>& plan, int** d_ids, int** d_rent) {
   std::vector<int> ids_all, rent_all;
+  std::vector<ElemOff> soff;
+  if (h->stream) soff.assign(h->ne + 1, ElemOff{});
   for (int g = 0; g < (int)h->grp.size(); ++g) {
     const Group& G = h->grp[g];
-    const std::vector<int>* lists[2] = {&G.real_elems, &G.cplx_elems};
-    if (!real) {
-      lists[0] = &G.elems;
-      lists[1] = nullptr;
+    std::vector<std::vector<int>> lists;
+    if (real) {
+      lists.push_back(G.real_elems);
+      lists.push_back(G.cplx_elems);
+    } else {
+      lists.push_back(G.elems);
     }
-    for (int li = 0; li < 2; ++li) {
-      if (!lists[li]) continue;
-      const std::vector<int>& L = *lists[li];
+    if (h->stream) {  // one colour per chunk: its elements share no unknown
+      std::vector<std::vector<int>> by_colour;
+      for (const std::vector<int>& L : lists)
+        for (int c = 0; c < h->ncolor; ++c) {
+          std::vector<int> part;
+          for (int e : L)
+            if (h->elem_color[e] == c) part.push_back(e);
+          if (!part.empty()) by_colour.push_back(part);
+        }
+      lists = by_colour;
+    }
+    for (size_t li = 0; li < lists.size(); ++li) {
+      const std::vector<int>& L = lists[li];
+      const bool is_real_list = real && !L.empty() && h->is_real[L[0]];
       for (size_t c0 = 0; c0 < L.size(); c0 += G.cap) {
         ChunkPlan cp;
         cp.g = g;
-        cp.real = real && li == 0;
+        cp.real = is_real_list;
         cp.count = (int)std::min<size_t>(G.cap, L.size() - c0);
         cp.ids_off = (int64_t)ids_all.size();
         ids_all.insert(ids_all.end(), L.begin() + c0, L.begin() + c0 + cp.count);
+        if (h->stream)
+          for (int k = 0; k < cp.count; ++k) {
+            const Sizes& S = G.sz;
+            ElemOff& o = soff[L[c0 + k]];
+            o.S = (int64_t)k * S.n_h * S.n_h;
+            o.Z = (int64_t)k * S.n_u * S.n_h;
+            o.L1 = 0;
+            o.h = (int64_t)k * S.n_h;
+            o.u = (int64_t)k * S.n_u;
+          }
         for (int k = 0; k < cp.count && !cp.restricted; ++k) cp.restricted = h->elem_sig[L[c0 + k]] >= 0;
         if (!cp.real) {
           std::vector<std::vector<int>> rents, rlists;
@@ -1341,6 +1394,10 @@ static int make_chunks(dpg_handle* h, bool real, std::vector<ChunkPlan>& plan, i
     cp.d_ids = *d_ids;
     cp.d_rent = *d_rent;
   }
+  if (h->stream) {
+    DPG_CUDA_TRY(h, cudaMemcpy(h->d_soff, soff.data(), sizeof(ElemOff) * soff.size(), cudaMemcpyHostToDevice));
+    h->soff_host = soff;
+  }
   return DPG_OK;
 }
 
@@ -1365,24 +1422,27 @@ int element_pass(dpg_handle* h, cudaStream_t s) {
     int rc = build_plan(h);
     if (rc) return rc;
   }
-  if (!h->use_graph) {
+  // streaming: the system is assembled chunk by chunk as the elements are condensed
+  auto pass = [&](cudaStream_t st) -> int {
+    if (h->stream) {
+      DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_val, 0, sizeof(double2) * h->nnz, st));
+      DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_b, 0, sizeof(double2) * h->n, st));
+    }
     for (const ChunkPlan& cp : h->plan) {
-      int rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, true, true, cp.real, &cp);
+      int rc = run_element_chunk(h, cp.g, nullptr, cp.count, st, true, true, cp.real, &cp);
+      if (rc == DPG_OK && h->stream) rc = assemble_chunk(h, cp.g, cp.d_ids + cp.ids_off, cp.count, st);
       if (rc) return rc;
     }
     return DPG_OK;
-  }
+  };
+  if (!h->use_graph) return pass(s);
   if (!h->graph_valid || h->graph_timing != h->timing) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     if (!h->cap_stream) DPG_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     DPG_CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     const int64_t l0 = h->launches;
-    int rc = DPG_OK;
-    for (const ChunkPlan& cp : h->plan) {
-      rc = run_element_chunk(h, cp.g, nullptr, cp.count, h->cap_stream, true, true, cp.real, &cp);
-      if (rc) break;
-    }
+    int rc = pass(h->cap_stream);
     cudaGraph_t gr = nullptr;
     cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &gr);
     if (rc == DPG_OK && ee != cudaSuccess) {
@@ -1508,17 +1568,20 @@ __device__ __forceinline__ double est_wsum(double v) {
 
 // u = z - Z uhat_slots for the elements of one group (one CTA per element).
 __global__ void __launch_bounds__(256) k_recover_u(int nh, int nu, const int* __restrict__ elems,
-                                                   const ElemOff* __restrict__ off, const int32_t* __restrict__ l2g,
+                                                   const ElemOff* __restrict__ off, const ElemOff* __restrict__ soff,
+                                                   const int32_t* __restrict__ l2g,
                                                    const double2* __restrict__ xfix, const double2* __restrict__ xhat,
                                                    const double2* __restrict__ Zst, const double2* __restrict__ zst,
                                                    double2* u_out) {
   extern __shared__ double2 su_sh[];
   const int e = elems[blockIdx.x];
   const ElemOff of = off[e];
+  Zst += soff[e].Z;
+  zst += soff[e].u;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int t = threadIdx.x; t < nh; t += blockDim.x) su_sh[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
   __syncthreads();
-  const double2* Ze = Zst + of.Z;
+  const double2* Ze = Zst;
   for (int i = wid; i < nu; i += nw) {
     double yr = 0.0, yi = 0.0;
     for (int j = lane; j < nh; j += 32) {
@@ -1529,7 +1592,7 @@ __global__ void __launch_bounds__(256) k_recover_u(int nh, int nu, const int* __
     yr = est_wsum(yr);
     yi = est_wsum(yi);
     if (lane == 0) {
-      const double2 zi = zst[of.u + i];
+      const double2 zi = zst[i];
       u_out[of.u + i] = make_double2(zi.x - yr, zi.y - yi);
     }
   }
@@ -1540,7 +1603,8 @@ __global__ void __launch_bounds__(256) k_recover_u(int nh, int nu, const int* __
 // (B[i][j] = conj(K[n_v + j][i]), l_i = conj(K[N-1][i])); K[n_v][i] = conj(r_i),
 // K[n_v][n_v] = 0.
 __global__ void __launch_bounds__(256) k_est_residual(Sizes S, const int* __restrict__ ids,
-                                                      const ElemOff* __restrict__ off, const int* __restrict__ sig,
+                                                      const ElemOff* __restrict__ off,
+                                                      const ElemOff* __restrict__ soff, const int* __restrict__ sig,
                                                       const RSig* __restrict__ rsig, const int32_t* __restrict__ rint,
                                                       const double* __restrict__ rdbl, const int32_t* __restrict__ l2g,
                                                       const double2* __restrict__ xfix,
@@ -1557,7 +1621,7 @@ __global__ void __launch_bounds__(256) k_est_residual(Sizes S, const int* __rest
   double2* A = K + (size_t)slot * N * N;
   for (int t = threadIdx.x; t < nh; t += blockDim.x) us[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
   __syncthreads();
-  const double2* Ze = Zst + of.Z;
+  const double2* Ze = Zst + soff[e].Z;
   for (int i = wid; i < nu; i += nw) {
     double yr = 0.0, yi = 0.0;
     for (int j = lane; j < nh; j += 32) {
@@ -1568,7 +1632,7 @@ __global__ void __launch_bounds__(256) k_est_residual(Sizes S, const int* __rest
     yr = est_wsum(yr);
     yi = est_wsum(yi);
     if (lane == 0) {
-      const double2 zi = zst[of.u + i];
+      const double2 zi = zst[soff[e].u + i];
       const double2 ui = make_double2(zi.x - yr, zi.y - yi);
       w[i] = ui;
       if (u_out) u_out[of.u + i] = ui;
@@ -1621,6 +1685,7 @@ __global__ void __launch_bounds__(256) k_est_residual(Sizes S, const int* __rest
 // rows n_v and n_v + 1 of K_r (two more columns of the real factorisation).
 __global__ void __launch_bounds__(256) k_est_residual_real(Sizes S, const int* __restrict__ ids,
                                                            const ElemOff* __restrict__ off,
+                                                           const ElemOff* __restrict__ soff,
                                                            const int* __restrict__ sig, const RSig* __restrict__ rsig,
                                                            const int32_t* __restrict__ rint,
                                                            const double* __restrict__ rdbl,
@@ -1639,7 +1704,7 @@ __global__ void __launch_bounds__(256) k_est_residual_real(Sizes S, const int* _
   double* A = K + (size_t)slot * N * N;
   for (int t = threadIdx.x; t < nh; t += blockDim.x) us[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
   __syncthreads();
-  const double2* Ze = Zst + of.Z;
+  const double2* Ze = Zst + soff[e].Z;
   for (int i = wid; i < nu; i += nw) {
     double yr = 0.0, yi = 0.0;
     for (int j = lane; j < nh; j += 32) {
@@ -1650,7 +1715,7 @@ __global__ void __launch_bounds__(256) k_est_residual_real(Sizes S, const int* _
     yr = est_wsum(yr);
     yi = est_wsum(yi);
     if (lane == 0) {
-      const double2 zi = zst[of.u + i];
+      const double2 zi = zst[soff[e].u + i];
       const double2 ui = make_double2(zi.x - yr, zi.y - yi);
       if (u_out) u_out[of.u + i] = ui;
       w[i] = i < nE ? make_double2(-ui.y, ui.x) : ui;  // times conj(-i) = i on E
@@ -1727,13 +1792,31 @@ __global__ void k_est_eta(int count, int N, int nv, const int* __restrict__ ids,
   eta2[ids[slot]] = v;
 }
 
-void recover_u(dpg_handle* h, const double2* xhat, double2* u, cudaStream_t s) {
+int recover_u(dpg_handle* h, const double2* xhat, double2* u, cudaStream_t s) {
+  if (h->stream) {  // condense every chunk again into the chunk stores, then recover
+    if (!h->plan_valid) {
+      int rc = build_plan(h);
+      if (rc) return rc;
+    }
+    for (const ChunkPlan& cp : h->plan) {
+      const Sizes& S = h->grp[cp.g].sz;
+      int rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, true, true, cp.real, &cp);
+      if (rc) return rc;
+      k_recover_u<<<cp.count, 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, cp.d_ids + cp.ids_off, h->d_off,
+                                                                  h->d_soff, h->d_l2g, h->d_xfix, xhat, h->d_Z,
+                                                                  h->d_z, u);
+      h->launches += 1;
+    }
+    return DPG_OK;
+  }
   for (const Group& G : h->grp) {
     const Sizes& S = G.sz;
     k_recover_u<<<(int)G.elems.size(), 256, sizeof(double2) * S.n_h, s>>>(S.n_h, S.n_u, G.d_elems, h->d_off,
-                                                                          h->d_l2g, h->d_xfix, xhat, h->d_Z, h->d_z, u);
+                                                                          h->d_off, h->d_l2g, h->d_xfix, xhat,
+                                                                          h->d_Z, h->d_z, u);
     h->launches += 1;
   }
+  return DPG_OK;
 }
 
 // The estimator's recompute pass over the est_plan chunks: eta_K^2 into eta2[e]
@@ -1747,17 +1830,27 @@ int estimate_pass(dpg_handle* h, const double2* xhat, double2* u, double* eta2, 
   for (const ChunkPlan& cp : h->plan) {
     const Group& G = h->grp[cp.g];
     const Sizes& S = G.sz;
-    int rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, false, false, cp.real, &cp);
+    int rc = DPG_OK;
+    if (h->stream) {
+      // the chunk's Z, z again (condensation into the chunk stores), then K
+      // formed again from the same quadrature matrices
+      rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, true, true, cp.real, &cp);
+      if (rc == DPG_OK) rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, false, false, cp.real, &cp, false);
+    } else {
+      rc = run_element_chunk(h, cp.g, nullptr, cp.count, s, false, false, cp.real, &cp);
+    }
     if (rc) return rc;
     const int* ids = cp.d_ids + cp.ids_off;
     const size_t sh = sizeof(double2) * (size_t)(S.n_u + 2 * S.n_h);
     double* Kr = reinterpret_cast<double*>(h->ws.K);
     const int extra = cp.real ? 2 : 1;  // columns after G: Re r, Im r (real path) or r
     if (cp.real)
-      k_est_residual_real<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_sig, h->d_rsig, h->d_rint, h->d_rdbl,
+      k_est_residual_real<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_soff, h->d_sig, h->d_rsig, h->d_rint,
+                                                    h->d_rdbl,
                                                     h->d_l2g, h->d_xfix, xhat, h->d_Z, h->d_z, Kr, u);
     else
-      k_est_residual<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_sig, h->d_rsig, h->d_rint, h->d_rdbl, h->d_l2g,
+      k_est_residual<<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_soff, h->d_sig, h->d_rsig, h->d_rint, h->d_rdbl,
+                                               h->d_l2g,
                                                h->d_xfix, xhat, h->d_Z, h->d_z, h->ws.K, u);
     if (h->factor_arith == DPG_FACTOR_TC_SPLIT) {
       if (factor_tc_launch(!cp.real, cp.count, S.N, S.n_v + extra, S.n_v, S.n_v, ids,

@@ -934,6 +934,7 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
     }
     // per group: its elements sorted by colour
     h->ncolor = ncol;
+    h->elem_color = color;
     for (Group& G : h->grp) {
       G.color_off.assign(ncol + 1, 0);
       for (int e : G.elems) G.color_off[color[e] + 1]++;
@@ -1039,15 +1040,26 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   DPG_ALLOC(h->d_mu, sizeof(double2) * ne);
   DPG_ALLOC(h->d_fbc, 6 * (size_t)ne);
   DPG_ALLOC(h->d_off, sizeof(ElemOff) * (ne + 1));
+  if (h->stream)
+    DPG_ALLOC(h->d_soff, sizeof(ElemOff) * (ne + 1));  // filled with the launch plan
+  else
+    h->d_soff = h->d_off;
   DPG_ALLOC(h->d_l2g, sizeof(int32_t) * tot.h);
   DPG_ALLOC(h->d_xfix, sizeof(double2) * tot.h);
   DPG_ALLOC(h->d_robin, sizeof(dpg_robin_group) * std::max<size_t>(1, h->robin.size()));
   DPG_ALLOC(h->d_status, sizeof(int) * (ne + 1));  // [ne]: tensor-core wait timeout flag
-  DPG_ALLOC(h->d_S, sizeof(double2) * tot.S);
-  DPG_ALLOC(h->d_s, sizeof(double2) * tot.h);
+  h->stream = (prm->flags & DPG_FLAG_STREAM) != 0;
+  if (h->stream && (prm->flags & DPG_FLAG_ADJOINT)) {
+    h->err = "DPG_FLAG_STREAM does not keep the factors the adjoint needs (DPG_FLAG_ADJOINT)";
+    return DPG_ERR_UNSUPPORTED;
+  }
+  if (!h->stream) {  // streaming allocates chunk-sized stores with the workspace
+    DPG_ALLOC(h->d_S, sizeof(double2) * tot.S);
+    DPG_ALLOC(h->d_s, sizeof(double2) * tot.h);
+    DPG_ALLOC(h->d_Z, sizeof(double2) * tot.Z);
+    DPG_ALLOC(h->d_z, sizeof(double2) * tot.u);
+  }
   DPG_ALLOC(h->d_c, sizeof(double) * ne);
-  DPG_ALLOC(h->d_Z, sizeof(double2) * tot.Z);
-  DPG_ALLOC(h->d_z, sizeof(double2) * tot.u);
   if (prm->flags & DPG_FLAG_ADJOINT) DPG_ALLOC(h->d_L1, sizeof(double2) * tot.L1);
   DPG_ALLOC(h->d_sig, sizeof(int) * ne);
   DPG_ALLOC(h->d_rsig, sizeof(RSig) * std::max<size_t>(1, h->rsig.size()));

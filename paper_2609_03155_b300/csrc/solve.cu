@@ -37,7 +37,10 @@ __device__ __forceinline__ int64_t csr_pos(const int64_t* __restrict__ rowptr, c
 // One block per element of one colour: elements of a colour share no
 // unknowns, so the plain read-modify-write below has no race and the sum
 // order per entry is the fixed colour order.
+// off: the element's trace-map offsets; soff: its store offsets (the same
+// table, or the slot-based one of the streaming mode).
 __global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict__ elems, const ElemOff* __restrict__ off,
+                                                  const ElemOff* __restrict__ soff,
                                                   const int32_t* __restrict__ l2g, const double2* __restrict__ xfix,
                                                   const double2* __restrict__ Sst, const double2* __restrict__ sst,
                                                   const int64_t* __restrict__ rowptr,
@@ -47,8 +50,8 @@ __global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict_
   const int e = elems[blockIdx.x];
   const ElemOff of = off[e];
   const int32_t* g = l2g + of.h;
-  const double2* Se = Sst + of.S;
-  sst += of.h;
+  const double2* Se = Sst + soff[e].S;
+  sst += soff[e].h;
   xfix += of.h;
   for (int t = threadIdx.x; t < nh * nh; t += blockDim.x) {
     const int i = t / nh, j = t - i * nh;
@@ -71,7 +74,27 @@ __global__ void __launch_bounds__(256) k_assemble(int nh, const int* __restrict_
   }
 }
 
+// Assembly of one colour-homogeneous chunk as it is condensed (streaming mode).
+int assemble_chunk(dpg_handle* h, int g, const int* ids, int count, cudaStream_t s) {
+  k_assemble<<<count, 256, 0, s>>>(h->grp[g].sz.n_h, ids, h->d_off, h->d_soff, h->d_l2g, h->d_xfix, h->d_S, h->d_s,
+                                   h->d_rowptr, h->d_row2blk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_val, h->d_b);
+  h->launches += 1;
+  DPG_CUDA_TRY(h, cudaGetLastError());
+  return DPG_OK;
+}
+
+void system_changed(dpg_handle* h) {
+  h->have_system = true;
+  h->have_val32 = false;
+  h->have_val32h = false;
+  h->have_valdw = false;
+  h->have_binvdw = false;
+  h->have_dinv = false;
+  h->have_binv = false;
+}
+
 int assemble_system(dpg_handle* h, cudaStream_t s) {
+  if (h->stream) return DPG_OK;  // assembled by the element pass
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_val, 0, sizeof(double2) * h->nnz, s));
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_b, 0, sizeof(double2) * h->n, s));
   // colour by colour; within a colour one launch per order group (the
@@ -80,19 +103,14 @@ int assemble_system(dpg_handle* h, cudaStream_t s) {
     for (const Group& G : h->grp) {
       const int cnt = G.color_off[c + 1] - G.color_off[c];
       if (cnt == 0) continue;
-      k_assemble<<<cnt, 256, 0, s>>>(G.sz.n_h, G.d_color_elems + G.color_off[c], h->d_off, h->d_l2g, h->d_xfix,
+      k_assemble<<<cnt, 256, 0, s>>>(G.sz.n_h, G.d_color_elems + G.color_off[c], h->d_off, h->d_off, h->d_l2g,
+                                     h->d_xfix,
                                      h->d_S, h->d_s, h->d_rowptr, h->d_row2blk, h->d_blk, h->d_blk_colptr, h->d_cols,
                                      h->d_val, h->d_b);
       h->launches += 1;
     }
   DPG_CUDA_TRY(h, cudaGetLastError());
-  h->have_system = true;
-  h->have_val32 = false;
-  h->have_val32h = false;
-  h->have_valdw = false;
-  h->have_binvdw = false;
-  h->have_dinv = false;
-  h->have_binv = false;
+  system_changed(h);
   return DPG_OK;
 }
 
@@ -1381,7 +1399,10 @@ __global__ void k_sqrt_sum(int n, const double* __restrict__ eta2, double* eta, 
 static int estimate_into(dpg_handle* h, const double2* xhat, double2* u, double* eta, double* eta_global,
                          double* eta2, cudaStream_t s) {
   if (!eta && !eta_global) {  // recovery only
-    if (u) recover_u(h, xhat, u, s);
+    if (u) {
+      const int rc = recover_u(h, xhat, u, s);
+      if (rc) return rc;
+    }
     DPG_CUDA_TRY(h, cudaGetLastError());
     return DPG_OK;
   }

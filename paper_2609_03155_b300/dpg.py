@@ -49,7 +49,7 @@ def element_sizes(p, dp=1):
 class DPG:
     """A DPG discretisation living on the current CUDA device (dpg_handle)."""
 
-    def __init__(self, mesh, alpha=1.0, chunk=0, adjoint=False, precision=0, stream=None):
+    def __init__(self, mesh, alpha=1.0, chunk=0, adjoint=False, precision=0, stream=None, streaming=False):
         L = _lib.lib()
         self.mesh = mesh
         keep = dict(
@@ -69,7 +69,7 @@ class DPG:
             n_robin=len(mesh.robin), robin=C.cast(rob, C.POINTER(_lib.dpg_robin_group)),
             n_dirichlet=len(mesh.dirichlet), dirichlet=C.cast(dirg, C.POINTER(_lib.dpg_dirichlet_group)))
         prm = _lib.dpg_params(omega=float(mesh.omega), alpha=float(alpha), dp=1, precision=int(precision), chunk=int(chunk),
-                              flags=_lib.DPG_FLAG_ADJOINT if adjoint else 0)
+                              flags=(_lib.DPG_FLAG_ADJOINT if adjoint else 0) | (_lib.DPG_FLAG_STREAM if streaming else 0))
         h = C.c_void_p()
         check(L.dpg_setup_mesh(C.byref(h), C.byref(desc), C.byref(prm), stream_handle(stream)))
         self.h = h

@@ -1,0 +1,75 @@
+"""Element-level parity at the stated sizes of the cavity, Fichera and obstacle configurations.
+
+The meshes are set up at full size in the streaming mode (no per-element
+condensation data is stored) and a few sampled elements are formed and
+condensed on the GPU and compared one by one with the oracle: G_K, B_K,
+B-hat_K, l_K at relative 1e-12 and S_K within 2 eps kappa(G_K).  Sizes: the
+32^3 sub-box of the jittered p = 3 cavity with random lossy permittivity
+(32,768 elements), the Fichera cavity with one level of 2:1 refinement near the
+re-entrant corner and degrees 1..4 (108,149 elements), and the 64^3 cavity
+with the eps = 20 + 5i sphere (262,144 elements).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import element as oel
+from oracle import system as osys
+from paper_2609_03155_b300 import inputs
+from test_gpu_parity import rel, s_bound
+
+
+@pytest.fixture(scope="module")
+def dpg_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_03155_b300 import dpg
+    return dpg
+
+
+def _check(mesh, out, ids, with_S):
+    for k, e in enumerate(ids):
+        el = oel.element_matrices(mesh.vert[mesh.elem[e]], int(mesh.p[e]), mesh.omega, complex(mesh.eps[e]),
+                                  complex(mesh.mu[e]), osys.element_faces(mesh, e))
+        assert rel(out['G'][k], el.G) < 1e-12
+        assert rel(out['B'][k], el.B) < 1e-12
+        assert rel(out['Bh'][k], el.Bh) < 1e-12
+        if with_S[k]:
+            cond = oel.condense(el)
+            assert rel(out['S'][k], cond['S']) < s_bound(el), (e, rel(out['S'][k], cond['S']), s_bound(el))
+
+
+def test_cavity3_subbox_32cubed_sampled_elements(dpg_mod):
+    mesh = inputs.cavity(32, 3, jitter=0.1, eps_mode='random')
+    d = dpg_mod.DPG(mesh, streaming=True)
+    ids = [0, 32 * 32 * 16 + 32 * 16 + 16, mesh.n_elem - 1]
+    out = d.element_dump(ids)
+    d.destroy()
+    _check(mesh, out, ids, [True] * len(ids))
+
+
+def test_fichera_amr_1e5_sampled_elements(dpg_mod):
+    mesh = inputs.fichera_amr(20, radius=0.6)
+    assert mesh.n_elem > 100000
+    d = dpg_mod.DPG(mesh, streaming=True)
+    m, _ = d.trace_map()
+    for p in (1, 2, 3, 4):
+        cand = [e for e in np.where(mesh.p == p)[0][:400]
+                if not np.any(m[d.h_off[e]:d.h_off[e + 1]] == -2)][:1]  # no lower-order or hanging entity
+        cand += [int(np.where(mesh.p == p)[0][-1])]
+        out = d.element_dump(cand)
+        _check(mesh, out, cand, [True] + [False] * (len(cand) - 1))
+    d.destroy()
+
+
+def test_obstacle_64cubed_sampled_elements(dpg_mod):
+    mesh = inputs.cavity(64, 2)
+    inputs.sphere_obstacle(mesh, radius=0.2, eps=20.0 + 5.0j)
+    d = dpg_mod.DPG(mesh, streaming=True)
+    inside = np.where(mesh.eps.imag > 0)[0]
+    ids = [0, int(inside[0]), int(inside[len(inside) // 2]), mesh.n_elem - 1]
+    out = d.element_dump(ids)
+    d.destroy()
+    _check(mesh, out, ids, [True] * len(ids))

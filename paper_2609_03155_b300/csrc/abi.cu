@@ -44,7 +44,7 @@ static void free_all(dpg_handle* h) {
                   h->d_valdw, h->d_pdw, h->d_binvdw};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  if (h->stream && h->d_soff) cudaFree(h->d_soff);
+  if (h->d_soff && h->d_soff != h->d_off) cudaFree(h->d_soff);
 }
 
 extern "C" int dpg_setup_mesh(dpg_handle** out, const dpg_mesh_desc* m, const dpg_params* prm, dpg_stream st) {

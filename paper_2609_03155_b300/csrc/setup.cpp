@@ -1039,6 +1039,7 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   DPG_ALLOC(h->d_eps, sizeof(double2) * ne);
   DPG_ALLOC(h->d_mu, sizeof(double2) * ne);
   DPG_ALLOC(h->d_fbc, 6 * (size_t)ne);
+  h->stream = (prm->flags & DPG_FLAG_STREAM) != 0;
   DPG_ALLOC(h->d_off, sizeof(ElemOff) * (ne + 1));
   if (h->stream)
     DPG_ALLOC(h->d_soff, sizeof(ElemOff) * (ne + 1));  // filled with the launch plan
@@ -1048,7 +1049,6 @@ int build_mesh(dpg_handle* h, const dpg_mesh_desc* m, const dpg_params* prm, cud
   DPG_ALLOC(h->d_xfix, sizeof(double2) * tot.h);
   DPG_ALLOC(h->d_robin, sizeof(dpg_robin_group) * std::max<size_t>(1, h->robin.size()));
   DPG_ALLOC(h->d_status, sizeof(int) * (ne + 1));  // [ne]: tensor-core wait timeout flag
-  h->stream = (prm->flags & DPG_FLAG_STREAM) != 0;
   if (h->stream && (prm->flags & DPG_FLAG_ADJOINT)) {
     h->err = "DPG_FLAG_STREAM does not keep the factors the adjoint needs (DPG_FLAG_ADJOINT)";
     return DPG_ERR_UNSUPPORTED;

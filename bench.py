@@ -100,6 +100,37 @@ def flops_factor_per_element(p):
             + 4 * nu ** 3 / 3 + 4 * nu ** 2 * (nh + 1) + 4 * nu * (nh + 1) ** 2)
 
 
+def tc_mma_flops_per_element(p, cplx):
+    """FP16 tensor-core flops one element's split-arithmetic factorisation issues.
+
+    The tile schedule of k_factor_tc: panels of 32 pivots (the first stage
+    stops at n_v), then for the rows below a panel, 128-row blocks times
+    NJ-column tiles up to the block's diagonal (NJ = 32 real, 16 complex);
+    each tile takes the 28 digit pairs (a, b) with a + b <= 6 of the seven
+    base-256 digits, each pair one 128 x NJ x 32 product (real) or four
+    128 x 16 x 32 products (complex: real part over the stacked Re/Im
+    columns, imaginary part as two cross products).  Equal to ncu's
+    sm__ops_path_tensor_op_utchmma_src_fp16_dst_fp32 count on the 979-row
+    p = 2 element.
+    """
+    rt, r = p + 2, p + 1
+    nv = 2 * 3 * rt * (rt + 1) ** 2
+    nu = 6 * (p + 1) ** 3
+    nh = 24 * r * r
+    N = nv + nu + nh + 1
+    TB, TM = 32, 128
+    NJ = 16 if cplx else 32
+    per_tile = 28 * (8 * 2 * TM * NJ * 16 if cplx else 2 * 2 * TM * NJ * 16)
+    k0, tot = 0, 0
+    while k0 < nv + nu:
+        k1 = k0 + min(TB, (nv if k0 < nv else nv + nu) - k0)
+        R = N - k1
+        for rho in range(0, R, TM):
+            tot += (min(rho + TM, R) + NJ - 1) // NJ * per_tile
+        k0 = k1
+    return tot
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -405,15 +436,43 @@ def main():
     fac_avg_ms = tim["factor_ms"] / max(1, tim["factor_launches"])
     fac_flops = float(fpe_el.sum()) * tim["factor_elements"] / mesh.n_elem
     fac_achieved = fac_flops / max(1e-9, tim["factor_ms"] / 1e3) / 1e12
-    roof_fac = {"bound": "alu", "kernel": "k_factor<double|double2> (blocked partial Cholesky + condensation, FP64 pipe)",
-                "achieved": fac_achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s", "frac": fac_achieved / (fp64 / 1e12),
-                "peak_source": "FP64 FMA throughput measured live by dpg_probe_peaks (DFMA loop)", "traffic": None,
-                "flops_per_element_complex": fpe if len(pvals) == 1 else {str(q): flops_factor_per_element(q)
-                                                                                for q in pvals},
-                "flops_per_element_real": fpe / 4 if len(pvals) == 1 else "a quarter of the complex figure",
-                "elements_real": n_real,
-                "elements_complex": n_cplx, "launches": tim["factor_launches"], "avg_launch_ms": fac_avg_ms,
-                "time_s": tim["factor_ms"] / 1e3}
+    common = {"flops_per_element_complex": fpe if len(pvals) == 1 else {str(q): flops_factor_per_element(q)
+                                                                          for q in pvals},
+              "flops_per_element_real": fpe / 4 if len(pvals) == 1 else "a quarter of the complex figure",
+              "elements_real": n_real, "elements_complex": n_cplx, "launches": tim["factor_launches"],
+              "avg_launch_ms": fac_avg_ms, "time_s": tim["factor_ms"] / 1e3}
+    if d.factor_arith == 1:
+        # trailing updates on the FP16 tensor cores through the exact digit
+        # split: the ceiling is the tensor rate of the issued digit-pair MMAs
+        # (FP16 runs at the bf16 rate); the FP64-equivalent rate is reported
+        # beside it
+        bf16_peak, bf16_src = 1800.0, "fallback 1.8 PFLOP/s bf16 (no MEASURED_PEAKS.json)"
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak = float(json.load(f)["bf16_tflops"])
+                bf16_src = "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 burst; FP16 MMAs run at the same rate)"
+        except Exception:
+            pass
+        is_cplx = ~is_real
+        tc_el = np.array([tc_mma_flops_per_element(int(q), bool(c)) for q, c in zip(mesh.p, is_cplx)], float)
+        tc_flops = float(tc_el.sum()) * tim["factor_elements"] / mesh.n_elem
+        tc_ach = tc_flops / max(1e-9, tim["factor_ms"] / 1e3) / 1e12
+        roof_fac = {"bound": "tensor", "kernel": "k_factor_tc<double|double2> (blocked partial Cholesky + "
+                    "condensation; trailing updates as FP16 digit-pair MMAs on tcgen05)",
+                    "achieved": tc_ach, "peak": bf16_peak, "unit": "TFLOP/s", "frac": tc_ach / bf16_peak,
+                    "peak_source": bf16_src, "traffic": None,
+                    "mma_flops_rule": "28 digit pairs x 128-row tiles of the lower trailing triangle per panel",
+                    "mma_flops_per_element_real": tc_mma_flops_per_element(p, False),
+                    "mma_flops_per_element_complex": tc_mma_flops_per_element(p, True),
+                    "fp64_equivalent_tflops": fac_achieved,
+                    "fp64_equivalent_vs_dfma_peak": fac_achieved / (fp64 / 1e12),
+                    "dfma_peak_tflops": fp64 / 1e12, **common}
+    else:
+        roof_fac = {"bound": "alu", "kernel": "k_factor<double|double2> (blocked partial Cholesky + condensation, "
+                    "FP64 pipe)", "achieved": fac_achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s",
+                    "frac": fac_achieved / (fp64 / 1e12),
+                    "peak_source": "FP64 FMA throughput measured live by dpg_probe_peaks (DFMA loop)",
+                    "traffic": None, **common}
     # persistent CG kernel (HBM bound).  Algorithmic bytes per iteration
     # (the method's own traffic): the matrix values, 16 B per complex FP64
     # non-zero or 8 B per complex FP32 non-zero of the inner solves, plus six
@@ -638,7 +697,7 @@ def complex_path_rate(mesh, args):
     fpe = flops_factor_per_element(p)
     return {"elements": int(slab.n_elem), "workload": f"{nx}x{ny}x4 slab of the same guide, real path off",
             "elements_per_s": slab.n_elem / (ms / 1e3), "element_pass_s": ms / 1e3,
-            "factor_tflops": fpe * tim["factor_elements"] / max(1e-9, tim["factor_ms"] / 1e3) / 1e12}
+            "factor_fp64_equivalent_tflops": fpe * tim["factor_elements"] / max(1e-9, tim["factor_ms"] / 1e3) / 1e12}
 
 
 def fp64_comparison(d, x, args):

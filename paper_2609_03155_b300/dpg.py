@@ -52,6 +52,7 @@ class DPG:
     def __init__(self, mesh, alpha=1.0, chunk=0, adjoint=False, precision=0, stream=None, streaming=False):
         L = _lib.lib()
         self.mesh = mesh
+        self.factor_arith = _lib.DPG_FACTOR_TC_SPLIT  # the library's default
         keep = dict(
             vert=np.ascontiguousarray(mesh.vert, dtype=np.float64),
             elem=np.ascontiguousarray(mesh.elem, dtype=np.int32),
@@ -151,6 +152,7 @@ class DPG:
 
     def set_factor_arith(self, arith=_lib.DPG_FACTOR_TC_SPLIT):
         check(_lib.lib().dpg_set_factor_arith(self.h, int(arith)), self.h)
+        self.factor_arith = int(arith)
 
     def set_wait_limit(self, wait_ns=5_000_000_000, hold=False):
         check(_lib.lib().dpg_set_wait_limit(self.h, int(wait_ns), int(hold)), self.h)

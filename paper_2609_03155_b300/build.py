@@ -9,7 +9,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = ["tables.cpp", "setup.cpp", "element.cu", "factor_tc.cu", "quad_tc.cu", "solve.cu", "adjoint.cu", "power.cu", "abi.cu"]
+SOURCES = ["tables.cpp", "setup.cpp", "element.cu", "quad_sf.cu", "factor_tc.cu", "quad_tc.cu", "solve.cu", "adjoint.cu", "power.cu", "abi.cu"]
 LIB = os.path.join(HERE, "libdpg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

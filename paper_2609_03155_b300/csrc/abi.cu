@@ -36,7 +36,7 @@ static void free_all(dpg_handle* h) {
                   h->d_s,     h->d_c,     h->d_Z,    h->d_z,     h->d_rowptr, h->d_row2blk, h->d_val,
                   h->d_b,     h->d_val32, h->d_r,    h->d_p,     h->d_Ap,    h->d_r32,  h->d_p32,
                   h->d_Ap32,  h->d_x32,   h->d_red,  h->d_cgstate,  h->ws.K,    h->ws.V,   h->ws.Cu,
-                  h->ws.PhiL, h->ws.MC,   h->ws.ids, h->ws.FV,   h->ws.FR,   h->ws.rent,
+                  h->ws.PhiL, h->ws.MC,   h->ws.ids, h->ws.FV,   h->ws.FR,   h->ws.rent, h->ws.WQ,
                   h->d_dinv,  h->d_dinv32, h->d_L1, h->d_u, h->d_zg, h->d_gc, h->d_lam, h->d_rhs_adj,
                   h->d_Pk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_binv_ptr, h->d_binv, h->d_binv32,
                   h->d_zv, h->d_z32, h->d_d64, h->ws.Q, h->d_est_neg,

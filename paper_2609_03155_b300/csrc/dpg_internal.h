@@ -52,12 +52,13 @@ struct RobinEntry {  // one Robin face of one element
 struct Workspace {
   int cap = 0;               // elements per chunk
   double2* K = nullptr;      // cap x N x N augmented Hermitian system (column-major, lower used)
+  // V, Cu, PhiL: cap elements for the tensor-core quadrature, one element
+  // with FP64 quadrature (V also serves as the real-path extraction scratch)
   double* V = nullptr;       // cap x 3nq x n_f   sqrt(w detJ) psi
   double* Cu = nullptr;      // cap x 3nq x n_f   sqrt(w detJ) curl psi
   double* PhiL = nullptr;    // cap x 3nq x 3nL   sqrt(w detJ) L e_d
   double* MC = nullptr;      // cap x (2 n_f^2 + 2 n_f 3nL): M, C, P, Q
-  double* F = nullptr;       // cap x nq x n_f    sqrt(w detJ) f_i (scalar factor of each test function)
-  double* KW = nullptr;      // cap x 6 x nq      (J^{-1} J^{-T})_{cd}, pairs 00 11 22 01 02 12
+  double* WQ = nullptr;      // cap x 30 x nq     geometric weights of the sum-factorised quadrature
   int* ids = nullptr;        // cap element ids of the chunk
   // Robin face scratch (per Robin entry of the chunk)
   int rcap = 0;
@@ -280,6 +281,11 @@ int recover_u(dpg_handle* h, const double2* xhat, double2* u, cudaStream_t s);
 int power(dpg_handle* h, const double2* xhat, double* q, double* flux_host, cudaStream_t s);
 // factor_tc.cu
 int factor_tc_init();
+// Sum-factorised FP64 quadrature of M, C, P, Q (quad_sf.cu).
+int quad_sf_init();
+size_t quad_sf_weight_bytes(const Sizes& S);
+int quad_sf_launch(const Tables& T, const Sizes& S, const double* X, const int* ids, int count, double* WQ,
+                   double* MC, cudaStream_t s);
 size_t factor_tc_scratch_bytes(int N, bool cplx);
 int factor_tc_launch(bool cplx, int count, int N, int nact, int nv, int npiv, const int* ids, void* K, int* status,
                      int* tc_err, uint8_t* qscr, cudaStream_t s);

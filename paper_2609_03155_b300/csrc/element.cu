@@ -29,6 +29,7 @@
 #include <cstdio>
 
 #include "dpg_internal.h"
+#include "geom.cuh"
 
 namespace dpg {
 
@@ -83,47 +84,6 @@ __device__ __forceinline__ void ref_curl(int c, const double g[3], double cu[3])
   }
 }
 
-// Trilinear map of the corner coordinates X (8 x 3) at reference point xi.
-__device__ __forceinline__ void geom(const double* X, const double xi[3], double J[3][3], double x[3]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    x[a] = 0.0;
-    J[a][0] = J[a][1] = J[a][2] = 0.0;
-  }
-#pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    double f0 = (v & 1) ? xi[0] : 1.0 - xi[0], d0 = (v & 1) ? 1.0 : -1.0;
-    double f1 = (v & 2) ? xi[1] : 1.0 - xi[1], d1 = (v & 2) ? 1.0 : -1.0;
-    double f2 = (v & 4) ? xi[2] : 1.0 - xi[2], d2 = (v & 4) ? 1.0 : -1.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double Xa = X[3 * v + a];
-      x[a] += f0 * f1 * f2 * Xa;
-      J[a][0] += d0 * f1 * f2 * Xa;
-      J[a][1] += f0 * d1 * f2 * Xa;
-      J[a][2] += f0 * f1 * d2 * Xa;
-    }
-  }
-}
-
-__device__ __forceinline__ double inv3(const double J[3][3], double Ji[3][3]) {
-  double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-  double id = 1.0 / det;
-  Ji[0][0] = c00 * id;
-  Ji[1][0] = c01 * id;
-  Ji[2][0] = c02 * id;
-  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
-  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
-  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
-  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
-  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
-  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
-  return det;
-}
-
 // complex square root, principal branch
 __device__ __forceinline__ double2 csqrt(double2 z) {
   double m = hypot(z.x, z.y);
@@ -163,8 +123,7 @@ __device__ void te_fields(const dpg_robin_group& g, double omega, const double x
 constexpr int QB = 8;
 
 __global__ void __launch_bounds__(256) k_vol_arrays(const __grid_constant__ Tables T, Sizes S, const double* __restrict__ Xall,
-                                                    const int* __restrict__ ids, double* V, double* Cu, double* PhiL,
-                                                    double* Fs, double* KW) {
+                                                    const int* __restrict__ ids, double* V, double* Cu, double* PhiL) {
   const int slot = blockIdx.y;
   const int e = ids[slot];
   __shared__ double sX[24];
@@ -188,12 +147,6 @@ __global__ void __launch_bounds__(256) k_vol_arrays(const __grid_constant__ Tabl
           sJs[threadIdx.x][3 * a + b] = J[a][b] * (s / det);
         }
       sw[threadIdx.x] = s;
-      if (KW) {  // metric of the covariant map, for the component-pair mass products
-        const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
-        for (int k = 0; k < 6; ++k)
-          KW[((size_t)slot * 6 + k) * nq + q] =
-              Ji[pa[k]][0] * Ji[pb[k]][0] + Ji[pa[k]][1] * Ji[pb[k]][1] + Ji[pa[k]][2] * Ji[pb[k]][2];
-      }
     }
   }
   __syncthreads();
@@ -219,7 +172,6 @@ __global__ void __launch_bounds__(256) k_vol_arrays(const __grid_constant__ Tabl
       Ve[((size_t)q * 3 + a) * nf + i] = s * Ji[3 * c + a] * f;  // (J^{-T})_{a c} = (J^{-1})_{c a}
       Ce[((size_t)q * 3 + a) * nf + i] = Js[3 * a + 0] * cr[0] + Js[3 * a + 1] * cr[1] + Js[3 * a + 2] * cr[2];
     }
-    if (Fs) Fs[(size_t)slot * nq * nf + (size_t)q * nf + i] = s * f;
   }
   const int nL = S.nL, w3 = 3 * nL;
   double* Pe = PhiL + slot * (size_t)3 * nq * w3;
@@ -985,11 +937,16 @@ __global__ void __launch_bounds__(256) k_restrict(int nt, int nu, const int* __r
 }
 
 // ------------------------------------------------------- orchestration --
-// Per-element bytes of the chunk workspace of one group.
-static size_t chunk_bytes(const Sizes& S) {
-  return sizeof(double2) * (size_t)S.N * S.N + sizeof(double) * 3 * (size_t)S.nq * (2 * S.n_f + 3 * S.nL) +
-         sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) +
-         sizeof(double) * (size_t)S.nq * (S.n_f + 6) + sizeof(int);
+// Per-element bytes of the chunk workspace of one group.  FP64 quadrature is
+// sum-factorised (quad_sf.cu) and keeps only per-point weights and, for the
+// real-path extraction, an n_u x n_h scratch; the tensor-core modes keep the
+// weighted basis values at every quadrature point.
+static size_t chunk_bytes(const Sizes& S, bool fp64q) {
+  const size_t mc = sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL);
+  const size_t k = sizeof(double2) * (size_t)S.N * S.N + sizeof(int);
+  if (fp64q)
+    return k + mc + quad_sf_weight_bytes(S) + sizeof(double) * (size_t)S.n_u * S.n_h;
+  return k + mc + sizeof(double) * 3 * (size_t)S.nq * (2 * S.n_f + 3 * S.nL);
 }
 
 // Default chunk capacity per group: a byte budget of 12 GB, raised to one
@@ -1001,7 +958,7 @@ void set_default_caps(dpg_handle* h, int chunk) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   for (Group& G : h->grp) {
-    const size_t per = chunk_bytes(G.sz);
+    const size_t per = chunk_bytes(G.sz, h->prec == DPG_PREC_FP64);
     const size_t budget = std::max((size_t)12 << 30, std::min((size_t)48 << 30, per * (size_t)sms));
     int cap = (int)std::max<size_t>(1, budget / per);
     if (chunk > 0) cap = chunk;
@@ -1013,11 +970,12 @@ void set_default_caps(dpg_handle* h, int chunk) {
 // One workspace sized for the largest group chunk (frees the previous one).
 int alloc_workspace(dpg_handle* h) {
   Workspace& w = h->ws;
-  void* old[] = {w.K, w.V, w.Cu, w.PhiL, w.MC, w.ids, w.FV, w.FR, w.rent, w.F, w.KW, w.Q};
+  void* old[] = {w.K, w.V, w.Cu, w.PhiL, w.MC, w.ids, w.FV, w.FR, w.rent, w.WQ, w.Q};
   for (void* b : old)
     if (b) cudaFree(b);
   w = Workspace{};
-  size_t bK = 0, bV = 0, bP = 0, bMC = 0, bFV = 0, bFR = 0, bF = 0, bKW = 0, bQ = 16;
+  const bool fp64q = h->prec == DPG_PREC_FP64;
+  size_t bK = 0, bV = 0, bCu = 0, bP = 0, bMC = 0, bFV = 0, bFR = 0, bWQ = 16, bQ = 16;
   int capmax = 1;
   for (Group& G : h->grp) {
     const Sizes& S = G.sz;
@@ -1025,11 +983,16 @@ int alloc_workspace(dpg_handle* h) {
     capmax = std::max(capmax, cap);
     const size_t nq3 = 3 * (size_t)S.nq;
     bK = std::max(bK, sizeof(double2) * (size_t)S.N * S.N * cap);
-    bV = std::max(bV, sizeof(double) * nq3 * S.n_f * cap);
-    bP = std::max(bP, sizeof(double) * nq3 * 3 * S.nL * cap);
+    // V, Cu, PhiL: basis values at the quadrature points for the tensor-core
+    // contractions; with FP64 quadrature one element's worth (the metric-free
+    // reference matrices) and V doubling as the real-path extraction scratch
+    const int vcap = fp64q ? 1 : cap;
+    bV = std::max(bV, sizeof(double) * nq3 * S.n_f * vcap);
+    if (fp64q) bV = std::max(bV, sizeof(double) * (size_t)S.n_u * S.n_h * cap);
+    bCu = std::max(bCu, sizeof(double) * nq3 * S.n_f * vcap);
+    bP = std::max(bP, sizeof(double) * nq3 * 3 * S.nL * vcap);
     bMC = std::max(bMC, sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) * cap);
-    bF = std::max(bF, sizeof(double) * (size_t)S.nq * S.n_f * cap);
-    bKW = std::max(bKW, sizeof(double) * 6 * (size_t)S.nq * cap);
+    if (fp64q) bWQ = std::max(bWQ, quad_sf_weight_bytes(S) * cap);
     if (h->factor_arith == DPG_FACTOR_TC_SPLIT) bQ = std::max(bQ, factor_tc_scratch_bytes(S.N, true) * cap);
   }
   w.rcap = std::max(6, std::min(capmax * 2, std::max(6, (int)h->robin_entries.size())));
@@ -1039,11 +1002,11 @@ int alloc_workspace(dpg_handle* h) {
     bFV = std::max(bFV, sizeof(double) * 3 * (size_t)S.nqf * Wf * w.rcap);
     bFR = std::max(bFR, sizeof(double) * (size_t)S.n_f * Wf * w.rcap);
   }
-  size_t bytes[] = {bK, bV, bV, bP, bMC, sizeof(int) * (size_t)capmax, bFV, bFR, sizeof(int) * 4 * (size_t)w.rcap,
-                    bF, bKW, bQ};
+  size_t bytes[] = {bK, bV, bCu, bP, bMC, sizeof(int) * (size_t)capmax, bFV, bFR, sizeof(int) * 4 * (size_t)w.rcap,
+                    bWQ, bQ};
   void** ptrs[] = {(void**)&w.K, (void**)&w.V, (void**)&w.Cu, (void**)&w.PhiL, (void**)&w.MC, (void**)&w.ids,
-                   (void**)&w.FV, (void**)&w.FR, (void**)&w.rent, (void**)&w.F, (void**)&w.KW, (void**)&w.Q};
-  for (int k = 0; k < 12; ++k) {
+                   (void**)&w.FV, (void**)&w.FR, (void**)&w.rent, (void**)&w.WQ, (void**)&w.Q};
+  for (int k = 0; k < 11; ++k) {
     if (cudaMalloc(ptrs[k], bytes[k]) != cudaSuccess) {
       cudaGetLastError();
       h->err = "workspace allocation of " + std::to_string(bytes[k]) + " bytes failed";
@@ -1086,7 +1049,7 @@ int init_kernel_attributes(dpg_handle* h) {
   const int s128 = (int)factor_smem<double2>();
   DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64));
   DPG_CUDA_TRY(h, cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128));
-  if (tc_init() != DPG_OK || factor_tc_init() != DPG_OK) {
+  if (tc_init() != DPG_OK || factor_tc_init() != DPG_OK || quad_sf_init() != DPG_OK) {
     h->err = "tensor-core kernel attribute setup failed";
     return DPG_ERR_CUDA;
   }
@@ -1175,44 +1138,19 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
   const int* ids = cp ? cp->d_ids + cp->ids_off : w.ids;
   if (!cp) DPG_CUDA_TRY(h, cudaMemcpyAsync(w.ids, ids_host, sizeof(int) * count, cudaMemcpyHostToDevice, s));
   if (quad) {
-    const size_t nq3 = 3 * (size_t)S.nq;
-    const bool fp64q = h->prec == DPG_PREC_FP64;
-    k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(G.tab, S, h->d_X, ids, w.V, w.Cu, w.PhiL,
-                                                                     fp64q ? w.F : nullptr, fp64q ? w.KW : nullptr);
-    const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
-    const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
-    const int nL3 = 3 * S.nL;
-    // M = V^T V, C = Cu^T Cu, P = V^T PhiL, Q = Cu^T PhiL (FP64, or the tensor cores)
     if (h->prec == DPG_PREC_FP64) {
-      // M_ij = sum_q w det f_i f_j (J^{-1} J^{-T})_{c_i c_j}: test functions are
-      // component-major (n_f / 3 per reference component), so the upper triangle
-      // of M is six weighted products over the n_q points (one per component
-      // pair) instead of one product over 3 n_q rows
-      {
-        const int nc = S.n_f / 3;
-        const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
-        const long long sF = (long long)S.nq * S.n_f;
-        for (int k = 0; k < 6; ++k)
-          gemm_tn(nc, nc, S.nq, w.F + (size_t)pa[k] * nc, S.n_f, sF, w.F + (size_t)pb[k] * nc, S.n_f, sF,
-                  w.MC + (size_t)pa[k] * nc * S.n_f + (size_t)pb[k] * nc, S.n_f, (long long)mcs, count, s,
-                  pa[k] == pb[k] ? 1 : 0, w.KW + (size_t)k * S.nq, 6LL * S.nq);
-        h->launches += 5;
+      // M, C, P, Q by sum factorisation over the tensor Gauss rule (quad_sf.cu)
+      if (quad_sf_launch(G.tab, S, h->d_X, ids, count, w.WQ, w.MC, s) != DPG_OK) {
+        h->err = "sum-factorised quadrature launch failed";
+        return DPG_ERR_CUDA;
       }
-      gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, sV, w.Cu, S.n_f, sV, w.MC + (size_t)S.n_f * S.n_f, S.n_f,
-              (long long)mcs, count, s, 1);
-      // PhiL is block diagonal over the component d (row q*3+d holds s_q L_l(q) in
-      // columns d nL + l only): P[:, d nL + l] = sum_q V[q*3+d][:] PhiL[q*3+d][d nL + l],
-      // one K = n_q product per d (rows of stride 3) instead of K = 3 n_q over the zero blocks
-      const int nL = S.nL;
-      for (int d = 0; d < 3; ++d) {
-        gemm_tn(S.n_f, nL, S.nq, w.V + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
-                3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)d * nL, nL3, (long long)mcs, count, s);
-        gemm_tn(S.n_f, nL, S.nq, w.Cu + (size_t)d * S.n_f, 3 * S.n_f, sV, w.PhiL + (size_t)d * nL3 + (size_t)d * nL,
-                3 * nL3, sP, w.MC + 2 * (size_t)S.n_f * S.n_f + (size_t)S.n_f * nL3 + (size_t)d * nL, nL3,
-                (long long)mcs, count, s);
-      }
-      h->launches += 4;
+      h->launches += 2;
     } else {
+      const size_t nq3 = 3 * (size_t)S.nq;
+      k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, count), 256, 0, s>>>(G.tab, S, h->d_X, ids, w.V, w.Cu, w.PhiL);
+      const long long sV = (long long)(nq3 * S.n_f), sP = (long long)(nq3 * 3 * S.nL);
+      const int nL3 = 3 * S.nL;
+      const size_t mcs = 2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL;
       const int split = h->prec == DPG_PREC_3XTF32 ? 3 : 1;
       int* terr = h->d_status + h->ne;
       int rc = 0;
@@ -1487,7 +1425,7 @@ int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem,
     const bool real = h->allow_real && G.real_elems.size() >= G.cplx_elems.size();
     const std::vector<int>& L = !h->allow_real ? G.elems : (real ? G.real_elems : G.cplx_elems);
     const int n = (int)L.size();
-    const size_t per = chunk_bytes(G.sz);
+    const size_t per = chunk_bytes(G.sz, h->prec == DPG_PREC_FP64);
     std::vector<int> cand;
     for (int k : {1, 2, 3, 4, 6, 8, 12, 16})
       if (k * sms <= n && (double)per * k * sms <= max_bytes) cand.push_back(k * sms);
@@ -1962,8 +1900,7 @@ int compute_reference_matrices(dpg_handle* h, int g, cudaStream_t s) {
   int zeros[32] = {0};
   DPG_CUDA_TRY(h, cudaMemcpyAsync(dXu, Xu, sizeof(Xu), cudaMemcpyHostToDevice, s));
   DPG_CUDA_TRY(h, cudaMemcpyAsync(dids, zeros, sizeof(zeros), cudaMemcpyHostToDevice, s));
-  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, 1), 256, 0, s>>>(G.tab, S, dXu, dids, w.V, w.Cu, w.PhiL, nullptr,
-                                                               nullptr);
+  k_vol_arrays<<<dim3((S.nq + QB - 1) / QB, 1), 256, 0, s>>>(G.tab, S, dXu, dids, w.V, w.Cu, w.PhiL);
   const size_t nq3 = 3 * (size_t)S.nq;
   gemm_tn(S.n_f, S.n_f, (int)nq3, w.Cu, S.n_f, 0, w.V, S.n_f, 0, G.d_Xref, S.n_f, 0, 1, s);
   // faces of the unit cube

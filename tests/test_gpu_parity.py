@@ -77,7 +77,7 @@ def _oracle_element(mesh, e):
     return el, oel.condense(el)
 
 
-@pytest.mark.parametrize("case", ["waveguide2d_p1", "lossy_p1", "lossy_p2", "lossy_p3"])
+@pytest.mark.parametrize("case", ["waveguide2d_p1", "lossy_p1", "lossy_p2", "lossy_p3", "lossy_p4"])
 def test_element_matrices_match_oracle(dpg_mod, case):
     if case == "waveguide2d_p1":
         mesh = inputs.waveguide_2d_config(p=1)
@@ -85,7 +85,7 @@ def test_element_matrices_match_oracle(dpg_mod, case):
     else:
         p = int(case[-1])
         mesh = _lossy_jittered(p)
-        ids = [0, 1, 2, 3]
+        ids = [0, 1, 2, 3] if p < 4 else [0, 1]  # the p = 4 oracle takes seconds per element
     d = dpg_mod.DPG(mesh)
     out = d.element_dump(ids)
     for k, e in enumerate(ids):

@@ -296,6 +296,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--chunk", type=int, default=0, help="elements per launch (0: library default)")
     ap.add_argument("--autotune", action="store_true", help="measure chunk sizes per degree before the warm-up")
+    ap.add_argument("--bucketed", action="store_true",
+                    help="order-bucketed element pass: waves of every order's chunks, persistent factorisation")
     ap.add_argument("--stream", action="store_true",
                     help="streaming element pass (no per-element condensation data; for the full-size configs)")
     ap.add_argument("--compare-fp64", action="store_true",
@@ -335,6 +337,8 @@ def main():
     d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk, adjoint=args.adjoint,
                 streaming=streaming)
     mode = CG_MODES[args.cg]
+    if args.bucketed:
+        d.set_bucketed(True)
     tuned = d.autotune() if args.autotune else None
     stream = torch.cuda.current_stream()
 
@@ -386,6 +390,11 @@ def main():
         dist.barrier()
     clocks = clk.stop()
     tim = d.timing_get()
+    # SM-busy fraction of the timed pass's factorisation launches (per-element stamps)
+    try:
+        balance = {"mode": "order-bucketed persistent" if args.bucketed else "per-order chunks", **d.factor_balance()}
+    except dpg.DPGError as err:
+        balance = {"unavailable": str(err)}
     ms = max_over_ranks(t_start.elapsed_time(t_end), dist, "cuda")
     ms_step = ms / args.steps
     br = {"element_pass_s": [], "assemble_s": [], "cg_s": [], "estimate_s": []}
@@ -533,7 +542,7 @@ def main():
                    "p": p if len(pvals) == 1 else {str(q): int((mesh.p == q).sum()) for q in pvals}, "dp": 1,
                    "quadrature": args.precision,
                    "chunks": {str(g[0]): g[2] for g in d.group_info()} if d.h else None,
-                   "autotuned": tuned is not None, "streaming": streaming,
+                   "autotuned": tuned is not None, "streaming": streaming, "bucketed": args.bucketed,
                    "trace_unknowns": int(d.n), "nnz": int(d.nnz), "cg": args.cg, "cg_rtol": args.rtol,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-element stores and CSR are tens of GB)"},
@@ -543,6 +552,7 @@ def main():
                       "cg_ms_per_iteration": 1e3 * br["cg_s"] / max(1, cg_iters)},
         "fp64_arm": fp64_arm,
         "complex_path_element_pass": complex_rate,
+        "factor_load_balance": balance,
         "roofline": roof,
         "roofline_secondary": roof2,
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

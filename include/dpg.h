@@ -359,6 +359,33 @@ int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle
  * Errors: DPG_ERR_ARG (unknown mode), DPG_ERR_NOMEM. */
 int dpg_set_factor_arith(dpg_handle* h, int32_t arith);
 
+/* Order-bucketed element pass (Sec. 4: p-adaptive and AMR meshes mix trial
+ * orders, so element work is uneven).  enable = 1: the pass runs in waves; a
+ * wave forms one chunk of every (order, arithmetic) list, each into its own
+ * slice of the K workspace, then factors all of them in ONE persistent launch
+ * (one CTA per SM) that takes elements from a work list ordered longest
+ * first (complex before real, then by matrix size: LPT), then extracts chunk
+ * by chunk.  The number of waves: at least what a 48 GB budget for the K
+ * workspace requires, and at least enough that the costliest list (largest
+ * N^3, complex four times real) puts no more elements into a wave than there
+ * are SMs; with the setup's chunk size, the largest list's share of a wave.  enable = 0: one launch per chunk of a single order (default).
+ * Results are identical in both modes (the same per-element arithmetic).
+ * Changing the mode reallocates the chunk workspace and invalidates the
+ * element stores.  The FP64-pipe factorisation (DPG_FACTOR_FP64) keeps one
+ * launch per chunk inside each wave.  dpg_autotune sizes per-order chunks and
+ * is refused in this mode.  Errors: DPG_ERR_ARG, DPG_ERR_NOMEM. */
+int dpg_set_bucketed(dpg_handle* h, int32_t enable);
+
+/* Load balance of the last element pass's tensor-core factorisation, from
+ * per-element stamps (SM, start and end on the global timer) that the
+ * factorisation kernels write.  busy (host, written): the sum over elements
+ * of their factorisation time divided by (number of SMs x the summed span of
+ * the factorisation launches), i.e. 1 minus the SM-idle fraction of those
+ * launches; span_ms: the summed span; items: elements counted.  Synchronous.
+ * Errors: DPG_ERR_ARG, DPG_ERR_STATE (no pass on the current plan, or the
+ * last pass used the FP64-pipe factorisation, which writes no stamps). */
+int dpg_factor_balance(dpg_handle* h, double* busy, double* span_ms, int64_t* items);
+
 /* Check hook of the two factorisation kernels: run the element factorisation
  * of dpg_element_batch on one augmented matrix given on the host.  A (host,
  * read): N x N column-major, lower triangle used, real (cplx = 0: N^2

@@ -93,7 +93,16 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
   std::vector<int> status(h->ne);
   DPG_CUDA_TRY(h, cudaMemcpyAsync(status.data(), h->d_status, sizeof(int) * h->ne, cudaMemcpyDeviceToHost, s));
   DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
-  if (h->timing) {
+  if (h->timing && h->bucketed && h->factor_arith == DPG_FACTOR_TC_SPLIT) {
+    for (const WavePlan& wp : h->waves) {  // one persistent launch per wave
+      float ms = 0;
+      DPG_CUDA_TRY(h, cudaEventElapsedTime(&ms, wp.ev0, wp.ev1));
+      h->factor_ms += ms;
+      h->factor_launches += (wp.nitems > wp.nitems_real) + (wp.nitems_real > 0);
+      h->factor_elements += wp.nitems;
+      h->factor_elements_real += wp.nitems_real;
+    }
+  } else if (h->timing) {
     for (const ChunkPlan& cp : h->plan) {
       float ms = 0;
       DPG_CUDA_TRY(h, cudaEventElapsedTime(&ms, cp.ev0, cp.ev1));
@@ -508,8 +517,67 @@ extern "C" int dpg_cg_bytes_per_iteration(dpg_handle* h, int32_t mode, int64_t* 
 
 extern "C" int dpg_set_real_path(dpg_handle* h, int32_t enable) {
   if (!h) return DPG_ERR_ARG;
-  if (h->allow_real != (enable != 0)) h->plan_valid = false;
+  if (h->allow_real == (enable != 0)) return DPG_OK;
+  h->plan_valid = false;
   h->allow_real = enable != 0;
+  if (h->bucketed) {  // the waves' lists change with the arithmetic split
+    set_default_caps(h, h->chunk_req);
+    return alloc_workspace(h);
+  }
+  return DPG_OK;
+}
+
+extern "C" int dpg_set_bucketed(dpg_handle* h, int32_t enable) {
+  if (!h) return DPG_ERR_ARG;
+  if (h->bucketed == (enable != 0)) return DPG_OK;
+  h->bucketed = enable != 0;
+  h->have_elements = false;
+  h->have_system = false;
+  set_default_caps(h, h->chunk_req);
+  return alloc_workspace(h);  // the K arena and the plan (waves) change
+}
+
+extern "C" int dpg_factor_balance(dpg_handle* h, double* busy, double* span_ms, int64_t* items) {
+  if (!h || !busy || !span_ms || !items) return DPG_ERR_ARG;
+  if (!h->d_stamps || h->n_stamps <= 0) {
+    h->err = "no element pass has run on the current plan";
+    return DPG_ERR_STATE;
+  }
+  std::vector<unsigned long long> st(3 * (size_t)h->n_stamps);
+  DPG_CUDA_TRY(h, cudaMemcpy(st.data(), h->d_stamps, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost));
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // launches: the waves (bucketed) or the chunks, each a range of stamps
+  std::vector<std::pair<int64_t, int64_t>> ranges;
+  if (h->bucketed && h->factor_arith == DPG_FACTOR_TC_SPLIT)
+    for (const WavePlan& wp : h->waves) {  // the complex and the real launch of the wave
+      const int64_t mid = wp.item_off + (wp.nitems - wp.nitems_real);
+      ranges.push_back({wp.item_off, mid});
+      ranges.push_back({mid, wp.item_off + wp.nitems});
+    }
+  else
+    for (const ChunkPlan& cp : h->plan) ranges.push_back({cp.ids_off, cp.ids_off + cp.count});
+  double work = 0, span = 0;
+  int64_t n = 0;
+  for (const auto& r : ranges) {
+    unsigned long long lo = ~0ull, hi = 0;
+    for (int64_t k = r.first; k < r.second; ++k) {
+      const unsigned long long t0 = st[3 * k + 1], t1 = st[3 * k + 2];
+      if (t0 == 0 || t1 < t0) {
+        h->err = "the last element pass left no factorisation stamps (FP64-pipe factorisation?)";
+        return DPG_ERR_STATE;
+      }
+      lo = std::min(lo, t0);
+      hi = std::max(hi, t1);
+      work += (double)(t1 - t0);
+      ++n;
+    }
+    if (r.second > r.first) span += (double)(hi - lo);
+  }
+  *busy = span > 0 ? work / (span * sms) : 0.0;
+  *span_ms = span * 1e-6;
+  *items = n;
   return DPG_OK;
 }
 

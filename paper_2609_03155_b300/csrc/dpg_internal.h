@@ -98,11 +98,32 @@ struct ChunkPlan {
   bool real = false;
   bool restricted = false;     // some element needs the trace restriction
   int64_t ids_off = 0;         // into d_plan_ids
+  int64_t koff = 0;            // byte offset of the chunk's matrices in the workspace K (order-bucketed waves)
   int count = 0;
   std::vector<int4> robin;     // sub-batches: (entries offset, entries, element list offset, elements) in the rent list
   const int* d_ids = nullptr;  // the plan's device element-id list (ids of this chunk at d_ids + ids_off)
   const int* d_rent = nullptr; // the plan's device Robin entry list
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the factorisation (timing)
+};
+
+// One item of the persistent factorisation's work list (factor_tc.cu): an
+// element's augmented matrix at byte offset koff of the K arena.
+struct FtItem {
+  int64_t koff;
+  int elem, cplx, N, nact, nv, npiv, pad;
+};
+
+// One wave of the order-bucketed element pass: chunks c0 .. c0 + nc - 1 of the
+// plan (at most one chunk of every order and arithmetic list) are formed into
+// their slices of the K arena, then factored by persistent launches over the
+// wave's work list (items item_off .. item_off + nitems - 1: the complex items
+// of every order longest first, then the real ones; one launch per
+// arithmetic), then extracted chunk by chunk.
+struct WavePlan {
+  int c0 = 0, nc = 0;
+  int64_t item_off = 0;
+  int nitems = 0, nitems_real = 0, nmax = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 // Elements of one trial degree: sizes, tables, reference matrices.
@@ -232,6 +253,18 @@ struct dpg_handle {
   int* d_plan_ids = nullptr;
   int* d_plan_rent = nullptr;
   int* d_est_neg = nullptr;       // count of clamped negative eta_K^2 (one int)
+  // order-bucketed element pass: waves of chunks of every order, one
+  // persistent factorisation launch per wave
+  bool bucketed = false;
+  int nwaves = 1;
+  int chunk_req = 0;  // the caller's chunk size at setup (0: by the byte budget)
+  std::vector<dpg::WavePlan> waves;
+  dpg::FtItem* d_items = nullptr;
+  int* d_wave_ctr = nullptr;
+  // factorisation stamps of the last pass: (SM, start ns, end ns) per element
+  // of the plan (per item in bucketed mode), in plan order
+  unsigned long long* d_stamps = nullptr;
+  int64_t n_stamps = 0;
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false, graph_timing = false;
@@ -267,8 +300,12 @@ void classify_elements(dpg_handle* h);
 void set_default_caps(dpg_handle* h, int chunk);
 int alloc_workspace(dpg_handle* h);
 int init_kernel_attributes(dpg_handle* h);
+// One chunk of the element pass: quadrature (quad), K formed (build), the
+// factorisation (factor), the extraction into the stores (extract).  Kc: the
+// chunk's matrices (default: the start of the K workspace).
 int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s, bool factor,
-                      bool extract, bool real = false, const ChunkPlan* cp = nullptr, bool quad = true);
+                      bool extract, bool real = false, const ChunkPlan* cp = nullptr, bool quad = true,
+                      bool build = true, void* Kc = nullptr);
 int build_plan(dpg_handle* h);
 void free_plan(dpg_handle* h);
 int element_pass(dpg_handle* h, cudaStream_t s);
@@ -288,7 +325,11 @@ int quad_sf_launch(const Tables& T, const Sizes& S, const double* X, const int* 
                    double* MC, cudaStream_t s);
 size_t factor_tc_scratch_bytes(int N, bool cplx);
 int factor_tc_launch(bool cplx, int count, int N, int nact, int nv, int npiv, const int* ids, void* K, int* status,
-                     int* tc_err, uint8_t* qscr, cudaStream_t s);
+                     int* tc_err, uint8_t* qscr, cudaStream_t s, unsigned long long* stamps = nullptr);
+size_t factor_tc_queue_scratch_bytes(int Nmax);
+int factor_tc_queue_launch(bool cplx, const FtItem* items, int nitems, int Nmax, int* counter, void* arena,
+                           int* status, int* tc_err, uint8_t* qscr, unsigned long long* stamps, int grid,
+                           cudaStream_t s);
 // quad_tc.cu
 int tc_init();
 int gemm_tn_tc(int split, int Ma, int Nb, int Kd, const double* A, int lda, long long sA, const double* B, int ldb,

@@ -953,10 +953,100 @@ static size_t chunk_bytes(const Sizes& S, bool fp64q) {
 // element per SM when a single chunk of the group is larger (high degrees), at
 // most 48 GB; a multiple of the SM count when large enough; or the caller's
 // fixed chunk.
+// The element lists the plan cuts into chunks: per order group, the lossless
+// elements (real path, when allowed) and the others; in streaming mode each
+// list split further by colour (a chunk is then colour-homogeneous).
+struct ElemList {
+  int g = 0;
+  bool real = false;
+  std::vector<int> elems;
+};
+
+static std::vector<ElemList> element_lists(const dpg_handle* h, bool real) {
+  std::vector<ElemList> out;
+  for (int g = 0; g < (int)h->grp.size(); ++g) {
+    const Group& G = h->grp[g];
+    std::vector<std::vector<int>> lists;
+    if (real) {
+      lists.push_back(G.real_elems);
+      lists.push_back(G.cplx_elems);
+    } else {
+      lists.push_back(G.elems);
+    }
+    if (h->stream) {
+      std::vector<std::vector<int>> by_colour;
+      for (const std::vector<int>& L : lists)
+        for (int c = 0; c < h->ncolor; ++c) {
+          std::vector<int> part;
+          for (int e : L)
+            if (h->elem_color[e] == c) part.push_back(e);
+          if (!part.empty()) by_colour.push_back(part);
+        }
+      lists = by_colour;
+    }
+    for (std::vector<int>& L : lists) {
+      if (L.empty()) continue;
+      ElemList el;
+      el.g = g;
+      el.real = real && h->is_real[L[0]];
+      el.elems = std::move(L);
+      out.push_back(std::move(el));
+    }
+  }
+  return out;
+}
+
+// Bytes of one element's augmented matrix in the K workspace.
+static size_t k_bytes(const Sizes& S, bool real) {
+  return (real ? sizeof(double) : sizeof(double2)) * (size_t)S.N * S.N;
+}
+
+// Chunk of list l in wave w of the order-bucketed pass: ceil(n_l / waves) elements.
+static int wave_cap(size_t n, int waves) { return (int)((n + waves - 1) / waves); }
+
 void set_default_caps(dpg_handle* h, int chunk) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  h->chunk_req = chunk;
+  if (h->bucketed) {
+    // Every list contributes ceil(n_l / waves) elements to each wave.  The
+    // number of waves: at least enough for the K arena budget (48 GB), and at
+    // least enough that the costliest list (largest N^3, complex 4x real)
+    // puts no more elements into a wave than there are SMs, since an SM that
+    // got two of them would double the wave's span; otherwise as few as
+    // possible, so that the cheaper elements fill the SMs around them.  With
+    // the caller's chunk: the largest list's share of a wave.
+    const std::vector<ElemList> lists = element_lists(h, h->allow_real);
+    size_t total = 0, nmax = 1, ncost = 1;
+    double cmax = -1.0;
+    for (const ElemList& L : lists) {
+      const Sizes& S = h->grp[L.g].sz;
+      total += k_bytes(S, L.real) * L.elems.size();
+      nmax = std::max(nmax, L.elems.size());
+      const double c = (double)S.N * S.N * S.N * (L.real ? 1.0 : 4.0);
+      if (c > cmax) {
+        cmax = c;
+        ncost = L.elems.size();
+      }
+    }
+    const size_t budget = (size_t)48 << 30;
+    int waves;
+    if (chunk > 0) {
+      waves = (int)((nmax + chunk - 1) / chunk);
+    } else {
+      const int w_mem = (int)((total + budget - 1) / budget);
+      const int w_sm = (int)((ncost + sms - 1) / sms);
+      waves = std::max(w_mem, w_sm);
+    }
+    h->nwaves = std::max(1, waves);
+    for (Group& G : h->grp) G.cap = 1;
+    for (const ElemList& L : lists) {
+      Group& G = h->grp[L.g];
+      G.cap = std::max(G.cap, wave_cap(L.elems.size(), h->nwaves));
+    }
+    return;
+  }
   for (Group& G : h->grp) {
     const size_t per = chunk_bytes(G.sz, h->prec == DPG_PREC_FP64);
     const size_t budget = std::max((size_t)12 << 30, std::min((size_t)48 << 30, per * (size_t)sms));
@@ -994,6 +1084,22 @@ int alloc_workspace(dpg_handle* h) {
     bMC = std::max(bMC, sizeof(double) * (2 * (size_t)S.n_f * S.n_f + 2 * (size_t)S.n_f * 3 * S.nL) * cap);
     if (fp64q) bWQ = std::max(bWQ, quad_sf_weight_bytes(S) * cap);
     if (h->factor_arith == DPG_FACTOR_TC_SPLIT) bQ = std::max(bQ, factor_tc_scratch_bytes(S.N, true) * cap);
+  }
+  if (h->bucketed) {
+    // the K arena holds one wave: every list's chunk side by side (256-byte
+    // aligned slices); the persistent factorisation's digit scratch is per SM
+    size_t arena = 0;
+    int nmax = 1;
+    for (const ElemList& L : element_lists(h, h->allow_real)) {
+      const Sizes& S = h->grp[L.g].sz;
+      arena += (k_bytes(S, L.real) * wave_cap(L.elems.size(), h->nwaves) + 255) / 256 * 256;
+      nmax = std::max(nmax, S.N);
+    }
+    bK = std::max(bK, arena);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    bQ = std::max(bQ, factor_tc_queue_scratch_bytes(nmax) * (size_t)sms);
   }
   w.rcap = std::max(6, std::min(capmax * 2, std::max(6, (int)h->robin_entries.size())));
   for (Group& G : h->grp) {
@@ -1091,7 +1197,7 @@ static void robin_batches(const dpg_handle* h, const int* ids_host, int count,
 
 // Face arrays, face GEMM and Robin terms of one sub-batch (device lists).
 static int robin_launch(dpg_handle* h, int g, const int* d_rent, int nent, const int* d_rlist, int nel,
-                        cudaStream_t s) {
+                        cudaStream_t s, double2* K) {
   Workspace& w = h->ws;
   const Group& G = h->grp[g];
   const Sizes& S = G.sz;
@@ -1099,7 +1205,7 @@ static int robin_launch(dpg_handle* h, int g, const int* d_rent, int nent, const
   k_face_arrays<<<dim3(1, nent), 256, 0, s>>>(G.tab, S, h->d_X, d_rent, h->d_robin, G.d_trfun, h->omega, 0, w.FV);
   gemm_tn(S.n_f, Wf, 3 * S.nqf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FV, Wf, (long long)3 * S.nqf * Wf, w.FR, Wf,
           (long long)S.n_f * Wf, nent, s);
-  k_robin_add<<<nel, 256, 0, s>>>(S, d_rlist, d_rent, h->d_robin, w.FR, w.K);
+  k_robin_add<<<nel, 256, 0, s>>>(S, d_rlist, d_rent, h->d_robin, w.FR, K);
   DPG_CUDA_TRY(h, cudaGetLastError());
   h->launches += 3;
   return DPG_OK;
@@ -1118,7 +1224,7 @@ static int run_robin(dpg_handle* h, int g, const int* ids_host, int count, cudaS
     int* d_rlist = w.rent + 4 * nent;
     DPG_CUDA_TRY(h, cudaMemcpyAsync(d_rlist, rlists[k].data(), sizeof(int) * rlists[k].size(), cudaMemcpyHostToDevice,
                                     s));
-    int rc = robin_launch(h, g, w.rent, nent, d_rlist, (int)rlists[k].size() / 2, s);
+    int rc = robin_launch(h, g, w.rent, nent, d_rlist, (int)rlists[k].size() / 2, s, w.K);
     if (rc) return rc;
     // the workspace list buffer is reused: wait for this sub-batch
     DPG_CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -1129,8 +1235,9 @@ static int run_robin(dpg_handle* h, int g, const int* ids_host, int count, cudaS
 // quad = false reuses the quadrature matrices already in the workspace (the
 // same chunk was formed just before) and only forms K again.
 int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s, bool factor,
-                      bool extract, bool real, const ChunkPlan* cp, bool quad) {
+                      bool extract, bool real, const ChunkPlan* cp, bool quad, bool build, void* Kc) {
   Workspace& w = h->ws;
+  double2* const Kw = Kc ? static_cast<double2*>(Kc) : w.K;  // the chunk's augmented matrices
   const Group& G = h->grp[g];
   const Sizes& S = G.sz;
   if (count > G.cap) return DPG_ERR_ARG;
@@ -1166,27 +1273,30 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
         h->err = "tensor-core contraction launch failed";
         return DPG_ERR_CUDA;
       }
+      h->launches += 5;  // basis arrays, four contractions
     }
   }
-  double* Kr = reinterpret_cast<double*>(w.K);
-  if (real) {
-    k_build_K_real<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, ids, h->d_eps, h->d_mu, w.MC, G.d_Xref,
-                                                    G.d_Tall, Kr);
-  } else {
-    k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
-                                               G.d_Xref, G.d_Tf, G.d_Tall, w.K);
-  }
-  DPG_CUDA_TRY(h, cudaGetLastError());
-  h->launches += 6;  // basis arrays, four GEMMs, K
-  if (!real) {
-    if (cp) {
-      for (const int4& rb : cp->robin) {
-        int rc = robin_launch(h, g, cp->d_rent + rb.x, rb.y, cp->d_rent + rb.z, rb.w, s);
+  double* Kr = reinterpret_cast<double*>(Kw);
+  if (build) {
+    if (real) {
+      k_build_K_real<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, ids, h->d_eps, h->d_mu, w.MC,
+                                                      G.d_Xref, G.d_Tall, Kr);
+    } else {
+      k_build_K<<<dim3(148, count), 256, 0, s>>>(S, h->omega, h->alpha, ids, h->d_eps, h->d_mu, h->d_fbc, w.MC,
+                                                 G.d_Xref, G.d_Tf, G.d_Tall, Kw);
+    }
+    DPG_CUDA_TRY(h, cudaGetLastError());
+    h->launches += 1;
+    if (!real) {
+      if (cp) {
+        for (const int4& rb : cp->robin) {
+          int rc = robin_launch(h, g, cp->d_rent + rb.x, rb.y, cp->d_rent + rb.z, rb.w, s, Kw);
+          if (rc) return rc;
+        }
+      } else {
+        int rc = run_robin(h, g, ids_host, count, s);
         if (rc) return rc;
       }
-    } else {
-      int rc = run_robin(h, g, ids_host, count, s);
-      if (rc) return rc;
     }
   }
   if (factor) {
@@ -1199,15 +1309,17 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
     const unsigned int rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (timed) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(cp->ev0, s, rec_flags));
     if (h->factor_arith == DPG_FACTOR_TC_SPLIT) {
-      if (factor_tc_launch(!real, count, S.N, S.N, S.n_v, S.n_v + S.n_u, ids, real ? (void*)Kr : (void*)w.K,
-                           h->d_status, h->d_status + h->ne, w.Q, s) != DPG_OK) {
+      // factorisation stamps of the plan's chunks (SM, start, end per element)
+      unsigned long long* st = (cp && h->d_stamps && !h->bucketed) ? h->d_stamps + 3 * cp->ids_off : nullptr;
+      if (factor_tc_launch(!real, count, S.N, S.N, S.n_v, S.n_v + S.n_u, ids, real ? (void*)Kr : (void*)Kw,
+                           h->d_status, h->d_status + h->ne, w.Q, s, st) != DPG_OK) {
         h->err = "tensor-core factorisation launch failed";
         return DPG_ERR_CUDA;
       }
     } else if (real) {
       k_factor<double><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, Kr, h->d_status);
     } else {
-      k_factor<double2><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, w.K, h->d_status);
+      k_factor<double2><<<count, 256, smem, s>>>(S.N, S.N, S.n_v, S.n_v + S.n_u, ids, Kw, h->d_status);
     }
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
@@ -1218,15 +1330,17 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
       k_extract_real<<<count, 256, 0, s>>>(S, ids, Kr, h->d_soff, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1,
                                            w.V);
     else
-      k_extract<<<count, 256, 0, s>>>(S, ids, w.K, h->d_soff, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
+      k_extract<<<count, 256, 0, s>>>(S, ids, Kw, h->d_soff, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1);
     DPG_CUDA_TRY(h, cudaGetLastError());
     h->launches += 1;
     bool any = cp ? cp->restricted : false;
     for (int k = 0; !cp && k < count && !any; ++k) any = h->elem_sig[ids_host[k]] >= 0;
     if (any) {
+      // scratch: each element's own (already extracted) matrix slot, N^2
+      // doubles on the real path and N^2 complex values otherwise
       k_restrict<<<count, 256, sizeof(double2) * S.n_h, s>>>(S.nt, S.n_u, ids, h->d_soff, h->d_sig, h->d_rsig,
-                                                            h->d_rint, h->d_rdbl, h->d_S, h->d_s, h->d_Z, w.K,
-                                                            (size_t)S.N * S.N);
+                                                            h->d_rint, h->d_rdbl, h->d_S, h->d_s, h->d_Z, Kw,
+                                                            real ? (size_t)S.N * S.N / 2 : (size_t)S.N * S.N);
       DPG_CUDA_TRY(h, cudaGetLastError());
       h->launches += 1;
     }
@@ -1249,6 +1363,18 @@ static void free_chunks(std::vector<ChunkPlan>& plan, int** d_ids, int** d_rent)
 
 void free_plan(dpg_handle* h) {
   free_chunks(h->plan, &h->d_plan_ids, &h->d_plan_rent);
+  for (WavePlan& wp : h->waves) {
+    if (wp.ev0) cudaEventDestroy(wp.ev0);
+    if (wp.ev1) cudaEventDestroy(wp.ev1);
+  }
+  h->waves.clear();
+  void* bufs[] = {h->d_items, h->d_wave_ctr, h->d_stamps};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  h->d_items = nullptr;
+  h->d_wave_ctr = nullptr;
+  h->d_stamps = nullptr;
+  h->n_stamps = 0;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
   h->plan_valid = false;
@@ -1261,66 +1387,129 @@ static int make_chunks(dpg_handle* h, bool real, std::vector<ChunkPlan>& plan, i
   std::vector<int> ids_all, rent_all;
   std::vector<ElemOff> soff;
   if (h->stream) soff.assign(h->ne + 1, ElemOff{});
-  for (int g = 0; g < (int)h->grp.size(); ++g) {
+  const std::vector<ElemList> lists = element_lists(h, real);
+  // (list, first element, count) of every chunk, in plan order: list by list,
+  // or wave by wave (the w-th chunk of every list) when order-bucketed
+  struct Cut {
+    int l;
+    size_t c0;
+    int count;
+    int wave;
+  };
+  std::vector<Cut> cuts;
+  const bool waves = h->bucketed;
+  if (waves) {
+    for (int w = 0; w < h->nwaves; ++w)
+      for (int l = 0; l < (int)lists.size(); ++l) {
+        const size_t n = lists[l].elems.size();
+        const int cap = wave_cap(n, h->nwaves);
+        const size_t c0 = (size_t)w * cap;
+        if (c0 < n) cuts.push_back({l, c0, (int)std::min<size_t>(cap, n - c0), w});
+      }
+  } else {
+    for (int l = 0; l < (int)lists.size(); ++l) {
+      const int cap = h->grp[lists[l].g].cap;
+      for (size_t c0 = 0; c0 < lists[l].elems.size(); c0 += cap)
+        cuts.push_back({l, c0, (int)std::min<size_t>(cap, lists[l].elems.size() - c0), -1});
+    }
+  }
+  std::vector<FtItem> items;
+  int64_t koff = 0;
+  int cur_wave = -1;
+  for (size_t ci = 0; ci < cuts.size(); ++ci) {
+    const Cut& cu = cuts[ci];
+    const ElemList& EL = lists[cu.l];
+    const int g = EL.g;
     const Group& G = h->grp[g];
-    std::vector<std::vector<int>> lists;
-    if (real) {
-      lists.push_back(G.real_elems);
-      lists.push_back(G.cplx_elems);
-    } else {
-      lists.push_back(G.elems);
+    const Sizes& S = G.sz;
+    const std::vector<int>& L = EL.elems;
+    const size_t c0 = cu.c0;
+    ChunkPlan cp;
+    cp.g = g;
+    cp.real = EL.real;
+    cp.count = cu.count;
+    cp.ids_off = (int64_t)ids_all.size();
+    ids_all.insert(ids_all.end(), L.begin() + c0, L.begin() + c0 + cp.count);
+    if (waves) {
+      if (cu.wave != cur_wave) {
+        cur_wave = cu.wave;
+        WavePlan wp;
+        wp.c0 = (int)plan.size();
+        wp.item_off = (int64_t)items.size();
+        DPG_CUDA_TRY(h, cudaEventCreate(&wp.ev0));
+        DPG_CUDA_TRY(h, cudaEventCreate(&wp.ev1));
+        h->waves.push_back(wp);
+        koff = 0;
+      }
+      WavePlan& wp = h->waves.back();
+      wp.nc += 1;
+      cp.koff = koff;
+      const size_t eb = k_bytes(S, cp.real);
+      for (int k = 0; k < cp.count; ++k) {
+        FtItem it{};
+        it.koff = koff + (int64_t)(eb * k);
+        it.elem = L[c0 + k];
+        it.cplx = cp.real ? 0 : 1;
+        it.N = S.N;
+        it.nact = S.N;
+        it.nv = S.n_v;
+        it.npiv = S.n_v + S.n_u;
+        items.push_back(it);
+      }
+      wp.nitems += cp.count;
+      if (cp.real) wp.nitems_real += cp.count;
+      wp.nmax = std::max(wp.nmax, S.N);
+      koff += (int64_t)((eb * cp.count + 255) / 256 * 256);
     }
-    if (h->stream) {  // one colour per chunk: its elements share no unknown
-      std::vector<std::vector<int>> by_colour;
-      for (const std::vector<int>& L : lists)
-        for (int c = 0; c < h->ncolor; ++c) {
-          std::vector<int> part;
-          for (int e : L)
-            if (h->elem_color[e] == c) part.push_back(e);
-          if (!part.empty()) by_colour.push_back(part);
-        }
-      lists = by_colour;
-    }
-    for (size_t li = 0; li < lists.size(); ++li) {
-      const std::vector<int>& L = lists[li];
-      const bool is_real_list = real && !L.empty() && h->is_real[L[0]];
-      for (size_t c0 = 0; c0 < L.size(); c0 += G.cap) {
-        ChunkPlan cp;
-        cp.g = g;
-        cp.real = is_real_list;
-        cp.count = (int)std::min<size_t>(G.cap, L.size() - c0);
-        cp.ids_off = (int64_t)ids_all.size();
-        ids_all.insert(ids_all.end(), L.begin() + c0, L.begin() + c0 + cp.count);
-        if (h->stream)
-          for (int k = 0; k < cp.count; ++k) {
-            const Sizes& S = G.sz;
-            ElemOff& o = soff[L[c0 + k]];
-            o.S = (int64_t)k * S.n_h * S.n_h;
-            o.Z = (int64_t)k * S.n_u * S.n_h;
-            o.L1 = 0;
-            o.h = (int64_t)k * S.n_h;
-            o.u = (int64_t)k * S.n_u;
-          }
-        for (int k = 0; k < cp.count && !cp.restricted; ++k) cp.restricted = h->elem_sig[L[c0 + k]] >= 0;
-        if (!cp.real) {
-          std::vector<std::vector<int>> rents, rlists;
-          robin_batches(h, L.data() + c0, cp.count, rents, rlists);
-          for (size_t k = 0; k < rents.size(); ++k) {
-            int4 rb;
-            rb.x = (int)rent_all.size();
-            rb.y = (int)rents[k].size() / 4;
-            rent_all.insert(rent_all.end(), rents[k].begin(), rents[k].end());
-            rb.z = (int)rent_all.size();
-            rb.w = (int)rlists[k].size() / 2;
-            rent_all.insert(rent_all.end(), rlists[k].begin(), rlists[k].end());
-            cp.robin.push_back(rb);
-          }
-        }
-        DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev0));
-        DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev1));
-        plan.push_back(std::move(cp));
+    if (h->stream)
+      for (int k = 0; k < cp.count; ++k) {
+        ElemOff& o = soff[L[c0 + k]];
+        o.S = (int64_t)k * S.n_h * S.n_h;
+        o.Z = (int64_t)k * S.n_u * S.n_h;
+        o.L1 = 0;
+        o.h = (int64_t)k * S.n_h;
+        o.u = (int64_t)k * S.n_u;
+      }
+    for (int k = 0; k < cp.count && !cp.restricted; ++k) cp.restricted = h->elem_sig[L[c0 + k]] >= 0;
+    if (!cp.real) {
+      std::vector<std::vector<int>> rents, rlists;
+      robin_batches(h, L.data() + c0, cp.count, rents, rlists);
+      for (size_t k = 0; k < rents.size(); ++k) {
+        int4 rb;
+        rb.x = (int)rent_all.size();
+        rb.y = (int)rents[k].size() / 4;
+        rent_all.insert(rent_all.end(), rents[k].begin(), rents[k].end());
+        rb.z = (int)rent_all.size();
+        rb.w = (int)rlists[k].size() / 2;
+        rent_all.insert(rent_all.end(), rlists[k].begin(), rlists[k].end());
+        cp.robin.push_back(rb);
       }
     }
+    DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev0));
+    DPG_CUDA_TRY(h, cudaEventCreate(&cp.ev1));
+    plan.push_back(std::move(cp));
+  }
+  if (waves) {
+    // each wave's work list: complex items, then real ones (one persistent
+    // launch each), each part longest first (by matrix size), element order
+    // among equals; the order fixes nothing in the results, only which SM
+    // takes which element
+    for (WavePlan& wp : h->waves) {
+      std::stable_sort(items.begin() + wp.item_off, items.begin() + wp.item_off + wp.nitems,
+                       [](const FtItem& x, const FtItem& y) {
+                         if (x.cplx != y.cplx) return x.cplx > y.cplx;
+                         return x.N > y.N;
+                       });
+    }
+    DPG_CUDA_TRY(h, cudaMalloc(&h->d_items, sizeof(FtItem) * std::max<size_t>(1, items.size())));
+    if (!items.empty())
+      DPG_CUDA_TRY(h, cudaMemcpy(h->d_items, items.data(), sizeof(FtItem) * items.size(), cudaMemcpyHostToDevice));
+    DPG_CUDA_TRY(h, cudaMalloc(&h->d_wave_ctr, 2 * sizeof(int) * std::max<size_t>(1, h->waves.size())));
+  }
+  {
+    h->n_stamps = waves ? (int64_t)items.size() : (int64_t)ids_all.size();
+    DPG_CUDA_TRY(h, cudaMalloc(&h->d_stamps, 3 * sizeof(unsigned long long) * std::max<int64_t>(1, h->n_stamps)));
+    DPG_CUDA_TRY(h, cudaMemset(h->d_stamps, 0, 3 * sizeof(unsigned long long) * std::max<int64_t>(1, h->n_stamps)));
   }
   DPG_CUDA_TRY(h, cudaMalloc(d_ids, sizeof(int) * std::max<size_t>(1, ids_all.size())));
   DPG_CUDA_TRY(h, cudaMalloc(d_rent, sizeof(int) * std::max<size_t>(1, rent_all.size())));
@@ -1351,6 +1540,36 @@ int build_plan(dpg_handle* h) {
   return DPG_OK;
 }
 
+// The persistent factorisation of one wave of the order-bucketed pass: one
+// CTA per SM over the wave's work list (every order, real and complex,
+// longest first), timed by the wave's events when timing is on.
+static int factor_wave(dpg_handle* h, int wi, cudaStream_t s) {
+  const WavePlan& wp = h->waves[wi];
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (h->timing) DPG_CUDA_TRY(h, cudaStreamIsCapturing(s, &cap));
+  const unsigned int rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+  if (h->timing) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(wp.ev0, s, rec_flags));
+  // complex items (all orders) first, then the real ones
+  const int ncplx = wp.nitems - wp.nitems_real;
+  const int64_t off[2] = {wp.item_off, wp.item_off + ncplx};
+  const int cnt[2] = {ncplx, wp.nitems_real};
+  for (int k = 0; k < 2; ++k) {
+    if (cnt[k] == 0) continue;
+    if (factor_tc_queue_launch(k == 0, h->d_items + off[k], cnt[k], wp.nmax, h->d_wave_ctr + 2 * wi + k, h->ws.K,
+                               h->d_status, h->d_status + h->ne, h->ws.Q,
+                               h->d_stamps ? h->d_stamps + 3 * off[k] : nullptr, sms, s) != DPG_OK) {
+      h->err = "persistent factorisation launch failed";
+      return DPG_ERR_CUDA;
+    }
+    h->launches += 1;
+  }
+  if (h->timing) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(wp.ev1, s, rec_flags));
+  return DPG_OK;
+}
+
 // The whole element pass: the plan's launches, captured once into a CUDA
 // graph (re-captured when the plan or the timing switch changes) and replayed
 // on the caller's stream.  Capture runs on a private stream, since the legacy
@@ -1362,9 +1581,44 @@ int element_pass(dpg_handle* h, cudaStream_t s) {
   }
   // streaming: the system is assembled chunk by chunk as the elements are condensed
   auto pass = [&](cudaStream_t st) -> int {
+    if (h->d_stamps)  // the factorisation stamps describe this pass only
+      DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_stamps, 0, 3 * sizeof(unsigned long long) * h->n_stamps, st));
     if (h->stream) {
       DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_val, 0, sizeof(double2) * h->nnz, st));
       DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_b, 0, sizeof(double2) * h->n, st));
+    }
+    if (h->bucketed) {
+      unsigned char* arena = reinterpret_cast<unsigned char*>(h->ws.K);
+      for (size_t wi = 0; wi < h->waves.size(); ++wi) {
+        const WavePlan& wp = h->waves[wi];
+        // every chunk of the wave formed into its slice of the arena
+        for (int c = wp.c0; c < wp.c0 + wp.nc; ++c) {
+          const ChunkPlan& cp = h->plan[c];
+          int rc = run_element_chunk(h, cp.g, nullptr, cp.count, st, false, false, cp.real, &cp, true, true,
+                                     arena + cp.koff);
+          if (rc) return rc;
+        }
+        int rc = DPG_OK;
+        if (h->factor_arith == DPG_FACTOR_TC_SPLIT) {
+          rc = factor_wave(h, (int)wi, st);
+        } else {  // FP64-pipe factorisation: one launch per chunk of the wave
+          for (int c = wp.c0; c < wp.c0 + wp.nc && rc == DPG_OK; ++c) {
+            const ChunkPlan& cp = h->plan[c];
+            rc = run_element_chunk(h, cp.g, nullptr, cp.count, st, true, false, cp.real, &cp, false, false,
+                                   arena + cp.koff);
+          }
+        }
+        if (rc) return rc;
+        // extraction (and in streaming mode assembly) chunk by chunk
+        for (int c = wp.c0; c < wp.c0 + wp.nc; ++c) {
+          const ChunkPlan& cp = h->plan[c];
+          rc = run_element_chunk(h, cp.g, nullptr, cp.count, st, false, true, cp.real, &cp, false, false,
+                                 arena + cp.koff);
+          if (rc == DPG_OK && h->stream) rc = assemble_chunk(h, cp.g, cp.d_ids + cp.ids_off, cp.count, st);
+          if (rc) return rc;
+        }
+      }
+      return DPG_OK;
     }
     for (const ChunkPlan& cp : h->plan) {
       int rc = run_element_chunk(h, cp.g, nullptr, cp.count, st, true, true, cp.real, &cp);
@@ -1413,6 +1667,10 @@ int element_pass(dpg_handle* h, cudaStream_t s) {
 // byte budget) and keep the fastest per element.  Stores of the timed elements
 // are overwritten (a full element pass rewrites them).
 int autotune(dpg_handle* h, double max_bytes, int32_t* caps, float* ms_per_elem, cudaStream_t s) {
+  if (h->bucketed) {
+    h->err = "the autotuner sizes per-order chunks; the order-bucketed pass sizes waves";
+    return DPG_ERR_UNSUPPORTED;
+  }
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -263,10 +263,16 @@ __device__ __forceinline__ void acc_level(const uint32_t v[16], int s, long long
 
 }  // namespace
 
+// The factorisation of one element's augmented matrix A (N x N,
+// column-major, lower triangle used) by the calling CTA.  The caller owns the
+// tensor memory (tmem, 512 columns) and the MMA completion barrier; `phase`
+// carries the barrier's parity from call to call.  Returns FT_DONE unless a
+// wait on the MMAs gave up, with FT_BAD added on a non-positive pivot.
+constexpr int FT_DONE = 1, FT_BAD = 2;
 template <typename T>
-__global__ void __launch_bounds__(FT_THREADS, 1)
-    k_factor_tc(int N, int nact, int nv, int npiv, const int* __restrict__ ids, T* K, int* status, int* tc_err,
-                uint8_t* qscr, long long qstride, int RP) {
+__device__ __forceinline__ int ft_factor(int N, int nact, int nv, int npiv, T* A, uint8_t* Q, int RP, uint32_t tmem,
+                                         uint32_t mbar_a, uint32_t& phase) {
+  __shared__ int bad;
   using O = Fs<T>;
   using Cf = TcCfg<T>;
   constexpr int KR = Cf::K, NJ = Cf::NJ, KC = KR / 8;
@@ -278,29 +284,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
   unsigned char* sJ = ftsm + NSL * ISLICE;  // two buffers
   T* sD = reinterpret_cast<T*>(sJ + 2 * NSL * JSLICE);
   int* s_exp = reinterpret_cast<int*>(sD + TB * TB);
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tmem_slot;
-  __shared__ int bad;
-  const int slot = blockIdx.x;
-  T* A = K + (size_t)slot * N * N;
-  uint8_t* Q = qscr + (size_t)slot * qstride;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t mbar_a = ft_smem_u32(&mbar);
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ft_smem_u32(&tmem_slot)),
-                 "r"(FT_TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    bad = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_slot;
-  uint32_t phase = 0;
+  if (tid == 0) bad = 0;  // first read after the diagonal block's barriers
   bool ok = true;
   for (int k0 = 0; k0 < npiv && ok;) {
     const int stage_end = (k0 < nv) ? nv : npiv;
@@ -541,20 +526,116 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
     __syncthreads();
     k0 = k1;
   }
+  __syncthreads();
+  return (ok ? FT_DONE : 0) | (bad ? FT_BAD : 0);
+}
+
+// CTA setup of the factorisation kernels: tensor memory and the MMA barrier.
+__device__ __forceinline__ uint32_t ft_setup(uint32_t* tmem_slot, uint32_t mbar_a) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ft_smem_u32(tmem_slot)),
+                 "r"(FT_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  return *tmem_slot;
+}
+
+// CTA teardown: after a failed wait, one more bounded wait for the MMAs in
+// flight; tensor memory is released only when nothing can still write it.
+__device__ __forceinline__ void ft_finish(bool ok, uint32_t tmem, uint32_t mbar_a, uint32_t phase, int* tc_err) {
   bool drained = true;
   if (!ok) {
-    if (tid == 0) atomicExch(tc_err, 1);
-    // once more (bounded) for the MMAs in flight; if they still have not
-    // completed, the tensor memory they write is left allocated
+    if (threadIdx.x == 0) atomicExch(tc_err, 1);
     drained = __syncthreads_and(ft_mbar_wait(mbar_a, phase ^ 1u) ? 1 : 0) != 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0 && drained) {
+  if ((threadIdx.x >> 5) == 0 && drained) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FT_TMEM_COLS));
   }
-  if (tid == 0 && bad) status[ids[slot]] = 1;
+}
+
+__device__ __forceinline__ unsigned int ft_smid() {
+  unsigned int r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// One CTA per element of a chunk.  stamps (optional): per element the SM, and
+// the start and end of its factorisation (global timer, ns).
+template <typename T>
+__global__ void __launch_bounds__(FT_THREADS, 1)
+    k_factor_tc(int N, int nact, int nv, int npiv, const int* __restrict__ ids, T* K, int* status, int* tc_err,
+                uint8_t* qscr, long long qstride, int RP, unsigned long long* stamps) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ unsigned long long s_t0;
+  const int slot = blockIdx.x;
+  const uint32_t mbar_a = ft_smem_u32(&mbar);
+  const uint32_t tmem = ft_setup(&tmem_slot, mbar_a);
+  if (threadIdx.x == 0) s_t0 = ft_global_ns();
+  uint32_t phase = 0;
+  const int res = ft_factor<T>(N, nact, nv, npiv, K + (size_t)slot * N * N, qscr + (size_t)slot * qstride, RP, tmem,
+                               mbar_a, phase);
+  const bool ok = (res & FT_DONE) != 0;
+  if (threadIdx.x == 0 && stamps) {
+    stamps[3 * (size_t)slot] = ft_smid();
+    stamps[3 * (size_t)slot + 1] = s_t0;
+    stamps[3 * (size_t)slot + 2] = ft_global_ns();
+  }
+  ft_finish(ok, tmem, mbar_a, phase, tc_err);
+  if (threadIdx.x == 0 && (res & FT_BAD)) status[ids[slot]] = 1;
+}
+
+// Persistent factorisation of a work list of one arithmetic (real or
+// complex) that mixes trial orders: one CTA per SM takes the next item of the
+// list (ordered longest first by the host) until the list is exhausted.  Each
+// item's matrix sits at its byte offset in the arena; the digit scratch is per
+// CTA.  stamps: per item the SM and the start and end times.
+template <typename T>
+__global__ void __launch_bounds__(FT_THREADS, 1)
+    k_factor_tc_queue(const FtItem* __restrict__ items, int nitems, int* counter, unsigned char* arena, int* status,
+                      int* tc_err, uint8_t* qscr, long long qstride, unsigned long long* stamps) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_item;
+  __shared__ unsigned long long s_t0;
+  const uint32_t mbar_a = ft_smem_u32(&mbar);
+  const uint32_t tmem = ft_setup(&tmem_slot, mbar_a);
+  uint8_t* Q = qscr + (size_t)blockIdx.x * qstride;
+  uint32_t phase = 0;
+  bool ok = true;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = s_item;
+    __syncthreads();  // every thread has its item before the next one is fetched
+    if (w >= nitems) break;
+    const FtItem it = items[w];
+    if (threadIdx.x == 0) s_t0 = ft_global_ns();
+    const int res = ft_factor<T>(it.N, it.nact, it.nv, it.npiv, reinterpret_cast<T*>(arena + it.koff), Q,
+                                 (it.N + TM - 1) / TM * TM, tmem, mbar_a, phase);
+    ok = (res & FT_DONE) != 0;
+    if (threadIdx.x == 0) {
+      if (res & FT_BAD) status[it.elem] = 1;
+      if (stamps) {
+        stamps[3 * (size_t)w] = ft_smid();
+        stamps[3 * (size_t)w + 1] = s_t0;
+        stamps[3 * (size_t)w + 2] = ft_global_ns();
+      }
+    }
+    __syncthreads();
+    if (!ok) break;
+  }
+  ft_finish(ok, tmem, mbar_a, phase, tc_err);
 }
 
 // Rows of the digit scratch for an augmented size N (multiple of TM).
@@ -573,29 +654,57 @@ static size_t ft_smem(bool cplx) {
          sizeof(double) * TB * TB;
 }
 
+// the row-exponent array rides after the fixed part; 3328 rows covers N <= 3315 (p = 4)
+constexpr int FT_MAX_RP = 3328;
+
 int factor_tc_init() {
-  // the row-exponent array rides after the fixed part; 3328 rows covers N <= 3315 (p = 4)
-  constexpr size_t exp_bytes = sizeof(int) * 3328;
+  constexpr size_t exp_bytes = sizeof(int) * FT_MAX_RP;
   if (cudaFuncSetAttribute(k_factor_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(ft_smem(false) + exp_bytes)) != cudaSuccess ||
       cudaFuncSetAttribute(k_factor_tc<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(ft_smem(true) + exp_bytes)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_factor_tc_queue<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(ft_smem(false) + exp_bytes)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_factor_tc_queue<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(ft_smem(true) + exp_bytes)) != cudaSuccess)
     return DPG_ERR_CUDA;
   return DPG_OK;
 }
 
 int factor_tc_launch(bool cplx, int count, int N, int nact, int nv, int npiv, const int* ids, void* K, int* status,
-                     int* tc_err, uint8_t* qscr, cudaStream_t s) {
+                     int* tc_err, uint8_t* qscr, cudaStream_t s, unsigned long long* stamps) {
   const int RP = ft_rows(N);
-  if (RP > 3328) return DPG_ERR_UNSUPPORTED;
+  if (RP > FT_MAX_RP) return DPG_ERR_UNSUPPORTED;
   const size_t smem = ft_smem(cplx) + sizeof(int) * (size_t)RP;
   const long long qstride = (long long)factor_tc_scratch_bytes(N, cplx);
   if (cplx)
     k_factor_tc<double2><<<count, FT_THREADS, smem, s>>>(N, nact, nv, npiv, ids, static_cast<double2*>(K), status,
-                                                         tc_err, qscr, qstride, RP);
+                                                         tc_err, qscr, qstride, RP, stamps);
   else
     k_factor_tc<double><<<count, FT_THREADS, smem, s>>>(N, nact, nv, npiv, ids, static_cast<double*>(K), status,
-                                                        tc_err, qscr, qstride, RP);
+                                                        tc_err, qscr, qstride, RP, stamps);
+  return cudaGetLastError() == cudaSuccess ? DPG_OK : DPG_ERR_CUDA;
+}
+
+// Digit scratch of one persistent CTA (the largest item it can meet).
+size_t factor_tc_queue_scratch_bytes(int Nmax) { return factor_tc_scratch_bytes(Nmax, true); }
+
+int factor_tc_queue_launch(bool cplx, const FtItem* items, int nitems, int Nmax, int* counter, void* arena,
+                           int* status, int* tc_err, uint8_t* qscr, unsigned long long* stamps, int grid,
+                           cudaStream_t s) {
+  if (nitems <= 0) return DPG_OK;
+  if (ft_rows(Nmax) > FT_MAX_RP) return DPG_ERR_UNSUPPORTED;
+  const size_t smem = ft_smem(cplx) + sizeof(int) * (size_t)ft_rows(Nmax);
+  const long long qstride = (long long)factor_tc_queue_scratch_bytes(Nmax);
+  if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) return DPG_ERR_CUDA;
+  const int g = grid < nitems ? grid : nitems;
+  unsigned char* ar = static_cast<unsigned char*>(arena);
+  if (cplx)
+    k_factor_tc_queue<double2><<<g, FT_THREADS, smem, s>>>(items, nitems, counter, ar, status, tc_err, qscr, qstride,
+                                                           stamps);
+  else
+    k_factor_tc_queue<double><<<g, FT_THREADS, smem, s>>>(items, nitems, counter, ar, status, tc_err, qscr, qstride,
+                                                          stamps);
   return cudaGetLastError() == cudaSuccess ? DPG_OK : DPG_ERR_CUDA;
 }
 

@@ -53,6 +53,7 @@ class DPG:
         L = _lib.lib()
         self.mesh = mesh
         self.factor_arith = _lib.DPG_FACTOR_TC_SPLIT  # the library's default
+        self.bucketed = False
         keep = dict(
             vert=np.ascontiguousarray(mesh.vert, dtype=np.float64),
             elem=np.ascontiguousarray(mesh.elem, dtype=np.int32),
@@ -153,6 +154,18 @@ class DPG:
     def set_factor_arith(self, arith=_lib.DPG_FACTOR_TC_SPLIT):
         check(_lib.lib().dpg_set_factor_arith(self.h, int(arith)), self.h)
         self.factor_arith = int(arith)
+
+    def set_bucketed(self, enable=True):
+        """Order-bucketed element pass: waves of every order's chunks, one persistent factorisation per wave."""
+        check(_lib.lib().dpg_set_bucketed(self.h, int(enable)), self.h)
+        self.bucketed = bool(enable)
+
+    def factor_balance(self):
+        """SM-busy fraction of the last pass's factorisation launches (1 - idle), their span and element count."""
+        busy, span = C.c_double(), C.c_double()
+        n = C.c_int64()
+        check(_lib.lib().dpg_factor_balance(self.h, C.byref(busy), C.byref(span), C.byref(n)), self.h)
+        return {"sm_busy": busy.value, "span_ms": span.value, "elements": n.value}
 
     def set_wait_limit(self, wait_ns=5_000_000_000, hold=False):
         check(_lib.lib().dpg_set_wait_limit(self.h, int(wait_ns), int(hold)), self.h)

@@ -5,7 +5,8 @@ Step (all on the GPU, through libdpg's C ABI):
   element pass  - quadrature, G_K = L L^H, condensation to S_K, s_K (Sec. 2.3, Algorithm 2)
   assembly      - deterministic sum of S_K, s_K into the CSR trace system
   CG            - to relative residual 1e-10 (default: FP32-inner iterative refinement with
-                  entity-block Jacobi preconditioning; --cg fp64 gives the paper's plain FP64 CG)
+                  entity-block Jacobi preconditioning, the inner operator applied element by element
+                  from FP32 tiles of S_K; --cg fp64 gives the paper's plain FP64 CG)
   estimate      - local recovery of u and the residual estimator eta_K
 Metric: DPG elements per second of the whole step (inputs resident in HBM), with
 the CG time-to-1e-10 and the per-phase breakdown in the same JSON line.
@@ -32,7 +33,7 @@ METRIC = "DPG elements/s (local solve+η_K) & CG time-to-1e-10; mixed/batched vs
 UNIT = "elements/s"
 CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3, "fp64-bjacobi": 4, "ir-bjacobi": 5,
             "ir-bjacobi-half": 5 | 16, "ir64v-bjacobi": 5 | 32, "ir64v": 1 | 32,
-            "dw": 64, "dw-bjacobi": 64 | 4}
+            "dw": 64, "dw-bjacobi": 64 | 4, "ir-ebe": 1 | 128, "ir-bjacobi-ebe": 5 | 128}
 PRECISIONS = {"fp64": 0, "tf32": 1, "3xtf32": 2}
 
 
@@ -284,7 +285,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="waveguide3d")
-    ap.add_argument("--cg", default="ir-bjacobi", choices=sorted(CG_MODES))
+    ap.add_argument("--cg", default="auto", choices=["auto"] + sorted(CG_MODES),
+                    help="auto: ir-bjacobi-ebe (element-by-element inner operator), ir-bjacobi when streaming")
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--max-iter", type=int, default=200000)
@@ -311,6 +313,9 @@ def main():
     ap.add_argument("--precision-report", action="store_true",
                     help="after the timed steps, solve again with FP64 quadrature and report the differences")
     args = ap.parse_args()
+    streaming_cfg = args.stream or args.config in ("cavity3-32", "fichera-amr-1e5", "obstacle-48", "obstacle-64")
+    if args.cg == "auto":  # the element-by-element operator needs every element's stored S_K
+        args.cg = "ir-bjacobi" if streaming_cfg else "ir-bjacobi-ebe"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -333,7 +338,7 @@ def main():
 
     from paper_2609_03155_b300 import dpg
     mesh = config_mesh(args.config)
-    streaming = args.stream or args.config in ("cavity3-32", "fichera-amr-1e5", "obstacle-48", "obstacle-64")
+    streaming = streaming_cfg
     d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk, adjoint=args.adjoint,
                 streaming=streaming)
     mode = CG_MODES[args.cg]
@@ -497,7 +502,7 @@ def main():
     bpi = d.cg_bytes_per_iteration(mode)
     vb = 8 if mode & 1 else 16
     # Hermitian half storage reads each off-diagonal block once: half the values
-    mb = vb // 2 if mode & 16 else vb
+    mb = vb // 2 if mode & (16 | 128) else vb
     algo_bpi = mb * int(d.nnz) + 6 * vb * int(d.n)
     # DRAM traffic per iteration / implementation bytes of the FP32 inner CG
     # kernel, from the ncu capture of the 12x6x24 guide (dram__bytes_read.sum +
@@ -506,16 +511,21 @@ def main():
     CG_TRAFFIC_RATIO_FP32 = 1.022
     cg_s = max(1e-9, tim["cg_kernel_ms"] / 1e3)
     cg_ach = algo_bpi * tim["cg_kernel_iterations"] / cg_s / 1e9
-    roof_cg = {"bound": "hbm", "kernel": "k_cg_persistent<%s> (one cooperative CG solve per launch)"
-               % ("float2" if mode & 1 else "double2"),
+    spmv = ("element by element, FP32 upper-triangle tiles of S_K" if mode & 128 else
+            "Hermitian half storage" if mode & 16 else "CSR rows")
+    roof_cg = {"bound": "hbm", "kernel": "k_cg_persistent<%s> (one cooperative CG solve per launch; SpMV: %s)"
+               % ("float2" if mode & 1 else "double2", spmv),
                "achieved": cg_ach, "peak": hbm_peak, "unit": "GB/s", "frac": cg_ach / hbm_peak,
                "traffic": (CG_TRAFFIC_RATIO_FP32 * bpi * tim["cg_kernel_iterations"] / max(1, tim["cg_kernel_launches"])
-                           if mode & 1 else None),
+                           if (mode & 1) and not (mode & (16 | 128)) else None),
                "traffic_unit": "bytes per launch (ncu ratio 1.022 x implementation bytes, from the 12x6x24 capture)",
                "peak_source": hbm_src, "bytes_per_iteration": algo_bpi,
                "bytes_rule": f"{mb} B x nnz + 6 x {vb} B x n (matrix values and six vector passes)",
                "overhead_bytes_per_iteration": bpi - algo_bpi,
-               "overhead_rule": "per-entity column lists, block-Jacobi inverses and the other vector passes",
+               "overhead_rule": ("element tile padding and the overlap of element matrices, the trace-slot "
+                                 "gathers, products and lists, block-Jacobi inverses and the other vector passes"
+                                 if mode & 128 else
+                                 "per-entity column lists, block-Jacobi inverses and the other vector passes"),
                "achieved_with_overhead": bpi * tim["cg_kernel_iterations"] / cg_s / 1e9,
                "iterations": tim["cg_kernel_iterations"], "launches": tim["cg_kernel_launches"],
                "avg_launch_ms": tim["cg_kernel_ms"] / max(1, tim["cg_kernel_launches"]),

@@ -96,7 +96,7 @@ enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2
 enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
 enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8, DPG_CG_HALF = 16,
-       DPG_CG_IR_V64 = 32, DPG_CG_DW = 64 };
+       DPG_CG_IR_V64 = 32, DPG_CG_DW = 64, DPG_CG_EBE = 128 };
 enum { DPG_FLAG_ADJOINT = 1, DPG_FLAG_STREAM = 2 };
 /* Arithmetic of the element factorisation's trailing updates (dpg_set_factor_arith). */
 enum { DPG_FACTOR_FP64 = 0, DPG_FACTOR_TC_SPLIT = 1 };
@@ -222,6 +222,15 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * (Dekker's two-product by FMA, Knuth's two-sum) on the FP32 pipes: FP64-class
  * accuracy (the convergence of FP64 CG) at the speed of the memory system
  * instead of the FP64 pipe.  The stopping test is on the FP64 residual.
+ * DPG_CG_EBE may be or-ed to DPG_CG_IR_FP32 (not with DPG_CG_HALF or
+ * DPG_CG_IR_V64; not in streaming mode): the inner solves apply the matrix
+ * element by element, A p = sum_K R_K^T S_K R_K p, from an FP32 copy of every
+ * element's condensed S_K kept as the upper triangle of 32 x 32 tiles (each
+ * Hermitian element matrix read once per product, the lower triangle applied
+ * as the conjugate transpose); each element's product goes to its trace
+ * slots and each row then sums its slots in ascending order (deterministic).
+ * The assembled matrix stays for the FP64 residuals and the preconditioner.
+ * Errors add DPG_ERR_UNSUPPORTED (streaming, or over 2^31 trace slots).
  * DPG_CG_X0 may be or-ed too: start from the x passed in (resume a stopped
  * solve, or warm-start from a nearby problem's solution) instead of x0 = 0.
  * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or

@@ -41,7 +41,8 @@ static void free_all(dpg_handle* h) {
                   h->d_Pk, h->d_blk, h->d_blk_colptr, h->d_cols, h->d_binv_ptr, h->d_binv, h->d_binv32,
                   h->d_zv, h->d_z32, h->d_d64, h->ws.Q, h->d_est_neg,
                   h->d_rowptr_h, h->d_toff, h->d_rev_ptr, h->d_rev_off, h->d_val32h, h->d_T,
-                  h->d_valdw, h->d_pdw, h->d_binvdw};
+                  h->d_valdw, h->d_pdw, h->d_binvdw, h->d_ebe, h->d_ebe_toff, h->d_ebe_hoff, h->d_ebe_rptr,
+                  h->d_ebe_ridx, h->d_ebe_ys};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->d_soff && h->d_soff != h->d_off) cudaFree(h->d_soff);

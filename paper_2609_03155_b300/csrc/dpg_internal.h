@@ -242,6 +242,16 @@ struct dpg_handle {
   float4* d_pdw = nullptr;          // n
   float4* d_binvdw = nullptr;       // block inverses
   bool have_valdw = false, have_binvdw = false;
+  // element-by-element FP32 operator of the inner solves (DPG_CG_EBE)
+  float2* d_ebe = nullptr;          // per element: upper-triangle 32 x 32 tiles of S_K
+  int64_t* d_ebe_toff = nullptr;    // per element: first tile entry (ne + 1)
+  int64_t* d_ebe_hoff = nullptr;    // per element: first slot (ne + 1)
+  int64_t* d_ebe_rptr = nullptr;    // per row: first entry of its slot list (n + 1)
+  int32_t* d_ebe_ridx = nullptr;    // slot lists
+  float2* d_ebe_ys = nullptr;       // per slot: the element product
+  bool have_ebe_idx = false, have_ebe = false;
+  int ebe_nbmax = 1;
+  int64_t ebe_tiles = 0, ebe_slots = 0, ebe_links = 0;
   bool have_elements = false, have_system = false, have_val32 = false, have_dinv = false;
   double* d_dinv = nullptr;     // inverse diagonal (Jacobi)
   float* d_dinv32 = nullptr;

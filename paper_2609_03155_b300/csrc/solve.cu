@@ -87,6 +87,7 @@ void system_changed(dpg_handle* h) {
   h->have_system = true;
   h->have_val32 = false;
   h->have_val32h = false;
+  h->have_ebe = false;
   h->have_valdw = false;
   h->have_binvdw = false;
   h->have_dinv = false;
@@ -136,6 +137,18 @@ struct SysView {
   const int64_t* toff;
   const int64_t* rev_ptr;
   const int64_t* rev_off;
+  // element-by-element operator (FP32 inner solves): per element the upper
+  // triangle of 32 x 32 tiles of S_K, its slots (trace map) and, per row, the
+  // slots that carry it
+  int ne;
+  int ebe_nbmax;              // 32-row blocks of the largest element
+  const float2* ebe;          // tiles, element by element
+  const int64_t* ebe_toff;    // per element: first tile entry (ne + 1)
+  const int64_t* ebe_hoff;    // per element: first slot (ne + 1)
+  const int32_t* l2g;         // per slot: global row (negative: fixed)
+  const int64_t* ebe_rptr;    // per row: first entry of its slot list (n + 1)
+  const int32_t* ebe_ridx;    // slot lists, ascending
+  float2* ebe_ys;             // per slot: the element product
 };
 
 struct CgState {          // device-resident
@@ -684,8 +697,79 @@ __global__ void k_to_dw(int64_t n, const double2* __restrict__ a, float4* b) {
 // V: precision of the vectors and recurrences; Mv: precision of the stored
 // matrix and of the SpMV products (FP32 values with FP64 recurrences keeps the
 // convergence rate of FP64 CG at the bandwidth of an FP32 matrix).
-template <typename V, typename Mv, bool HALF>
-__global__ void __launch_bounds__(CG_THREADS, HALF ? 4 : 5) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
+// Element-by-element product y_K = S_K x_K of one element by one warp, FP32.
+// The element's S_K (Hermitian, n_h rows) is stored as the upper triangle of
+// 32 x 32 tiles (I <= J, row-major, I-major order; diagonal tiles whole, zero
+// padding past n_h).  Lane l holds column l of a tile, loaded one row per
+// step (coalesced): the column part of an off-diagonal tile,
+// y_J[l] += sum_i conj(a_il) x_I[i], stays in the lane; the row part,
+// y_I[i] += sum_l a_il x_J[l], is summed across the warp by a transposing
+// reduction (5 exchange steps, 31 shuffles per component) that leaves row l's
+// sum in lane l.  Every sum has one fixed order.  xs, ya: this warp's shared
+// staging of x_K and y_K (nbmax x 32 entries each).  y_K goes to the slots.
+__device__ __forceinline__ void ebe_element(const SysView& S, int e, const float2* __restrict__ p, float2* xs,
+                                            float2* ya) {
+  const int lane = threadIdx.x & 31;
+  const int64_t h0 = S.ebe_hoff[e];
+  const int nh = (int)(S.ebe_hoff[e + 1] - h0);
+  const int nb = (nh + 31) >> 5;
+  for (int i = lane; i < nb * 32; i += 32) {
+    float2 v = make_float2(0.0f, 0.0f);
+    if (i < nh) {
+      const int g = S.l2g[h0 + i];
+      if (g >= 0) v = p[g];
+    }
+    xs[i] = v;
+    ya[i] = make_float2(0.0f, 0.0f);
+  }
+  __syncwarp();
+  const float2* t = S.ebe + S.ebe_toff[e];
+  for (int I = 0; I < nb; ++I) {
+    for (int J = I; J < nb; ++J, t += 1024) {
+      const float2 xj = xs[J * 32 + lane];
+      float pr[32], pi[32];
+      float cr = 0.0f, ci = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float2 a = t[i * 32 + lane];
+        const float2 xi = xs[I * 32 + i];
+        cr = fmaf(a.x, xi.x, fmaf(a.y, xi.y, cr));   // conj(a) x_i
+        ci = fmaf(a.x, xi.y, fmaf(-a.y, xi.x, ci));
+        pr[i] = fmaf(a.x, xj.x, -a.y * xj.y);         // a x_j
+        pi[i] = fmaf(a.x, xj.y, a.y * xj.x);
+      }
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const bool up = (lane & sh) != 0;
+#pragma unroll
+        for (int k = 0; k < sh; ++k) {
+          const float sr = up ? pr[k] : pr[k + sh], si = up ? pi[k] : pi[k + sh];
+          const float kr = up ? pr[k + sh] : pr[k], ki = up ? pi[k + sh] : pi[k];
+          pr[k] = kr + __shfl_xor_sync(0xffffffffu, sr, sh);
+          pi[k] = ki + __shfl_xor_sync(0xffffffffu, si, sh);
+        }
+      }
+      float2 yr = ya[I * 32 + lane];
+      yr.x += pr[0];
+      yr.y += pi[0];
+      ya[I * 32 + lane] = yr;
+      if (J > I) {
+        float2 yc = ya[J * 32 + lane];
+        yc.x += cr;
+        yc.y += ci;
+        ya[J * 32 + lane] = yc;
+      }
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < nh; i += 32) S.ebe_ys[h0 + i] = ya[i];
+  __syncwarp();
+}
+
+// SP: the SpMV of the inner solve: 0 rows of the CSR, 1 Hermitian half
+// storage, 2 element by element.
+template <typename V, typename Mv, int SP>
+__global__ void __launch_bounds__(CG_THREADS, SP == 1 ? 4 : (SP == 2 ? 2 : 5)) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
                                                              V* Ap, V* z, int precond,
                                                              const typename RealOf<V>::T* __restrict__ dinv,
                                                              const V* __restrict__ binv, double* red, CgState* st,
@@ -722,7 +806,26 @@ __global__ void __launch_bounds__(CG_THREADS, HALF ? 4 : 5) k_cg_persistent(SysV
   while (!done && it < max_iter) {
     // A: Ap = A p and Re(p^H A p)
     R pap = 0;
-    if (HALF) {
+    if constexpr (SP == 2) {
+      // element products into the slots, then each row the sum of its slots
+      float2* xs = reinterpret_cast<float2*>(cg_smem + (CG_THREADS / 32) * (size_t)S.dmax * sizeof(V)) +
+                   (size_t)(threadIdx.x >> 5) * 2 * 32 * S.ebe_nbmax;
+      float2* ya = xs + 32 * S.ebe_nbmax;
+      for (int e = gw; e < S.ne; e += warps) ebe_element(S, e, reinterpret_cast<const float2*>(p), xs, ya);
+      if (!grid_barrier(st, gen)) return;
+      for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < S.n; row += (int64_t)G * blockDim.x) {
+        float yr = 0.0f, yi = 0.0f;
+        for (int64_t k = S.ebe_rptr[row]; k < S.ebe_rptr[row + 1]; ++k) {
+          const float2 v = S.ebe_ys[S.ebe_ridx[k]];
+          yr += v.x;
+          yi += v.y;
+        }
+        const V y = mkv(yr, yi, (V*)nullptr);
+        Ap[row] = y;
+        const V pr = p[row];
+        pap += pr.x * y.x + pr.y * y.y;
+      }
+    } else if constexpr (SP == 1) {
       // lower blocks and diagonal blocks, conjugate-transpose partial sums
       for (int b = gw; b < S.nblk; b += warps) half_block_lower<V, Mv>(S, b, val, p, Ap, T);
       if (!grid_barrier(st, gen)) return;
@@ -943,6 +1046,15 @@ static SysView sys_view(dpg_handle* h) {
   v.toff = h->d_toff;
   v.rev_ptr = h->d_rev_ptr;
   v.rev_off = h->d_rev_off;
+  v.ne = h->ne;
+  v.ebe_nbmax = h->ebe_nbmax;
+  v.ebe = h->d_ebe;
+  v.ebe_toff = h->d_ebe_toff;
+  v.ebe_hoff = h->d_ebe_hoff;
+  v.l2g = h->d_l2g;
+  v.ebe_rptr = h->d_ebe_rptr;
+  v.ebe_ridx = h->d_ebe_ridx;
+  v.ebe_ys = h->d_ebe_ys;
   return v;
 }
 
@@ -1019,16 +1131,17 @@ static int launch_persistent(dpg_handle* h, const void* kernel, void** args, CgS
 }
 
 // One persistent solve of A d = r0 (d = 0 at entry; r holds r0 at entry).
-template <typename V, typename Mv, bool HALF>
+template <typename V, typename Mv, int SP>
 static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
                           const typename RealOf<V>::T* dinv, const V* binv, double tol2, int max_iter,
                           cudaStream_t s, int* iters, double* rr_out, V* T = nullptr) {
-  const size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
+  size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
+  if (SP == 2) smem += (CG_THREADS / 32) * 2 * 32 * (size_t)h->ebe_nbmax * sizeof(float2);  // x_K, y_K per warp
   SysView S = sys_view(h);
   double* red = h->d_red;
   CgState* st = nullptr;
   void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st, &T};
-  return launch_persistent(h, (const void*)k_cg_persistent<V, Mv, HALF>, args, &st, smem, tol2, max_iter,
+  return launch_persistent(h, (const void*)k_cg_persistent<V, Mv, SP>, args, &st, smem, tol2, max_iter,
                            sizeof(Mv) == sizeof(float2), s, iters, rr_out);
 }
 
@@ -1085,6 +1198,81 @@ static int prepare_preconditioner(dpg_handle* h, cudaStream_t s) {
   DPG_CUDA_TRY(h, cudaGetLastError());
   h->have_binv = true;
   h->have_dinv = true;
+  return DPG_OK;
+}
+
+// Element-by-element FP32 operator: per element the upper-triangle 32 x 32
+// tiles of its stored S_K (row-major n_h x n_h, FP64), zero past n_h.
+__global__ void __launch_bounds__(256) k_ebe_pack(const ElemOff* __restrict__ off, const int64_t* __restrict__ toff,
+                                                  const double2* __restrict__ Sst, float2* ebe) {
+  const int e = blockIdx.x;
+  const int nh = (int)(off[e + 1].h - off[e].h), nb = (nh + 31) >> 5;
+  const double2* Se = Sst + off[e].S;
+  float2* t = ebe + toff[e];
+  const int ntile = nb * (nb + 1) / 2;
+  for (int64_t q = threadIdx.x; q < (int64_t)ntile * 1024; q += blockDim.x) {
+    int k = (int)(q >> 10);
+    const int ij = (int)(q & 1023), i = ij >> 5, j = ij & 31;
+    int I = 0;
+    while (k >= nb - I) {  // tile k of the I-major upper triangle
+      k -= nb - I;
+      ++I;
+    }
+    const int J = I + k;
+    const int row = I * 32 + i, col = J * 32 + j;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (row < nh && col < nh) {
+      const double2 a = Se[(size_t)row * nh + col];
+      v = make_float2((float)a.x, (float)a.y);
+    }
+    t[q] = v;
+  }
+}
+
+// Index structures of the element-by-element operator (once per mesh): tile
+// and slot offsets per element, and per row its slots in ascending order.
+static int build_ebe_index(dpg_handle* h) {
+  if (h->have_ebe_idx) return DPG_OK;
+  const int ne = h->ne;
+  std::vector<int64_t> toff(ne + 1, 0), hoff(ne + 1, 0);
+  int nbmax = 1;
+  for (int e = 0; e < ne; ++e) {
+    const int nh = (int)(h->off[e + 1].h - h->off[e].h), nb = (nh + 31) / 32;
+    nbmax = std::max(nbmax, nb);
+    toff[e + 1] = toff[e] + (int64_t)nb * (nb + 1) / 2 * 1024;
+    hoff[e] = h->off[e].h;
+  }
+  hoff[ne] = h->off[ne].h;
+  const int64_t slots = hoff[ne];
+  if (slots >= ((int64_t)1 << 31)) {
+    h->err = "too many trace slots for the element-by-element operator";
+    return DPG_ERR_UNSUPPORTED;
+  }
+  std::vector<int64_t> rptr(h->n + 1, 0);
+  for (int64_t q = 0; q < slots; ++q)
+    if (h->l2g[q] >= 0) rptr[h->l2g[q] + 1] += 1;
+  for (int64_t i = 0; i < h->n; ++i) rptr[i + 1] += rptr[i];
+  std::vector<int32_t> ridx(std::max<int64_t>(1, rptr[h->n]));
+  std::vector<int64_t> fill(rptr.begin(), rptr.end() - 1);
+  for (int64_t q = 0; q < slots; ++q)
+    if (h->l2g[q] >= 0) ridx[fill[h->l2g[q]]++] = (int32_t)q;
+  int rc = 0;
+  rc |= ensure_buf(h, (void**)&h->d_ebe, sizeof(float2) * std::max<int64_t>(1, toff[ne]));
+  rc |= ensure_buf(h, (void**)&h->d_ebe_toff, sizeof(int64_t) * (ne + 1));
+  rc |= ensure_buf(h, (void**)&h->d_ebe_hoff, sizeof(int64_t) * (ne + 1));
+  rc |= ensure_buf(h, (void**)&h->d_ebe_rptr, sizeof(int64_t) * (h->n + 1));
+  rc |= ensure_buf(h, (void**)&h->d_ebe_ridx, sizeof(int32_t) * ridx.size());
+  rc |= ensure_buf(h, (void**)&h->d_ebe_ys, sizeof(float2) * std::max<int64_t>(1, slots));
+  if (rc) return DPG_ERR_NOMEM;
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_ebe_toff, toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_ebe_hoff, hoff.data(), sizeof(int64_t) * hoff.size(), cudaMemcpyHostToDevice));
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_ebe_rptr, rptr.data(), sizeof(int64_t) * rptr.size(), cudaMemcpyHostToDevice));
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_ebe_ridx, ridx.data(), sizeof(int32_t) * ridx.size(), cudaMemcpyHostToDevice));
+  h->ebe_nbmax = nbmax;
+  h->ebe_tiles = toff[ne];
+  h->ebe_slots = slots;
+  h->ebe_links = rptr[h->n];
+  h->have_ebe_idx = true;
   return DPG_OK;
 }
 
@@ -1167,7 +1355,18 @@ int64_t cg_bytes_per_iteration(const dpg_handle* h, int mode) {
   const int64_t mb = ir ? 8 : 16, vb = (ir && !v64) ? 8 : 16;  // DW: 16 B values (two FP32 pairs), FP64 vectors
   int64_t ncol = (int64_t)h->cols.size();
   int64_t bytes = 0;
-  if (ir && (mode & DPG_CG_HALF)) {
+  if (ir && (mode & DPG_CG_EBE)) {
+    // element by element: the tiles, per slot the x gather, the trace map, the
+    // product written and read back, its index in the row lists; per row the
+    // list pointer; the vector passes
+    int64_t tiles = 0;
+    for (int e = 0; e < h->ne; ++e) {
+      const int64_t nb = (h->off[e + 1].h - h->off[e].h + 31) / 32;
+      tiles += nb * (nb + 1) / 2 * 1024;
+    }
+    const int64_t slots = h->off[h->ne].h;
+    bytes = 8 * tiles + slots * (8 + 4 + 8 + 8 + 4) + 8 * (h->n + 1) + 13 * vb * h->n;
+  } else if (ir && (mode & DPG_CG_HALF)) {
     // half storage: stored prefixes, their column lists, the partial sums T
     // (written once, read once) and their offsets
     int64_t nh = 0, ncol_h = 0, tl = 0;
@@ -1201,8 +1400,9 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     return DPG_ERR_ARG;
   }
   if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0 | DPG_CG_HALF | DPG_CG_IR_V64 |
-               DPG_CG_DW) ||
+               DPG_CG_DW | DPG_CG_EBE) ||
       ((mode & DPG_CG_HALF) && (mode & DPG_CG_IR_V64)) ||
+      ((mode & DPG_CG_EBE) && (!(mode & DPG_CG_IR_FP32) || (mode & (DPG_CG_HALF | DPG_CG_IR_V64)))) ||
       ((mode & DPG_CG_DW) && (mode & (DPG_CG_IR_FP32 | DPG_CG_JACOBI))) ||
       ((mode & DPG_CG_JACOBI) && (mode & DPG_CG_BLOCK_JACOBI))) {
     h->err = "unknown CG mode";
@@ -1228,6 +1428,11 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
   }
   if (rc) return DPG_ERR_NOMEM;
   const bool half = ir && (mode & DPG_CG_HALF) && !(mode & DPG_CG_IR_V64);
+  const bool ebe = ir && (mode & DPG_CG_EBE);
+  if (ebe && h->stream) {
+    h->err = "the element-by-element operator reads every element's S_K; streaming keeps chunk stores only";
+    return DPG_ERR_UNSUPPORTED;
+  }
   const bool dw = (mode & DPG_CG_DW) != 0;
   if (dw) {
     rc |= ensure_buf(h, (void**)&h->d_valdw, sizeof(float4) * h->nnz);
@@ -1236,6 +1441,9 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
   }
   if (half) {
     rc = build_half(h);
+    if (rc) return rc;
+  } else if (ebe) {
+    rc = build_ebe_index(h);
     if (rc) return rc;
   } else if (ir) {
     rc = ensure_buf(h, (void**)&h->d_val32, sizeof(float2) * h->nnz);
@@ -1269,7 +1477,13 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     h->launches += 1;
     h->have_val32h = true;
   }
-  if (ir && !half && !h->have_val32) {
+  if (ebe && !h->have_ebe) {
+    k_ebe_pack<<<h->ne, 256, 0, s>>>(h->d_off, h->d_ebe_toff, h->d_S, h->d_ebe);
+    h->launches += 1;
+    DPG_CUDA_TRY(h, cudaGetLastError());
+    h->have_ebe = true;
+  }
+  if (ir && !half && !ebe && !h->have_val32) {
     k_to_f32<<<1184, 256, 0, s>>>(h->nnz, h->d_val, h->d_val32);
     h->launches += 1;
     h->have_val32 = true;
@@ -1308,7 +1522,7 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     } else if (ir && (mode & DPG_CG_IR_V64)) {
       // inner CG over the FP32 matrix (FP32 products) with FP64 vectors and recurrences
       const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
-      rc = run_persistent<double2, float2, false>(h, h->d_val32, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond,
+      rc = run_persistent<double2, float2, 0>(h, h->d_val32, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond,
                                                   h->d_dinv, h->d_binv, itol * itol, max_iter - total_iters, s, &it,
                                                   &rr);
       if (rc) return rc;
@@ -1318,13 +1532,17 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
       k_to_f32<<<1184, 256, 0, s>>>((int64_t)n, h->d_r, h->d_r32);
       h->launches += 1;
       if (half)
-        rc = run_persistent<float2, float2, true>(h, h->d_val32h, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
-                                                  precond, h->d_dinv32, h->d_binv32, itol * itol,
-                                                  max_iter - total_iters, s, &it, &rr, h->d_T);
+        rc = run_persistent<float2, float2, 1>(h, h->d_val32h, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
+                                               precond, h->d_dinv32, h->d_binv32, itol * itol,
+                                               max_iter - total_iters, s, &it, &rr, h->d_T);
+      else if (ebe)
+        rc = run_persistent<float2, float2, 2>(h, (const float2*)nullptr, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32,
+                                               h->d_z32, precond, h->d_dinv32, h->d_binv32, itol * itol,
+                                               max_iter - total_iters, s, &it, &rr);
       else
-        rc = run_persistent<float2, float2, false>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
-                                                   precond, h->d_dinv32, h->d_binv32, itol * itol,
-                                                   max_iter - total_iters, s, &it, &rr);
+        rc = run_persistent<float2, float2, 0>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
+                                               precond, h->d_dinv32, h->d_binv32, itol * itol,
+                                               max_iter - total_iters, s, &it, &rr);
       if (rc) return rc;
       k_add_correction<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_x32);
     } else {

@@ -183,10 +183,10 @@ def test_te10_waveguide_field_error(dpg_mod):
     d.destroy()
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 1 | 16, 5 | 16, 5 | 32, 64, 64 | 4])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 1 | 16, 5 | 16, 5 | 32, 64, 64 | 4, 1 | 128, 5 | 128])
 def test_cg_modes_match_fp64(dpg_mod, mode):
-    """IR (FP32 inner: full or Hermitian half storage, FP32 or FP64 inner vectors), Jacobi, entity-block Jacobi
-    and the double-word (FP32 pair) solver reach the plain FP64 CG solution."""
+    """IR (FP32 inner: full or Hermitian half storage or element by element, FP32 or FP64 inner vectors),
+    Jacobi, entity-block Jacobi and the double-word (FP32 pair) solver reach the plain FP64 CG solution."""
     mesh = _lossy_jittered(1, n=(2, 2, 2))
     d = dpg_mod.DPG(mesh)
     d.element_batch()
@@ -215,7 +215,26 @@ def test_deterministic_assembly_and_solve(dpg_mod):
     x2, _ = d.cg_solve(rtol=1e-12)
     assert np.array_equal(v1, v2) and np.array_equal(b1, b2)
     assert torch.equal(x1, x2)
+    # the element-by-element inner operator sums every row's slots in one fixed order
+    x3, _ = d.cg_solve(mode=5 | 128, rtol=1e-12)
+    x4, _ = d.cg_solve(mode=5 | 128, rtol=1e-12)
+    assert torch.equal(x3, x4)
     d.destroy()
+
+
+def test_element_by_element_operator_on_mixed_degrees_and_hanging_faces(dpg_mod):
+    """Per-element slot counts differ (orders 1..4) and restricted elements
+    map slots through the hanging-face constraints: the element-by-element
+    inner solves must still reach the FP64 solution."""
+    for mesh in (inputs.fichera_cavity(2, grade=1.5, mix=(0.4, 0.3, 0.3)), inputs.fichera_amr(2, radius=0.5)):
+        d = dpg_mod.DPG(mesh)
+        d.element_batch()
+        d.assemble()
+        x64, _ = d.cg_solve(rtol=1e-12, max_iter=200000)
+        xe, re_ = d.cg_solve(mode=5 | 128, rtol=1e-12, max_iter=200000, inner_rtol=1e-4)
+        assert re_['converged']
+        assert rel(xe.cpu().numpy(), x64.cpu().numpy()) < 1e-9
+        d.destroy()
 
 
 def _obstacle_cavity(n=3, p=1):

@@ -509,6 +509,9 @@ def main():
     # dram__bytes_write.sum over 279 iterations); the traffic per iteration
     # scales with the system, so a launch's traffic is this ratio times its bytes
     CG_TRAFFIC_RATIO_FP32 = 1.022
+    # the same for the element-by-element operator (12x6x24 capture: 444 MB of
+    # DRAM traffic per iteration against 450 MB of implementation bytes)
+    CG_TRAFFIC_RATIO_EBE = 0.99
     cg_s = max(1e-9, tim["cg_kernel_ms"] / 1e3)
     cg_ach = algo_bpi * tim["cg_kernel_iterations"] / cg_s / 1e9
     spmv = ("element by element, FP32 upper-triangle tiles of S_K" if mode & 128 else
@@ -516,9 +519,11 @@ def main():
     roof_cg = {"bound": "hbm", "kernel": "k_cg_persistent<%s> (one cooperative CG solve per launch; SpMV: %s)"
                % ("float2" if mode & 1 else "double2", spmv),
                "achieved": cg_ach, "peak": hbm_peak, "unit": "GB/s", "frac": cg_ach / hbm_peak,
-               "traffic": (CG_TRAFFIC_RATIO_FP32 * bpi * tim["cg_kernel_iterations"] / max(1, tim["cg_kernel_launches"])
-                           if (mode & 1) and not (mode & (16 | 128)) else None),
-               "traffic_unit": "bytes per launch (ncu ratio 1.022 x implementation bytes, from the 12x6x24 capture)",
+               "traffic": ((CG_TRAFFIC_RATIO_EBE if mode & 128 else CG_TRAFFIC_RATIO_FP32) * bpi
+                           * tim["cg_kernel_iterations"] / max(1, tim["cg_kernel_launches"])
+                           if (mode & 1) and not (mode & 16) else None),
+               "traffic_unit": "bytes per launch (ncu ratio %s x implementation bytes, from the 12x6x24 capture)"
+                               % ("0.99" if mode & 128 else "1.022"),
                "peak_source": hbm_src, "bytes_per_iteration": algo_bpi,
                "bytes_rule": f"{mb} B x nnz + 6 x {vb} B x n (matrix values and six vector passes)",
                "overhead_bytes_per_iteration": bpi - algo_bpi,

@@ -374,10 +374,12 @@ int dpg_set_factor_arith(dpg_handle* h, int32_t arith);
  * slice of the K workspace, then factors all of them in ONE persistent launch
  * (one CTA per SM) that takes elements from a work list ordered longest
  * first (complex before real, then by matrix size: LPT), then extracts chunk
- * by chunk.  The number of waves: at least what a 48 GB budget for the K
- * workspace requires, and at least enough that the costliest list (largest
- * N^3, complex four times real) puts no more elements into a wave than there
- * are SMs; with the setup's chunk size, the largest list's share of a wave.  enable = 0: one launch per chunk of a single order (default).
+ * by chunk.  Waves are formed per wave group (one per chunk colour in
+ * streaming mode, one otherwise).  A group's number of waves: at least what a
+ * 48 GB budget for the K workspace requires, and at least enough that its
+ * costliest list (largest N^3, complex four times real) puts no more elements
+ * into a wave than there are SMs; with the setup's chunk size, the group's
+ * largest list's share of a wave.  enable = 0: one launch per chunk of a single order (default).
  * Results are identical in both modes (the same per-element arithmetic).
  * Changing the mode reallocates the chunk workspace and invalidates the
  * element stores.  The FP64-pipe factorisation (DPG_FACTOR_FP64) keeps one

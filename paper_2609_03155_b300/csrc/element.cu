@@ -959,6 +959,7 @@ static size_t chunk_bytes(const Sizes& S, bool fp64q) {
 struct ElemList {
   int g = 0;
   bool real = false;
+  int colour = 0;  // streaming: the chunk colour of the list (one wave group per colour); else 0
   std::vector<int> elems;
 };
 
@@ -973,22 +974,29 @@ static std::vector<ElemList> element_lists(const dpg_handle* h, bool real) {
     } else {
       lists.push_back(G.elems);
     }
+    std::vector<int> colours(lists.size(), 0);
     if (h->stream) {
       std::vector<std::vector<int>> by_colour;
+      colours.clear();
       for (const std::vector<int>& L : lists)
         for (int c = 0; c < h->ncolor; ++c) {
           std::vector<int> part;
           for (int e : L)
             if (h->elem_color[e] == c) part.push_back(e);
-          if (!part.empty()) by_colour.push_back(part);
+          if (!part.empty()) {
+            by_colour.push_back(part);
+            colours.push_back(c);
+          }
         }
       lists = by_colour;
     }
-    for (std::vector<int>& L : lists) {
+    for (size_t k = 0; k < lists.size(); ++k) {
+      std::vector<int>& L = lists[k];
       if (L.empty()) continue;
       ElemList el;
       el.g = g;
       el.real = real && h->is_real[L[0]];
+      el.colour = colours[k];
       el.elems = std::move(L);
       out.push_back(std::move(el));
     }
@@ -1004,46 +1012,64 @@ static size_t k_bytes(const Sizes& S, bool real) {
 // Chunk of list l in wave w of the order-bucketed pass: ceil(n_l / waves) elements.
 static int wave_cap(size_t n, int waves) { return (int)((n + waves - 1) / waves); }
 
+// Waves of the order-bucketed pass, per list.  The lists form wave groups
+// (one per chunk colour in streaming mode, one otherwise); a group's waves
+// each take ceil(n_l / waves) elements of every list of the group.  A group
+// has at least as many waves as the K arena budget (48 GB) requires, and at
+// least enough that its costliest list (largest N^3, complex 4x real) puts no
+// more elements into a wave than there are SMs, since an SM that got two of
+// them would double the wave's span; otherwise as few as possible, so that
+// the cheaper elements fill the SMs around the long ones.  With the caller's
+// chunk size: the group's largest list's share of a wave.
+static std::vector<int> list_waves(const dpg_handle* h, const std::vector<ElemList>& lists, int chunk, int sms) {
+  int ngroup = 1;
+  for (const ElemList& L : lists) ngroup = std::max(ngroup, L.colour + 1);
+  std::vector<int> waves_of(ngroup, 1);
+  const size_t budget = (size_t)48 << 30;
+  for (int c = 0; c < ngroup; ++c) {
+    size_t total = 0, nmax = 0, ncost = 0;
+    double cmax = -1.0;
+    for (const ElemList& L : lists) {
+      if (L.colour != c) continue;
+      const Sizes& S = h->grp[L.g].sz;
+      total += k_bytes(S, L.real) * L.elems.size();
+      nmax = std::max(nmax, L.elems.size());
+      const double cost = (double)S.N * S.N * S.N * (L.real ? 1.0 : 4.0);
+      if (cost > cmax) {
+        cmax = cost;
+        ncost = L.elems.size();
+      }
+    }
+    if (nmax == 0) continue;
+    int w;
+    if (chunk > 0) {
+      w = (int)((nmax + chunk - 1) / chunk);
+    } else {
+      const int w_mem = (int)((total + budget - 1) / budget);
+      const int w_sm = (int)((ncost + sms - 1) / sms);
+      w = std::max(w_mem, w_sm);
+    }
+    waves_of[c] = std::max(1, w);
+  }
+  std::vector<int> out(lists.size());
+  for (size_t l = 0; l < lists.size(); ++l) out[l] = waves_of[lists[l].colour];
+  return out;
+}
+
 void set_default_caps(dpg_handle* h, int chunk) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   h->chunk_req = chunk;
   if (h->bucketed) {
-    // Every list contributes ceil(n_l / waves) elements to each wave.  The
-    // number of waves: at least enough for the K arena budget (48 GB), and at
-    // least enough that the costliest list (largest N^3, complex 4x real)
-    // puts no more elements into a wave than there are SMs, since an SM that
-    // got two of them would double the wave's span; otherwise as few as
-    // possible, so that the cheaper elements fill the SMs around them.  With
-    // the caller's chunk: the largest list's share of a wave.
     const std::vector<ElemList> lists = element_lists(h, h->allow_real);
-    size_t total = 0, nmax = 1, ncost = 1;
-    double cmax = -1.0;
-    for (const ElemList& L : lists) {
-      const Sizes& S = h->grp[L.g].sz;
-      total += k_bytes(S, L.real) * L.elems.size();
-      nmax = std::max(nmax, L.elems.size());
-      const double c = (double)S.N * S.N * S.N * (L.real ? 1.0 : 4.0);
-      if (c > cmax) {
-        cmax = c;
-        ncost = L.elems.size();
-      }
-    }
-    const size_t budget = (size_t)48 << 30;
-    int waves;
-    if (chunk > 0) {
-      waves = (int)((nmax + chunk - 1) / chunk);
-    } else {
-      const int w_mem = (int)((total + budget - 1) / budget);
-      const int w_sm = (int)((ncost + sms - 1) / sms);
-      waves = std::max(w_mem, w_sm);
-    }
-    h->nwaves = std::max(1, waves);
+    const std::vector<int> lw = list_waves(h, lists, chunk, sms);
+    h->nwaves = 0;
+    for (int w : lw) h->nwaves = std::max(h->nwaves, w);
     for (Group& G : h->grp) G.cap = 1;
-    for (const ElemList& L : lists) {
-      Group& G = h->grp[L.g];
-      G.cap = std::max(G.cap, wave_cap(L.elems.size(), h->nwaves));
+    for (size_t l = 0; l < lists.size(); ++l) {
+      Group& G = h->grp[lists[l].g];
+      G.cap = std::max(G.cap, wave_cap(lists[l].elems.size(), lw[l]));
     }
     return;
   }
@@ -1088,17 +1114,21 @@ int alloc_workspace(dpg_handle* h) {
   if (h->bucketed) {
     // the K arena holds one wave: every list's chunk side by side (256-byte
     // aligned slices); the persistent factorisation's digit scratch is per SM
-    size_t arena = 0;
-    int nmax = 1;
-    for (const ElemList& L : element_lists(h, h->allow_real)) {
-      const Sizes& S = h->grp[L.g].sz;
-      arena += (k_bytes(S, L.real) * wave_cap(L.elems.size(), h->nwaves) + 255) / 256 * 256;
-      nmax = std::max(nmax, S.N);
-    }
-    bK = std::max(bK, arena);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const std::vector<ElemList> lists = element_lists(h, h->allow_real);
+    const std::vector<int> lw = list_waves(h, lists, h->chunk_req, sms);
+    std::vector<size_t> arena_of(1, 0);
+    int nmax = 1;
+    for (size_t l = 0; l < lists.size(); ++l) {
+      const ElemList& L = lists[l];
+      const Sizes& S = h->grp[L.g].sz;
+      if ((int)arena_of.size() <= L.colour) arena_of.resize(L.colour + 1, 0);
+      arena_of[L.colour] += (k_bytes(S, L.real) * wave_cap(L.elems.size(), lw[l]) + 255) / 256 * 256;
+      nmax = std::max(nmax, S.N);
+    }
+    for (size_t a : arena_of) bK = std::max(bK, a);
     bQ = std::max(bQ, factor_tc_queue_scratch_bytes(nmax) * (size_t)sms);
   }
   w.rcap = std::max(6, std::min(capmax * 2, std::max(6, (int)h->robin_entries.size())));
@@ -1399,13 +1429,26 @@ static int make_chunks(dpg_handle* h, bool real, std::vector<ChunkPlan>& plan, i
   std::vector<Cut> cuts;
   const bool waves = h->bucketed;
   if (waves) {
-    for (int w = 0; w < h->nwaves; ++w)
-      for (int l = 0; l < (int)lists.size(); ++l) {
-        const size_t n = lists[l].elems.size();
-        const int cap = wave_cap(n, h->nwaves);
-        const size_t c0 = (size_t)w * cap;
-        if (c0 < n) cuts.push_back({l, c0, (int)std::min<size_t>(cap, n - c0), w});
-      }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const std::vector<int> lw = list_waves(h, lists, h->chunk_req, sms);
+    int ngroup = 1;
+    for (const ElemList& L : lists) ngroup = std::max(ngroup, L.colour + 1);
+    int wave_id = 0;  // waves numbered across the groups, group by group
+    for (int c = 0; c < ngroup; ++c) {
+      int wg = 0;
+      for (size_t l = 0; l < lists.size(); ++l)
+        if (lists[l].colour == c) wg = std::max(wg, lw[l]);
+      for (int w = 0; w < wg; ++w, ++wave_id)
+        for (int l = 0; l < (int)lists.size(); ++l) {
+          if (lists[l].colour != c) continue;
+          const size_t n = lists[l].elems.size();
+          const int cap = wave_cap(n, lw[l]);
+          const size_t c0 = (size_t)w * cap;
+          if (c0 < n) cuts.push_back({l, c0, (int)std::min<size_t>(cap, n - c0), wave_id});
+        }
+    }
   } else {
     for (int l = 0; l < (int)lists.size(); ++l) {
       const int cap = h->grp[lists[l].g].cap;

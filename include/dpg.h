@@ -96,7 +96,7 @@ enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2
 enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
 enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8, DPG_CG_HALF = 16,
-       DPG_CG_IR_V64 = 32, DPG_CG_DW = 64, DPG_CG_EBE = 128 };
+       DPG_CG_IR_V64 = 32, DPG_CG_DW = 64, DPG_CG_EBE = 128, DPG_CG_RELIABLE = 256 };
 enum { DPG_FLAG_ADJOINT = 1, DPG_FLAG_STREAM = 2 };
 /* Arithmetic of the element factorisation's trailing updates (dpg_set_factor_arith). */
 enum { DPG_FACTOR_FP64 = 0, DPG_FACTOR_TC_SPLIT = 1 };
@@ -231,6 +231,12 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * slots and each row then sums its slots in ascending order (deterministic).
  * The assembled matrix stays for the FP64 residuals and the preconditioner.
  * Errors add DPG_ERR_UNSUPPORTED (streaming, or over 2^31 trace slots).
+ * DPG_CG_RELIABLE may be or-ed to DPG_CG_IR_FP32 (with any inner operator):
+ * reliable updates instead of restarts.  After each inner solve the residual
+ * is replaced by the true FP64 residual b - A x as before, but the next inner
+ * solve continues the previous search direction, p = z + beta p with
+ * beta = r^H z / (r^H z)_previous, instead of starting again from p = z, so
+ * the Krylov information of the earlier inner solves is kept.
  * DPG_CG_X0 may be or-ed too: start from the x passed in (resume a stopped
  * solve, or warm-start from a nearby problem's solution) instead of x0 = 0.
  * x: device, n complex (caller-owned, overwritten).  b: device, n complex, or

@@ -160,7 +160,8 @@ struct CgState {          // device-resident
   unsigned int bar[2];    // grid barrier counter / generation
   unsigned long long wait_ns;  // in: a barrier wait gives up after this long
   int hold;               // in: test hook, no barrier ever releases (every wait runs out)
-  int pad_;
+  int cont;               // in: continue the previous solve's direction p (reliable update)
+  double rz_prev;         // in: r^H z at the end of the previous solve (cont)
 };
 
 constexpr int CG_THREADS = 256;
@@ -786,14 +787,17 @@ __global__ void __launch_bounds__(CG_THREADS, SP == 1 ? 4 : (SP == 2 ? 2 : 5)) k
   unsigned int gen = *((volatile unsigned int*)&st->bar[1]);
   const double tol2 = st->tol2;
   const int max_iter = st->max_iter;
-  // phase 0: z = M^{-1} r, p = z, x = 0
+  // phase 0: z = M^{-1} r, x = 0, and p = z; or, continuing the previous
+  // solve after its residual was replaced by the true one (reliable update),
+  // p = z + beta p with beta = r^H z / (r^H z)_previous
+  const bool cont = st->cont != 0;
   R rr0 = 0, rz0 = 0;
   for (int b = gw; b < S.nblk; b += warps) {
     block_precond<V>(S, b, precond, r, z, dinv, binv, rs, rr0, rz0);
     __syncwarp();
     const int4 B = S.blk[b];
     for (int i = threadIdx.x & 31; i < B.y; i += 32) {
-      p[B.x + i] = z[B.x + i];
+      if (!cont) p[B.x + i] = z[B.x + i];
       x[B.x + i] = mkv(0.0, 0.0, (V*)nullptr);
     }
   }
@@ -801,6 +805,17 @@ __global__ void __launch_bounds__(CG_THREADS, SP == 1 ? 4 : (SP == 2 ? 2 : 5)) k
   if (!grid_barrier(st, gen)) return;
   double rr, rz;
   grid_total(redB0, redB1, rr, rz);
+  if (cont) {
+    const R beta0 = (R)(rz / st->rz_prev);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)G * blockDim.x) {
+      const V zv = z[i];
+      V pv = p[i];
+      pv.x = fma(beta0, pv.x, zv.x);
+      pv.y = fma(beta0, pv.y, zv.y);
+      p[i] = pv;
+    }
+    if (!grid_barrier(st, gen)) return;
+  }
   int it = 0;
   bool done = rr <= tol2;
   while (!done && it < max_iter) {
@@ -1088,7 +1103,8 @@ static int persistent_grid(dpg_handle* h, const void* kernel, size_t smem, int* 
 // One cooperative launch of a persistent CG kernel whose last argument is the
 // CgState; the state is initialised before and read back after the solve.
 static int launch_persistent(dpg_handle* h, const void* kernel, void** args, CgState** st_arg, size_t smem,
-                             double tol2, int max_iter, bool fp32, cudaStream_t s, int* iters, double* rr_out) {
+                             double tol2, int max_iter, bool fp32, cudaStream_t s, int* iters, double* rr_out,
+                             int cont = 0, double rz_prev = 0.0, double* rz_out = nullptr) {
   int grid = 0;
   int rc = persistent_grid(h, kernel, smem, &grid);
   if (rc) return rc;
@@ -1097,6 +1113,8 @@ static int launch_persistent(dpg_handle* h, const void* kernel, void** args, CgS
   host.max_iter = max_iter;
   host.wait_ns = (unsigned long long)h->wait_ns;
   host.hold = h->wait_hold ? 1 : 0;
+  host.cont = cont;
+  host.rz_prev = rz_prev;
   CgState* st = static_cast<CgState*>(h->d_cgstate);
   *st_arg = st;
   DPG_CUDA_TRY(h, cudaMemcpyAsync(st, &host, sizeof(CgState), cudaMemcpyHostToDevice, s));
@@ -1127,6 +1145,7 @@ static int launch_persistent(dpg_handle* h, const void* kernel, void** args, CgS
   }
   *iters = host.iters;
   *rr_out = host.rr;
+  if (rz_out) *rz_out = host.rz;
   return DPG_OK;
 }
 
@@ -1134,7 +1153,8 @@ static int launch_persistent(dpg_handle* h, const void* kernel, void** args, CgS
 template <typename V, typename Mv, int SP>
 static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap, V* z, int precond,
                           const typename RealOf<V>::T* dinv, const V* binv, double tol2, int max_iter,
-                          cudaStream_t s, int* iters, double* rr_out, V* T = nullptr) {
+                          cudaStream_t s, int* iters, double* rr_out, V* T = nullptr, int cont = 0,
+                          double rz_prev = 0.0, double* rz_out = nullptr) {
   size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
   if (SP == 2) smem += (CG_THREADS / 32) * 2 * 32 * (size_t)h->ebe_nbmax * sizeof(float2);  // x_K, y_K per warp
   SysView S = sys_view(h);
@@ -1142,7 +1162,7 @@ static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap,
   CgState* st = nullptr;
   void* args[] = {&S, &val, &x, &r, &p, &Ap, &z, &precond, &dinv, &binv, &red, &st, &T};
   return launch_persistent(h, (const void*)k_cg_persistent<V, Mv, SP>, args, &st, smem, tol2, max_iter,
-                           sizeof(Mv) == sizeof(float2), s, iters, rr_out);
+                           sizeof(Mv) == sizeof(float2), s, iters, rr_out, cont, rz_prev, rz_out);
 }
 
 // The same in the double-word mode (k_cg_dw).
@@ -1400,7 +1420,8 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     return DPG_ERR_ARG;
   }
   if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0 | DPG_CG_HALF | DPG_CG_IR_V64 |
-               DPG_CG_DW | DPG_CG_EBE) ||
+               DPG_CG_DW | DPG_CG_EBE | DPG_CG_RELIABLE) ||
+      ((mode & DPG_CG_RELIABLE) && !(mode & DPG_CG_IR_FP32)) ||
       ((mode & DPG_CG_HALF) && (mode & DPG_CG_IR_V64)) ||
       ((mode & DPG_CG_EBE) && (!(mode & DPG_CG_IR_FP32) || (mode & (DPG_CG_HALF | DPG_CG_IR_V64)))) ||
       ((mode & DPG_CG_DW) && (mode & (DPG_CG_IR_FP32 | DPG_CG_JACOBI))) ||
@@ -1511,9 +1532,14 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
   }
   bool conv = rnorm <= tol;
   const int max_outer = ir ? 100 : 8;
+  // reliable updates: every inner solve after the first continues the previous
+  // one's search direction (p = z + beta p) from the replaced true residual
+  const bool reliable = (mode & DPG_CG_RELIABLE) != 0;
+  double rz_last = 0.0;
   while (!conv && total_iters < max_iter && outer < max_outer) {
     int it = 0;
     double rr = 0;
+    const int cont = (reliable && outer > 0 && rz_last > 0.0) ? 1 : 0;
     if (dw) {
       const double itol = 0.5 * tol;
       rc = run_dw(h, h->d_d64, h->d_r, precond, itol * itol, max_iter - total_iters, s, &it, &rr);
@@ -1523,8 +1549,8 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
       // inner CG over the FP32 matrix (FP32 products) with FP64 vectors and recurrences
       const double itol = std::max(inner_rtol * rnorm, 0.5 * tol);
       rc = run_persistent<double2, float2, 0>(h, h->d_val32, h->d_d64, h->d_r, h->d_p, h->d_Ap, h->d_zv, precond,
-                                                  h->d_dinv, h->d_binv, itol * itol, max_iter - total_iters, s, &it,
-                                                  &rr);
+                                              h->d_dinv, h->d_binv, itol * itol, max_iter - total_iters, s, &it,
+                                              &rr, nullptr, cont, rz_last, &rz_last);
       if (rc) return rc;
       k_add_correction64<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_d64);
     } else if (ir) {
@@ -1534,15 +1560,18 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
       if (half)
         rc = run_persistent<float2, float2, 1>(h, h->d_val32h, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
                                                precond, h->d_dinv32, h->d_binv32, itol * itol,
-                                               max_iter - total_iters, s, &it, &rr, h->d_T);
+                                               max_iter - total_iters, s, &it, &rr, h->d_T, cont, rz_last,
+                                               &rz_last);
       else if (ebe)
         rc = run_persistent<float2, float2, 2>(h, (const float2*)nullptr, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32,
                                                h->d_z32, precond, h->d_dinv32, h->d_binv32, itol * itol,
-                                               max_iter - total_iters, s, &it, &rr);
+                                               max_iter - total_iters, s, &it, &rr, nullptr, cont, rz_last,
+                                               &rz_last);
       else
         rc = run_persistent<float2, float2, 0>(h, h->d_val32, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
                                                precond, h->d_dinv32, h->d_binv32, itol * itol,
-                                               max_iter - total_iters, s, &it, &rr);
+                                               max_iter - total_iters, s, &it, &rr, nullptr, cont, rz_last,
+                                               &rz_last);
       if (rc) return rc;
       k_add_correction<<<1184, 256, 0, s>>>((int64_t)n, x, h->d_x32);
     } else {

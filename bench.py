@@ -34,7 +34,7 @@ UNIT = "elements/s"
 CG_MODES = {"fp64": 0, "ir": 1, "fp64-jacobi": 2, "ir-jacobi": 3, "fp64-bjacobi": 4, "ir-bjacobi": 5,
             "ir-bjacobi-half": 5 | 16, "ir64v-bjacobi": 5 | 32, "ir64v": 1 | 32,
             "dw": 64, "dw-bjacobi": 64 | 4, "ir-ebe": 1 | 128, "ir-bjacobi-ebe": 5 | 128,
-            "ir-bjacobi-rel": 5 | 256, "ir-bjacobi-ebe-rel": 5 | 128 | 256}
+            "ir-bjacobi-rel": 5 | 256, "ir-bjacobi-ebe-rel": 5 | 128 | 256, "ir-bjacobi-ebe-bulk": 5 | 128 | 512}
 PRECISIONS = {"fp64": 0, "tf32": 1, "3xtf32": 2}
 
 

@@ -96,7 +96,7 @@ enum { DPG_DIRICHLET_ZERO = 0, DPG_DIRICHLET_SIN_PI_X2 = 1, DPG_DIRICHLET_TE = 2
 enum { DPG_PREC_FP64 = 0, DPG_PREC_TF32 = 1, DPG_PREC_3XTF32 = 2 };
 enum { DPG_PASS_ASSEMBLE = 0 };
 enum { DPG_CG_FP64 = 0, DPG_CG_IR_FP32 = 1, DPG_CG_JACOBI = 2, DPG_CG_BLOCK_JACOBI = 4, DPG_CG_X0 = 8, DPG_CG_HALF = 16,
-       DPG_CG_IR_V64 = 32, DPG_CG_DW = 64, DPG_CG_EBE = 128, DPG_CG_RELIABLE = 256 };
+       DPG_CG_IR_V64 = 32, DPG_CG_DW = 64, DPG_CG_EBE = 128, DPG_CG_RELIABLE = 256, DPG_CG_EBE_BULK = 512 };
 enum { DPG_FLAG_ADJOINT = 1, DPG_FLAG_STREAM = 2 };
 /* Arithmetic of the element factorisation's trailing updates (dpg_set_factor_arith). */
 enum { DPG_FACTOR_FP64 = 0, DPG_FACTOR_TC_SPLIT = 1 };
@@ -230,6 +230,11 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * as the conjugate transpose); each element's product goes to its trace
  * slots and each row then sums its slots in ascending order (deterministic).
  * The assembled matrix stays for the FP64 residuals and the preconditioner.
+ * DPG_CG_EBE_BULK may be or-ed to DPG_CG_EBE: the tiles are staged through
+ * shared memory by the bulk-copy (TMA) engine, a ring of 8 KB buffers per warp
+ * with one mbarrier each, refilled ahead across element boundaries; the same
+ * products.  Its staging allows one block per SM (the default loads the tiles
+ * into registers, two blocks per SM).
  * Errors add DPG_ERR_UNSUPPORTED (streaming, or over 2^31 trace slots).
  * DPG_CG_RELIABLE may be or-ed to DPG_CG_IR_FP32 (with any inner operator):
  * reliable updates instead of restarts.  After each inner solve the residual

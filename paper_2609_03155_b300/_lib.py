@@ -25,6 +25,7 @@ DPG_CG_IR_V64 = 32
 DPG_CG_DW = 64
 DPG_CG_EBE = 128
 DPG_CG_RELIABLE = 256
+DPG_CG_EBE_BULK = 512
 DPG_FLAG_ADJOINT = 1
 DPG_FLAG_STREAM = 2
 DPG_FACTOR_FP64, DPG_FACTOR_TC_SPLIT = 0, 1

@@ -251,6 +251,7 @@ struct dpg_handle {
   float2* d_ebe_ys = nullptr;       // per slot: the element product
   bool have_ebe_idx = false, have_ebe = false;
   int ebe_nbmax = 1;
+  int ebe_stages = 2;
   int64_t ebe_tiles = 0, ebe_slots = 0, ebe_links = 0;
   bool have_elements = false, have_system = false, have_val32 = false, have_dinv = false;
   double* d_dinv = nullptr;     // inverse diagonal (Jacobi)

@@ -149,6 +149,7 @@ struct SysView {
   const int64_t* ebe_rptr;    // per row: first entry of its slot list (n + 1)
   const int32_t* ebe_ridx;    // slot lists, ascending
   float2* ebe_ys;             // per slot: the element product
+  int ebe_stages;             // staging buffers per warp of the bulk-copy variant
 };
 
 struct CgState {          // device-resident
@@ -708,10 +709,50 @@ __global__ void k_to_dw(int64_t n, const double2* __restrict__ a, float4* b) {
 // reduction (5 exchange steps, 31 shuffles per component) that leaves row l's
 // sum in lane l.  Every sum has one fixed order.  xs, ya: this warp's shared
 // staging of x_K and y_K (nbmax x 32 entries each).  y_K goes to the slots.
-__device__ __forceinline__ void ebe_element(const SysView& S, int e, const float2* __restrict__ p, float2* xs,
-                                            float2* ya) {
+// One tile (I, J) of an element's product: t points at its 32 x 32 values
+// (global or shared memory), xs at the element's x_K, ya at its y_K.
+__device__ __forceinline__ void ebe_tile(const float2* __restrict__ t, int I, int J, const float2* xs, float2* ya) {
   const int lane = threadIdx.x & 31;
-  const int64_t h0 = S.ebe_hoff[e];
+  const float2 xj = xs[J * 32 + lane];
+  float pr[32], pi[32];
+  float cr = 0.0f, ci = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const float2 a = t[i * 32 + lane];
+    const float2 xi = xs[I * 32 + i];
+    cr = fmaf(a.x, xi.x, fmaf(a.y, xi.y, cr));   // conj(a) x_i
+    ci = fmaf(a.x, xi.y, fmaf(-a.y, xi.x, ci));
+    pr[i] = fmaf(a.x, xj.x, -a.y * xj.y);         // a x_j
+    pi[i] = fmaf(a.x, xj.y, a.y * xj.x);
+  }
+#pragma unroll
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    const bool up = (lane & sh) != 0;
+#pragma unroll
+    for (int k = 0; k < sh; ++k) {
+      const float sr = up ? pr[k] : pr[k + sh], si = up ? pi[k] : pi[k + sh];
+      const float kr = up ? pr[k + sh] : pr[k], ki = up ? pi[k + sh] : pi[k];
+      pr[k] = kr + __shfl_xor_sync(0xffffffffu, sr, sh);
+      pi[k] = ki + __shfl_xor_sync(0xffffffffu, si, sh);
+    }
+  }
+  float2 yr = ya[I * 32 + lane];
+  yr.x += pr[0];
+  yr.y += pi[0];
+  ya[I * 32 + lane] = yr;
+  if (J > I) {
+    float2 yc = ya[J * 32 + lane];
+    yc.x += cr;
+    yc.y += ci;
+    ya[J * 32 + lane] = yc;
+  }
+}
+
+// x_K of element e into xs (zero past n_h and on fixed unknowns), y_K = 0.
+__device__ __forceinline__ int ebe_begin(const SysView& S, int e, const float2* __restrict__ p, float2* xs,
+                                         float2* ya, int64_t& h0) {
+  const int lane = threadIdx.x & 31;
+  h0 = S.ebe_hoff[e];
   const int nh = (int)(S.ebe_hoff[e + 1] - h0);
   const int nb = (nh + 31) >> 5;
   for (int i = lane; i < nb * 32; i += 32) {
@@ -724,53 +765,105 @@ __device__ __forceinline__ void ebe_element(const SysView& S, int e, const float
     ya[i] = make_float2(0.0f, 0.0f);
   }
   __syncwarp();
+  return nh;
+}
+
+__device__ __forceinline__ void ebe_end(const SysView& S, int64_t h0, int nh, const float2* ya) {
+  __syncwarp();
+  for (int i = threadIdx.x & 31; i < nh; i += 32) S.ebe_ys[h0 + i] = ya[i];
+  __syncwarp();
+}
+
+__device__ __forceinline__ void ebe_element(const SysView& S, int e, const float2* __restrict__ p, float2* xs,
+                                            float2* ya) {
+  int64_t h0;
+  const int nh = ebe_begin(S, e, p, xs, ya, h0);
+  const int nb = (nh + 31) >> 5;
   const float2* t = S.ebe + S.ebe_toff[e];
-  for (int I = 0; I < nb; ++I) {
-    for (int J = I; J < nb; ++J, t += 1024) {
-      const float2 xj = xs[J * 32 + lane];
-      float pr[32], pi[32];
-      float cr = 0.0f, ci = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float2 a = t[i * 32 + lane];
-        const float2 xi = xs[I * 32 + i];
-        cr = fmaf(a.x, xi.x, fmaf(a.y, xi.y, cr));   // conj(a) x_i
-        ci = fmaf(a.x, xi.y, fmaf(-a.y, xi.x, ci));
-        pr[i] = fmaf(a.x, xj.x, -a.y * xj.y);         // a x_j
-        pi[i] = fmaf(a.x, xj.y, a.y * xj.x);
-      }
-#pragma unroll
-      for (int sh = 16; sh >= 1; sh >>= 1) {
-        const bool up = (lane & sh) != 0;
-#pragma unroll
-        for (int k = 0; k < sh; ++k) {
-          const float sr = up ? pr[k] : pr[k + sh], si = up ? pi[k] : pi[k + sh];
-          const float kr = up ? pr[k + sh] : pr[k], ki = up ? pi[k + sh] : pi[k];
-          pr[k] = kr + __shfl_xor_sync(0xffffffffu, sr, sh);
-          pi[k] = ki + __shfl_xor_sync(0xffffffffu, si, sh);
-        }
-      }
-      float2 yr = ya[I * 32 + lane];
-      yr.x += pr[0];
-      yr.y += pi[0];
-      ya[I * 32 + lane] = yr;
-      if (J > I) {
-        float2 yc = ya[J * 32 + lane];
-        yc.x += cr;
-        yc.y += ci;
-        ya[J * 32 + lane] = yc;
+  for (int I = 0; I < nb; ++I)
+    for (int J = I; J < nb; ++J, t += 1024) ebe_tile(t, I, J, xs, ya);
+  ebe_end(S, h0, nh, ya);
+}
+
+__device__ __forceinline__ uint32_t cg_smem_u32(const void* q) { return (uint32_t)__cvta_generic_to_shared(q); }
+
+// Bounded wait on an mbarrier phase (false: the limit ran out).
+__device__ __forceinline__ bool cg_mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+    if (done) return true;
+    if (global_ns() - t0 > limit) return false;
+  }
+}
+
+// The element products of this warp's elements (e = gw, gw + warps, ...) with
+// the tiles staged through shared memory by the bulk-copy engine: a ring of
+// `stages` 8 KB buffers, one mbarrier each; lane 0 keeps up to `stages` tile
+// copies in flight, across element boundaries, and refills a buffer once the
+// warp has consumed it.  tiles_done: tiles this warp consumed so far in the
+// launch (it fixes every buffer's mbarrier parity).
+__device__ __forceinline__ void ebe_pass_bulk(const SysView& S, const float2* __restrict__ p, float2* xs, float2* ya,
+                                              float2* ring, uint64_t* mbar, int gw, int warps, uint32_t& tiles_done,
+                                              CgState* st) {
+  const int lane = threadIdx.x & 31;
+  const int nst = S.ebe_stages;
+  int pe = gw, pk = 0;
+  uint32_t pn = tiles_done, cn = tiles_done;
+  auto ntiles = [&](int e) {
+    const int nb = (int)((S.ebe_hoff[e + 1] - S.ebe_hoff[e] + 31) >> 5);
+    return nb * (nb + 1) / 2;
+  };
+  auto produce = [&]() {
+    if (lane != 0) return;
+    while (pn < cn + (uint32_t)nst && pe < S.ne) {
+      const int stg = (int)(pn % (uint32_t)nst);
+      const uint32_t mb = cg_smem_u32(mbar + stg);
+      const float2* src = S.ebe + S.ebe_toff[pe] + (int64_t)pk * 1024;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(8192) : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       cg_smem_u32(ring + (size_t)stg * 1024)),
+                   "l"(src), "r"(8192), "r"(mb)
+                   : "memory");
+      ++pn;
+      if (++pk == ntiles(pe)) {
+        pk = 0;
+        pe += warps;
       }
     }
+  };
+  produce();
+  for (int e = gw; e < S.ne; e += warps) {
+    int64_t h0;
+    const int nh = ebe_begin(S, e, p, xs, ya, h0);
+    const int nb = (nh + 31) >> 5;
+    for (int I = 0; I < nb; ++I)
+      for (int J = I; J < nb; ++J) {
+        const int stg = (int)(cn % (uint32_t)nst);
+        if (!cg_mbar_wait(cg_smem_u32(mbar + stg), (cn / (uint32_t)nst) & 1u, st->wait_ns) && lane == 0)
+          atomicExch(&st->status, 1);
+        ebe_tile(ring + (size_t)stg * 1024, I, J, xs, ya);
+        __syncwarp();
+        // the buffer's generic-proxy reads come before the next bulk copy into it
+        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ++cn;
+        produce();
+      }
+    ebe_end(S, h0, nh, ya);
   }
-  __syncwarp();
-  for (int i = lane; i < nh; i += 32) S.ebe_ys[h0 + i] = ya[i];
-  __syncwarp();
+  tiles_done = cn;
 }
 
 // SP: the SpMV of the inner solve: 0 rows of the CSR, 1 Hermitian half
 // storage, 2 element by element.
 template <typename V, typename Mv, int SP>
-__global__ void __launch_bounds__(CG_THREADS, SP == 1 ? 4 : (SP == 2 ? 2 : 5)) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
+__global__ void __launch_bounds__(CG_THREADS, SP == 1 ? 4 : (SP == 2 ? 2 : (SP == 3 ? 1 : 5))) k_cg_persistent(SysView S, const Mv* __restrict__ val, V* x, V* r, V* p,
                                                              V* Ap, V* z, int precond,
                                                              const typename RealOf<V>::T* __restrict__ dinv,
                                                              const V* __restrict__ binv, double* red, CgState* st,
@@ -787,6 +880,18 @@ __global__ void __launch_bounds__(CG_THREADS, SP == 1 ? 4 : (SP == 2 ? 2 : 5)) k
   unsigned int gen = *((volatile unsigned int*)&st->bar[1]);
   const double tol2 = st->tol2;
   const int max_iter = st->max_iter;
+  // bulk-copy staging of the element tiles (SP = 3): per warp up to four
+  // mbarriers, one per staging buffer, and the count of tiles it consumed
+  __shared__ __align__(8) uint64_t ebe_mbar[(CG_THREADS / 32) * 4];
+  uint32_t ebe_tiles_done = 0;
+  if constexpr (SP == 3) {
+    if ((threadIdx.x & 31) == 0) {
+      for (int k = 0; k < S.ebe_stages; ++k)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cg_smem_u32(ebe_mbar + (threadIdx.x >> 5) * 4 + k)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+  }
   // phase 0: z = M^{-1} r, x = 0, and p = z; or, continuing the previous
   // solve after its residual was replaced by the true one (reliable update),
   // p = z + beta p with beta = r^H z / (r^H z)_previous
@@ -821,12 +926,20 @@ __global__ void __launch_bounds__(CG_THREADS, SP == 1 ? 4 : (SP == 2 ? 2 : 5)) k
   while (!done && it < max_iter) {
     // A: Ap = A p and Re(p^H A p)
     R pap = 0;
-    if constexpr (SP == 2) {
+    if constexpr (SP == 2 || SP == 3) {
       // element products into the slots, then each row the sum of its slots
       float2* xs = reinterpret_cast<float2*>(cg_smem + (CG_THREADS / 32) * (size_t)S.dmax * sizeof(V)) +
                    (size_t)(threadIdx.x >> 5) * 2 * 32 * S.ebe_nbmax;
       float2* ya = xs + 32 * S.ebe_nbmax;
-      for (int e = gw; e < S.ne; e += warps) ebe_element(S, e, reinterpret_cast<const float2*>(p), xs, ya);
+      if constexpr (SP == 3) {
+        const size_t base = ((CG_THREADS / 32) * (size_t)S.dmax * sizeof(V) +
+                             (CG_THREADS / 32) * 2 * 32 * (size_t)S.ebe_nbmax * sizeof(float2) + 127) / 128 * 128;
+        float2* ring = reinterpret_cast<float2*>(cg_smem + base) + (size_t)(threadIdx.x >> 5) * S.ebe_stages * 1024;
+        ebe_pass_bulk(S, reinterpret_cast<const float2*>(p), xs, ya, ring, ebe_mbar + (threadIdx.x >> 5) * 4, gw,
+                      warps, ebe_tiles_done, st);
+      } else {
+        for (int e = gw; e < S.ne; e += warps) ebe_element(S, e, reinterpret_cast<const float2*>(p), xs, ya);
+      }
       if (!grid_barrier(st, gen)) return;
       for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < S.n; row += (int64_t)G * blockDim.x) {
         float yr = 0.0f, yi = 0.0f;
@@ -1070,6 +1183,7 @@ static SysView sys_view(dpg_handle* h) {
   v.ebe_rptr = h->d_ebe_rptr;
   v.ebe_ridx = h->d_ebe_ridx;
   v.ebe_ys = h->d_ebe_ys;
+  v.ebe_stages = h->ebe_stages;
   return v;
 }
 
@@ -1156,7 +1270,8 @@ static int run_persistent(dpg_handle* h, const Mv* val, V* x, V* r, V* p, V* Ap,
                           cudaStream_t s, int* iters, double* rr_out, V* T = nullptr, int cont = 0,
                           double rz_prev = 0.0, double* rz_out = nullptr) {
   size_t smem = (CG_THREADS / 32) * (size_t)std::max(1, h->blk_dmax) * sizeof(V);
-  if (SP == 2) smem += (CG_THREADS / 32) * 2 * 32 * (size_t)h->ebe_nbmax * sizeof(float2);  // x_K, y_K per warp
+  if (SP == 2 || SP == 3) smem += (CG_THREADS / 32) * 2 * 32 * (size_t)h->ebe_nbmax * sizeof(float2);  // x_K, y_K
+  if (SP == 3) smem = (smem + 127) / 128 * 128 + (CG_THREADS / 32) * (size_t)h->ebe_stages * 8192;  // tile staging
   SysView S = sys_view(h);
   double* red = h->d_red;
   CgState* st = nullptr;
@@ -1289,6 +1404,13 @@ static int build_ebe_index(dpg_handle* h) {
   DPG_CUDA_TRY(h, cudaMemcpy(h->d_ebe_rptr, rptr.data(), sizeof(int64_t) * rptr.size(), cudaMemcpyHostToDevice));
   DPG_CUDA_TRY(h, cudaMemcpy(h->d_ebe_ridx, ridx.data(), sizeof(int32_t) * ridx.size(), cudaMemcpyHostToDevice));
   h->ebe_nbmax = nbmax;
+  // staging buffers per warp of the bulk-copy variant: three, or two when the
+  // x_K / y_K staging of the largest element leaves no room for three
+  {
+    const size_t fixed = (CG_THREADS / 32) * ((size_t)std::max(1, h->blk_dmax) * sizeof(float2) +
+                                              2 * 32 * (size_t)nbmax * sizeof(float2)) + 128;
+    h->ebe_stages = fixed + (CG_THREADS / 32) * 3 * 8192 <= 227 * 1024 ? 3 : 2;
+  }
   h->ebe_tiles = toff[ne];
   h->ebe_slots = slots;
   h->ebe_links = rptr[h->n];
@@ -1420,7 +1542,8 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
     return DPG_ERR_ARG;
   }
   if (mode & ~(DPG_CG_IR_FP32 | DPG_CG_JACOBI | DPG_CG_BLOCK_JACOBI | DPG_CG_X0 | DPG_CG_HALF | DPG_CG_IR_V64 |
-               DPG_CG_DW | DPG_CG_EBE | DPG_CG_RELIABLE) ||
+               DPG_CG_DW | DPG_CG_EBE | DPG_CG_RELIABLE | DPG_CG_EBE_BULK) ||
+      ((mode & DPG_CG_EBE_BULK) && !(mode & DPG_CG_EBE)) ||
       ((mode & DPG_CG_RELIABLE) && !(mode & DPG_CG_IR_FP32)) ||
       ((mode & DPG_CG_HALF) && (mode & DPG_CG_IR_V64)) ||
       ((mode & DPG_CG_EBE) && (!(mode & DPG_CG_IR_FP32) || (mode & (DPG_CG_HALF | DPG_CG_IR_V64)))) ||
@@ -1561,6 +1684,11 @@ int cg_solve(dpg_handle* h, int mode, double rtol, double atol, int max_iter, do
         rc = run_persistent<float2, float2, 1>(h, h->d_val32h, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_z32,
                                                precond, h->d_dinv32, h->d_binv32, itol * itol,
                                                max_iter - total_iters, s, &it, &rr, h->d_T, cont, rz_last,
+                                               &rz_last);
+      else if (ebe && (mode & DPG_CG_EBE_BULK))
+        rc = run_persistent<float2, float2, 3>(h, (const float2*)nullptr, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32,
+                                               h->d_z32, precond, h->d_dinv32, h->d_binv32, itol * itol,
+                                               max_iter - total_iters, s, &it, &rr, nullptr, cont, rz_last,
                                                &rz_last);
       else if (ebe)
         rc = run_persistent<float2, float2, 2>(h, (const float2*)nullptr, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32,

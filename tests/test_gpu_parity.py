@@ -183,8 +183,8 @@ def test_te10_waveguide_field_error(dpg_mod):
     d.destroy()
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 1 | 16, 5 | 16, 5 | 32, 64, 64 | 4, 1 | 128, 5 | 128, 5 | 256,
-                                  5 | 128 | 256, 5 | 32 | 256])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 1 | 16, 5 | 16, 5 | 32, 64, 64 | 4, 1 | 128, 5 | 128, 5 | 128 | 512,
+                                  5 | 256, 5 | 128 | 256, 5 | 32 | 256])
 def test_cg_modes_match_fp64(dpg_mod, mode):
     """IR (FP32 inner: full or Hermitian half storage or element by element, FP32 or FP64 inner vectors),
     Jacobi, entity-block Jacobi and the double-word (FP32 pair) solver reach the plain FP64 CG solution."""

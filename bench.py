@@ -347,6 +347,8 @@ def main():
     d = dpg.DPG(mesh, precision=PRECISIONS[args.precision], chunk=args.chunk, adjoint=args.adjoint,
                 streaming=streaming)
     mode = CG_MODES[args.cg]
+    if not streaming:  # eta_K from the X = (L^-1 [B Bh l])^H the element pass keeps
+        d.set_estimator_store(True)
     if args.bucketed:
         d.set_bucketed(True)
     tuned = d.autotune() if args.autotune else None
@@ -563,6 +565,8 @@ def main():
                    "quadrature": args.precision,
                    "chunks": {str(g[0]): g[2] for g in d.group_info()} if d.h else None,
                    "autotuned": tuned is not None, "streaming": streaming, "bucketed": args.bucketed,
+                   "estimator": ("L^-1 r_K from the stored L^-1 [B Bh l]" if not streaming
+                                 else "L^-1 r_K by a second (recondensing) element pass"),
                    "trace_unknowns": int(d.n), "nnz": int(d.nnz), "cg": args.cg, "cg_rtol": args.rtol,
                    "cg_inner_rtol": args.inner_rtol,
                    "parallelism": f"replicas x{world}",

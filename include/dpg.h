@@ -379,6 +379,18 @@ int dpg_grad_eps(dpg_handle* h, const dpg_complex* xhat, const uint8_t* obstacle
  * Errors: DPG_ERR_ARG (unknown mode), DPG_ERR_NOMEM. */
 int dpg_set_factor_arith(dpg_handle* h, int32_t arith);
 
+/* Stored-factor estimator (Sec. 2.3: eta_K = ||Psi_K||_V = ||L^{-1} r_K||).
+ * enable = 1: every element pass keeps, per element, X = (L^{-1} [B | B-hat |
+ * l])^H, which its factorisation leaves below G's factor (n_v x (m + 1)
+ * values, m = n_u + n_h; real on the real path: 1.8 MB per p = 2 element), and
+ * dpg_estimate / dpg_estimate_noalloc form L^{-1} r_K = L^{-1} l - (L^{-1} B) u
+ * - (L^{-1} B-hat) uhat_K from it directly, instead of a second element pass
+ * that forms K and factors G again.  Same definition, different order of the
+ * same exact operations.  The next dpg_element_batch writes X (until then the
+ * estimator keeps the second pass).  enable = 0 frees it.  Not with
+ * DPG_FLAG_STREAM.  Errors: DPG_ERR_ARG, DPG_ERR_NOMEM, DPG_ERR_UNSUPPORTED. */
+int dpg_set_estimator_store(dpg_handle* h, int32_t enable);
+
 /* Order-bucketed element pass (Sec. 4: p-adaptive and AMR meshes mix trial
  * orders, so element work is uneven).  enable = 1: the pass runs in waves; a
  * wave forms one chunk of every (order, arithmetic) list, each into its own

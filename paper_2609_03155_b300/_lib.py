@@ -105,6 +105,7 @@ def lib():
     L.dpg_set_wait_limit.argtypes = [vp, i64, i32]
     L.dpg_set_factor_arith.argtypes = [vp, i32]
     L.dpg_set_bucketed.argtypes = [vp, i32]
+    L.dpg_set_estimator_store.argtypes = [vp, i32]
     L.dpg_factor_balance.argtypes = [vp, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(i64)]
     L.dpg_estimate_clamped.argtypes = [vp, C.POINTER(i32)]
     L.dpg_mark_fraction.argtypes = [vp, vp, dbl, dbl, i32, vp, vp]
@@ -131,7 +132,7 @@ def lib():
                  "dpg_update_elements", "dpg_timing_enable", "dpg_timing_get", "dpg_grad_eps",
                  "dpg_set_real_path", "dpg_cg_bytes_per_iteration", "dpg_element_layout", "dpg_tc_gemm", "dpg_set_graph", "dpg_autotune", "dpg_power",
                  "dpg_set_wait_limit", "dpg_set_factor_arith", "dpg_factor_check", "dpg_estimate_clamped", "dpg_mark_fraction",
-                 "dpg_group_info", "dpg_set_bucketed", "dpg_factor_balance"):
+                 "dpg_group_info", "dpg_set_bucketed", "dpg_factor_balance", "dpg_set_estimator_store"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -42,7 +42,7 @@ static void free_all(dpg_handle* h) {
                   h->d_zv, h->d_z32, h->d_d64, h->ws.Q, h->d_est_neg,
                   h->d_rowptr_h, h->d_toff, h->d_rev_ptr, h->d_rev_off, h->d_val32h, h->d_T,
                   h->d_valdw, h->d_pdw, h->d_binvdw, h->d_ebe, h->d_ebe_toff, h->d_ebe_hoff, h->d_ebe_rptr,
-                  h->d_ebe_ridx, h->d_ebe_ys};
+                  h->d_ebe_ridx, h->d_ebe_ys, h->d_Xst, h->d_xst_off};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->d_soff && h->d_soff != h->d_off) cudaFree(h->d_soff);
@@ -131,6 +131,7 @@ extern "C" int dpg_element_batch(dpg_handle* h, int32_t pass, dpg_stream st) {
   }
   // only a pass whose every pivot was positive feeds assembly and estimation
   h->have_elements = true;
+  h->xst_valid = h->d_Xst != nullptr && !h->stream;
   if (h->stream) system_changed(h);  // assembled during the pass
   return DPG_OK;
 }
@@ -516,15 +517,59 @@ extern "C" int dpg_cg_bytes_per_iteration(dpg_handle* h, int32_t mode, int64_t* 
   return DPG_OK;
 }
 
+extern "C" int dpg_set_estimator_store(dpg_handle* h, int32_t enable);
+
 extern "C" int dpg_set_real_path(dpg_handle* h, int32_t enable) {
   if (!h) return DPG_ERR_ARG;
   if (h->allow_real == (enable != 0)) return DPG_OK;
   h->plan_valid = false;
   h->allow_real = enable != 0;
+  if (h->d_Xst) {  // X is sized by each element's arithmetic
+    dpg_set_estimator_store(h, 0);
+    const int rc = dpg_set_estimator_store(h, 1);
+    if (rc) return rc;
+  }
   if (h->bucketed) {  // the waves' lists change with the arithmetic split
     set_default_caps(h, h->chunk_req);
     return alloc_workspace(h);
   }
+  return DPG_OK;
+}
+
+extern "C" int dpg_set_estimator_store(dpg_handle* h, int32_t enable) {
+  if (!h) return DPG_ERR_ARG;
+  if ((h->d_Xst != nullptr) == (enable != 0)) return DPG_OK;
+  h->xst_valid = false;
+  h->graph_valid = false;  // the element pass gains or loses its X extraction
+  if (!enable) {
+    cudaFree(h->d_Xst);
+    cudaFree(h->d_xst_off);
+    h->d_Xst = nullptr;
+    h->d_xst_off = nullptr;
+    return DPG_OK;
+  }
+  if (h->stream) {
+    h->err = "streaming keeps no per-element data; the estimator condenses each chunk again";
+    return DPG_ERR_UNSUPPORTED;
+  }
+  std::vector<int64_t> xoff(h->ne + 1, 0);
+  for (int e = 0; e < h->ne; ++e) {
+    const Sizes& S = h->grp[h->elem_grp[e]].sz;
+    const int64_t vals = (int64_t)S.n_v * (S.N - S.n_v);
+    xoff[e + 1] = xoff[e] + ((h->allow_real && h->is_real[e]) ? vals : 2 * vals);
+  }
+  if (cudaMalloc(&h->d_Xst, sizeof(double) * std::max<int64_t>(1, xoff[h->ne])) != cudaSuccess ||
+      cudaMalloc(&h->d_xst_off, sizeof(int64_t) * (h->ne + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->d_Xst);
+    h->d_Xst = nullptr;
+    h->d_xst_off = nullptr;
+    h->err = "allocation of the stored-factor estimator data (" + std::to_string(8 * xoff[h->ne]) +
+             " bytes) failed";
+    return DPG_ERR_NOMEM;
+  }
+  DPG_CUDA_TRY(h, cudaMemcpy(h->d_xst_off, xoff.data(), sizeof(int64_t) * xoff.size(), cudaMemcpyHostToDevice));
+  h->have_elements = false;  // the next element pass writes X
   return DPG_OK;
 }
 

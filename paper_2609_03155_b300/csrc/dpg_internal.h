@@ -251,6 +251,12 @@ struct dpg_handle {
   float2* d_ebe_ys = nullptr;       // per slot: the element product
   bool have_ebe_idx = false, have_ebe = false;
   int ebe_nbmax = 1;
+  // stored-factor estimator (dpg_set_estimator_store): per element
+  // X = (L^{-1} [B | B-hat | l])^H, n_v columns of m + 1 entries (doubles on the
+  // real path, complex pairs otherwise), written by every element pass
+  double* d_Xst = nullptr;
+  int64_t* d_xst_off = nullptr;  // per element: offset in doubles
+  bool xst_valid = false;        // X describes the current elements
   int ebe_stages = 2;
   int64_t ebe_tiles = 0, ebe_slots = 0, ebe_links = 0;
   bool have_elements = false, have_system = false, have_val32 = false, have_dinv = false;

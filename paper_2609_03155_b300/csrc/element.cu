@@ -1264,6 +1264,21 @@ static int run_robin(dpg_handle* h, int g, const int* ids_host, int count, cudaS
 
 // quad = false reuses the quadrature matrices already in the workspace (the
 // same chunk was formed just before) and only forms K again.
+// The stored X of a chunk's elements after their factorisation (see
+// k_est_stored): column i of rows n_v..N-1 of K, contiguous in K.
+template <typename T>
+__global__ void __launch_bounds__(256) k_extract_x(Sizes S, const int* __restrict__ ids, const T* __restrict__ K,
+                                                   const int64_t* __restrict__ xoff, double* Xst) {
+  const int slot = blockIdx.x, e = ids[slot];
+  const int N = S.N, nv = S.n_v, m1 = N - nv;
+  const T* A = K + (size_t)slot * N * N;
+  T* dst = reinterpret_cast<T*>(Xst + xoff[e]);
+  for (int64_t q = threadIdx.x; q < (int64_t)nv * m1; q += blockDim.x) {
+    const int i = (int)(q / m1), t = (int)(q - (int64_t)i * m1);
+    dst[q] = A[(size_t)nv + t + (size_t)i * N];
+  }
+}
+
 int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cudaStream_t s, bool factor,
                       bool extract, bool real, const ChunkPlan* cp, bool quad, bool build, void* Kc) {
   Workspace& w = h->ws;
@@ -1356,6 +1371,14 @@ int run_element_chunk(dpg_handle* h, int g, const int* ids_host, int count, cuda
     if (timed) DPG_CUDA_TRY(h, cudaEventRecordWithFlags(cp->ev1, s, rec_flags));
   }
   if (extract) {
+    if (h->d_Xst && !h->stream) {  // X = (L^{-1} [B | B-hat | l])^H for the stored-factor estimator
+      if (real)
+        k_extract_x<double><<<count, 256, 0, s>>>(S, ids, Kr, h->d_xst_off, h->d_Xst);
+      else
+        k_extract_x<double2><<<count, 256, 0, s>>>(S, ids, Kw, h->d_xst_off, h->d_Xst);
+      DPG_CUDA_TRY(h, cudaGetLastError());
+      h->launches += 1;
+    }
     if (real)
       k_extract_real<<<count, 256, 0, s>>>(S, ids, Kr, h->d_soff, h->d_S, h->d_s, h->d_c, h->d_Z, h->d_z, h->d_L1,
                                            w.V);
@@ -1837,6 +1860,130 @@ __global__ void __launch_bounds__(256) k_recover_u(int nh, int nu, const int* __
   }
 }
 
+// The residual's unknowns of element e into w (m = n_u + n_h entries): u
+// recovered from the stored Z, z and the trace solution, then the element's
+// own trace coefficients uhat_K = R_K uhat_slots; with `phased` (the real
+// path's w_r = D_w^H w) the E and E-hat entries are multiplied by i.  us:
+// shared scratch of n_h entries; u_out (may be NULL) receives u.
+__device__ __forceinline__ void est_w(const Sizes& S, int e, const ElemOff& of, const ElemOff* __restrict__ soff,
+                                      const int* __restrict__ sig, const RSig* __restrict__ rsig,
+                                      const int32_t* __restrict__ rint, const double* __restrict__ rdbl,
+                                      const int32_t* __restrict__ l2g, const double2* __restrict__ xfix,
+                                      const double2* __restrict__ xhat, const double2* __restrict__ Zst,
+                                      const double2* __restrict__ zst, double2* w, double2* us, double2* u_out,
+                                      bool phased) {
+  const int nu = S.n_u, nh = S.n_h, nE = 3 * S.nL, nt = S.nt;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) us[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
+  __syncthreads();
+  const double2* Ze = Zst + soff[e].Z;
+  for (int i = wid; i < nu; i += nw) {
+    double yr = 0.0, yi = 0.0;
+    for (int j = lane; j < nh; j += 32) {
+      const double2 v = Ze[(size_t)i * nh + j], x = us[j];
+      yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
+      yi = fma(v.x, x.y, fma(v.y, x.x, yi));
+    }
+    yr = est_wsum(yr);
+    yi = est_wsum(yi);
+    if (lane == 0) {
+      const double2 zi = zst[soff[e].u + i];
+      const double2 ui = make_double2(zi.x - yr, zi.y - yi);
+      if (u_out) u_out[of.u + i] = ui;
+      w[i] = (phased && i < nE) ? make_double2(-ui.y, ui.x) : ui;  // times conj(-i) = i on E
+    }
+  }
+  const int sg = sig[e];
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) {
+    double2 a;
+    if (sg >= 0) {  // uhat_K = R uhat (slots)
+      const RSig R = rsig[sg];
+      const int32_t* rp = rint + R.rptr;
+      const int32_t* ri = rint + R.ridx;
+      const double* rw = rdbl + R.rw;
+      const int tt = t < nt ? t : t - nt, base = t < nt ? 0 : nt;
+      a = make_double2(0.0, 0.0);
+      for (int k = rp[tt]; k < rp[tt + 1]; ++k) {
+        const double2 x = us[base + ri[k]];
+        a.x = fma(rw[k], x.x, a.x);
+        a.y = fma(rw[k], x.y, a.y);
+      }
+    } else {
+      a = us[t];
+    }
+    w[nu + t] = (phased && t < nt) ? make_double2(-a.y, a.x) : a;  // times i on E-hat
+  }
+  __syncthreads();
+}
+
+// eta_K^2 of the stored-factor estimator: the element pass leaves
+// X = (L^{-1} [B | B-hat | l])^H below G's factor (columns 0..n_v-1 of rows
+// n_v..N-1; the later pivots never touch them), kept per element column by
+// column (n_v columns of m + 1 entries).  L^{-1} r = L^{-1} l - L^{-1} B u -
+// L^{-1} B-hat uhat_K: y_i = conj(X[m][i]) - sum_t conj(X[t][i]) w_t, and
+// eta_K^2 = ||y||^2 (Sec. 2.3).  Real path: X_r real, no load, w phased,
+// y_r = -X_r^T w_r (real and imaginary parts).  One block per element.
+template <bool REAL>
+__global__ void __launch_bounds__(256) k_est_stored(Sizes S, const int* __restrict__ ids, const ElemOff* __restrict__ off,
+                                                    const ElemOff* __restrict__ soff, const int* __restrict__ sig,
+                                                    const RSig* __restrict__ rsig, const int32_t* __restrict__ rint,
+                                                    const double* __restrict__ rdbl, const int32_t* __restrict__ l2g,
+                                                    const double2* __restrict__ xfix,
+                                                    const double2* __restrict__ xhat,
+                                                    const double2* __restrict__ Zst,
+                                                    const double2* __restrict__ zst, const double* __restrict__ Xst,
+                                                    const int64_t* __restrict__ xoff, double2* u_out, double* eta2) {
+  extern __shared__ double2 es_sh[];
+  const int e = ids[blockIdx.x];
+  const ElemOff of = off[e];
+  const int nv = S.n_v, m = S.n_u + S.n_h;
+  double2* w = es_sh;       // m
+  double2* us = w + m;      // nh
+  __shared__ double part[256 / 32];
+  est_w(S, e, of, soff, sig, rsig, rint, rdbl, l2g, xfix, xhat, Zst, zst, w, us, u_out, REAL);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double acc = 0.0;  // sum of |y_i|^2 over this warp's rows i
+  if (REAL) {
+    const double* X = Xst + xoff[e];
+    for (int i = wid; i < nv; i += nw) {
+      const double* col = X + (size_t)i * (m + 1);
+      double yr = 0.0, yi = 0.0;
+      for (int t = lane; t < m; t += 32) {
+        const double b = col[t];
+        const double2 x = w[t];
+        yr = fma(b, x.x, yr);
+        yi = fma(b, x.y, yi);
+      }
+      yr = est_wsum(yr);
+      yi = est_wsum(yi);
+      acc += yr * yr + yi * yi;
+    }
+  } else {
+    const double2* X = reinterpret_cast<const double2*>(Xst + xoff[e]);
+    for (int i = wid; i < nv; i += nw) {
+      const double2* col = X + (size_t)i * (m + 1);
+      double yr = 0.0, yi = 0.0;
+      for (int t = lane; t < m; t += 32) {
+        const double2 b = col[t], x = w[t];  // conj(b) x
+        yr = fma(b.x, x.x, fma(b.y, x.y, yr));
+        yi = fma(b.x, x.y, fma(-b.y, x.x, yi));
+      }
+      yr = est_wsum(yr);
+      yi = est_wsum(yi);
+      const double2 l = col[m];  // conj(L^{-1} l)_i
+      const double dr = l.x - yr, di = -l.y - yi;
+      acc += dr * dr + di * di;
+    }
+  }
+  if (lane == 0) part[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += part[k];
+    eta2[e] = t;
+  }
+}
+
 // Per element of a chunk (K freshly formed, not factored): u, the element's
 // own trace coefficients uhat_K = R_K uhat_slots, r = l - B u - B-hat uhat_K
 // (B[i][j] = conj(K[n_v + j][i]), l_i = conj(K[N-1][i])); K[n_v][i] = conj(r_i),
@@ -1858,46 +2005,7 @@ __global__ void __launch_bounds__(256) k_est_residual(Sizes S, const int* __rest
   double2* us = w + m;      // nh: uhat in the trace slots
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double2* A = K + (size_t)slot * N * N;
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) us[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
-  __syncthreads();
-  const double2* Ze = Zst + soff[e].Z;
-  for (int i = wid; i < nu; i += nw) {
-    double yr = 0.0, yi = 0.0;
-    for (int j = lane; j < nh; j += 32) {
-      const double2 v = Ze[(size_t)i * nh + j], x = us[j];
-      yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
-      yi = fma(v.x, x.y, fma(v.y, x.x, yi));
-    }
-    yr = est_wsum(yr);
-    yi = est_wsum(yi);
-    if (lane == 0) {
-      const double2 zi = zst[soff[e].u + i];
-      const double2 ui = make_double2(zi.x - yr, zi.y - yi);
-      w[i] = ui;
-      if (u_out) u_out[of.u + i] = ui;
-    }
-  }
-  const int sg = sig[e];
-  if (sg >= 0) {  // element trace coefficients from the slots: uhat_K = R uhat
-    const RSig R = rsig[sg];
-    const int32_t* rp = rint + R.rptr;
-    const int32_t* ri = rint + R.ridx;
-    const double* rw = rdbl + R.rw;
-    const int nt = nh / 2;
-    for (int t = threadIdx.x; t < nh; t += blockDim.x) {
-      const int tt = t < nt ? t : t - nt, base = t < nt ? 0 : nt;
-      double2 a = make_double2(0.0, 0.0);
-      for (int k = rp[tt]; k < rp[tt + 1]; ++k) {
-        const double2 x = us[base + ri[k]];
-        a.x = fma(rw[k], x.x, a.x);
-        a.y = fma(rw[k], x.y, a.y);
-      }
-      w[nu + t] = a;
-    }
-  } else {
-    for (int t = threadIdx.x; t < nh; t += blockDim.x) w[nu + t] = us[t];
-  }
-  __syncthreads();
+  est_w(S, e, of, soff, sig, rsig, rint, rdbl, l2g, xfix, xhat, Zst, zst, w, us, u_out, false);
   for (int i = wid; i < nv; i += nw) {
     const double2* col = A + (size_t)i * N + nv;
     double rr = 0.0, ri2 = 0.0;
@@ -1936,51 +2044,12 @@ __global__ void __launch_bounds__(256) k_est_residual_real(Sizes S, const int* _
   extern __shared__ double2 err_sh[];
   const int slot = blockIdx.x, e = ids[slot];
   const ElemOff of = off[e];
-  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h, m = nu + nh, nE = 3 * S.nL, nt = S.nt;
+  const int N = S.N, nv = S.n_v, nu = S.n_u, nh = S.n_h, m = nu + nh;
   double2* w = err_sh;      // m: u_r, then uhat_r
   double2* us = w + m;      // nh: uhat in the trace slots
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* A = K + (size_t)slot * N * N;
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) us[t] = trace_value(l2g, xfix, xhat, (size_t)of.h + t);
-  __syncthreads();
-  const double2* Ze = Zst + soff[e].Z;
-  for (int i = wid; i < nu; i += nw) {
-    double yr = 0.0, yi = 0.0;
-    for (int j = lane; j < nh; j += 32) {
-      const double2 v = Ze[(size_t)i * nh + j], x = us[j];
-      yr = fma(v.x, x.x, fma(-v.y, x.y, yr));
-      yi = fma(v.x, x.y, fma(v.y, x.x, yi));
-    }
-    yr = est_wsum(yr);
-    yi = est_wsum(yi);
-    if (lane == 0) {
-      const double2 zi = zst[soff[e].u + i];
-      const double2 ui = make_double2(zi.x - yr, zi.y - yi);
-      if (u_out) u_out[of.u + i] = ui;
-      w[i] = i < nE ? make_double2(-ui.y, ui.x) : ui;  // times conj(-i) = i on E
-    }
-  }
-  const int sg = sig[e];
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) {
-    double2 a;
-    if (sg >= 0) {  // uhat_K = R uhat (slots)
-      const RSig R = rsig[sg];
-      const int32_t* rp = rint + R.rptr;
-      const int32_t* ri = rint + R.ridx;
-      const double* rw = rdbl + R.rw;
-      const int tt = t < nt ? t : t - nt, base = t < nt ? 0 : nt;
-      a = make_double2(0.0, 0.0);
-      for (int k = rp[tt]; k < rp[tt + 1]; ++k) {
-        const double2 x = us[base + ri[k]];
-        a.x = fma(rw[k], x.x, a.x);
-        a.y = fma(rw[k], x.y, a.y);
-      }
-    } else {
-      a = us[t];
-    }
-    w[nu + t] = t < nt ? make_double2(-a.y, a.x) : a;  // times i on E-hat
-  }
-  __syncthreads();
+  est_w(S, e, of, soff, sig, rsig, rint, rdbl, l2g, xfix, xhat, Zst, zst, w, us, u_out, true);
   for (int i = wid; i < nv; i += nw) {
     const double* col = A + (size_t)i * N + nv;
     double rr = 0.0, ri2 = 0.0;
@@ -2066,9 +2135,25 @@ int estimate_pass(dpg_handle* h, const double2* xhat, double2* u, double* eta2, 
     return DPG_ERR_STATE;
   }
   DPG_CUDA_TRY(h, cudaMemsetAsync(h->d_est_neg, 0, sizeof(int), s));
+  const bool stored = h->d_Xst && h->xst_valid && h->have_elements && !h->stream;
   for (const ChunkPlan& cp : h->plan) {
     const Group& G = h->grp[cp.g];
     const Sizes& S = G.sz;
+    if (stored) {  // y = L^{-1} r from the X kept by the element pass: no second pass
+      const int* ids = cp.d_ids + cp.ids_off;
+      const size_t sh = sizeof(double2) * (size_t)(S.n_u + 2 * S.n_h);
+      if (cp.real)
+        k_est_stored<true><<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_soff, h->d_sig, h->d_rsig, h->d_rint,
+                                                     h->d_rdbl, h->d_l2g, h->d_xfix, xhat, h->d_Z, h->d_z, h->d_Xst,
+                                                     h->d_xst_off, u, eta2);
+      else
+        k_est_stored<false><<<cp.count, 256, sh, s>>>(S, ids, h->d_off, h->d_soff, h->d_sig, h->d_rsig, h->d_rint,
+                                                      h->d_rdbl, h->d_l2g, h->d_xfix, xhat, h->d_Z, h->d_z, h->d_Xst,
+                                                      h->d_xst_off, u, eta2);
+      DPG_CUDA_TRY(h, cudaGetLastError());
+      h->launches += 1;
+      continue;
+    }
     int rc = DPG_OK;
     if (h->stream) {
       // the chunk's Z, z again (condensation into the chunk stores), then K

@@ -155,6 +155,10 @@ class DPG:
         check(_lib.lib().dpg_set_factor_arith(self.h, int(arith)), self.h)
         self.factor_arith = int(arith)
 
+    def set_estimator_store(self, enable=True):
+        """Keep L^{-1}[B | B-hat | l] from each element pass; eta_K then needs no second element pass."""
+        check(_lib.lib().dpg_set_estimator_store(self.h, int(enable)), self.h)
+
     def set_bucketed(self, enable=True):
         """Order-bucketed element pass: waves of every order's chunks, one persistent factorisation per wave."""
         check(_lib.lib().dpg_set_bucketed(self.h, int(enable)), self.h)

@@ -9,7 +9,9 @@ TE10 port and absorbing end):
   referenced off-rank columns, send lists mirror the halos; only adjacent
   slabs exchange);
 * CG on 2 and 3 gloo ranks reaches the oracle's direct solution, with the
-  iteration count of the single-process CG on the same system.
+  iteration count of the single-process CG on the same system;
+* the same on 2 ranks for the Fichera cavity with mixed orders 1..3 (the
+  oracle's restricted, order-jumping trace system).
 """
 import os
 import socket
@@ -36,6 +38,19 @@ def guide():
     A = sol['A'].tocsr()
     A.sort_indices()
     elem_rows = [sol['free'][g] for g in sol['l2g']]
+    z = mesh.vert[mesh.elem].mean(axis=1)[:, 2]
+    return dict(A=A, b=sol['b'], x=sol['x'], elem_rows=elem_rows, z=z, n=sol['n'])
+
+
+@pytest.fixture(scope="module")
+def fichera():
+    """Mixed orders 1..3 with order jumps across faces (trace restriction)."""
+    from oracle import mixed
+    mesh = inputs.fichera_cavity(1)
+    sol = mixed.solve_mixed(mesh)
+    A = sol['A'].tocsr()
+    A.sort_indices()
+    elem_rows = [sol['free'][gl] for _, gl in sol['R']]
     z = mesh.vert[mesh.elem].mean(axis=1)[:, 2]
     return dict(A=A, b=sol['b'], x=sol['x'], elem_rows=elem_rows, z=z, n=sol['n'])
 
@@ -128,6 +143,16 @@ def _serial_cg_iterations(A, b, rtol):
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_dist_cg_gloo_matches_direct_solve(guide, world):
+    _check_dist_cg(guide, world)
+
+
+def test_dist_cg_gloo_mixed_orders(fichera):
+    er, owner, lays = _layouts(fichera, 2)
+    partition.check_layouts(lays, fichera['A'].indptr, fichera['A'].indices, owner)
+    _check_dist_cg(fichera, 2)
+
+
+def _check_dist_cg(guide, world):
     A = guide['A']
     g = dict(indptr=A.indptr, indices=A.indices, data=A.data, b=guide['b'], elem_rows=guide['elem_rows'],
              z=guide['z'], n=guide['n'])

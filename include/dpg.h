@@ -200,7 +200,8 @@ int dpg_assemble(dpg_handle* h, dpg_stream s);
  * mode DPG_CG_FP64: plain FP64 CG (the paper's solver).  DPG_CG_IR_FP32:
  * iterative refinement, FP64 residuals and updates around FP32 inner CG
  * solves on an FP32 copy of the matrix (inner relative tolerance inner_rtol;
- * about 1e-3 is fastest on the waveguide cases).
+ * about 5e-2 takes the fewest total inner iterations on the 3D waveguide:
+ * restarts are cheap, and a loose inner solve wastes less of its Krylov space).
  * DPG_CG_JACOBI or DPG_CG_BLOCK_JACOBI may be or-ed to either: diagonal
  * preconditioning z = D^{-1} r, or the inverses of the entity diagonal blocks
  * (each mesh entity's E-hat and H-hat unknowns together).  The paper leaves

@@ -102,7 +102,7 @@ class DPG:
         check(_lib.lib().dpg_assemble(self.h, stream_handle(stream)), self.h)
 
     def cg_solve(self, x=None, b=None, mode=_lib.DPG_CG_FP64, rtol=1e-10, atol=0.0, max_iter=100000,
-                 inner_rtol=1e-3, stream=None, raise_on_nonconvergence=True):
+                 inner_rtol=5e-2, stream=None, raise_on_nonconvergence=True):
         if x is None:
             x = torch.zeros(self.n, dtype=torch.complex128, device='cuda')
         rep = _lib.dpg_cg_report()
